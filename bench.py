@@ -1,0 +1,400 @@
+"""Throughput of isolated-system Poisson solves on GB300.
+
+One step = one whole solve (x forward, y forward, z forward x Green's
+spectrum x z inverse, y inverse, x inverse) of the 256^3 multi-sphere
+workload (doubled mesh 512^3, h = 1/256, 8 seeded homogeneous spheres plus a
+Gaussian blob) in FP32, inputs resident in HBM.  Four source/potential pairs
+(512 MB, more than the 129 MB L2) rotate between steps.  Also measured:
+the same solve in FP64, the end-to-end rate through ipf_solve_host (host
+buffers, copies inside the timed region), mean per-pass device times and
+the roofline of the dominant pass.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With --impl reference the FP64 CPU oracle is timed instead (host cores,
+Green's spectrum built once outside the timed steps, as the paper's
+Create/Solve split does).  Multi-GPU runs are independent replicas: each
+rank solves its own stream of workloads; no collective is on the data path.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_BENCH = 256
+METRIC = "isolated solves/s & HBM GB/s at 256^3 (FP32 vs FP64); serving p50/p99 ms"
+WORKLOAD = "multisphere-256: 256^3 cells (doubled mesh 512^3), h=1/256, 8 spheres + Gaussian, seed 0"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="isofft", choices=["isofft", "reference"])
+    ap.add_argument("--n", type=int, default=N_BENCH)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes (what each pass must move at least once)
+# ---------------------------------------------------------------------------
+def pass_bytes(N, M, es):
+    """Per-pass algorithmic HBM bytes of one solve; es = bytes per real."""
+    Nx, Ny, Nz = N
+    Mx, My, Mz = M
+    K = Mx // 2
+    c = 2 * es
+    src = es * Nx * Ny * Nz
+    wy = c * K * Ny * Nz            # x spectra of the active rows
+    wall = c * K * My * Nz          # after the y pass
+    g = es * (My // 2 + 1) * (Mz // 2 + 1) * (K + 1)
+    return {
+        "x_forward": src + wy,
+        "y_forward": wy + wall,
+        "z_convolve": 2 * wall + g,
+        "y_inverse": wall + wy,
+        "x_inverse": wy + src,
+    }
+
+
+PASSES = ["x_forward", "y_forward", "z_convolve", "y_inverse", "x_inverse"]
+KERNELS = {"x_forward": "k_x_forward", "y_forward": "k_y_forward", "z_convolve": "k_z_convolve",
+           "y_inverse": "k_y_inverse", "x_inverse": "k_x_inverse"}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profile_traffic(kernel, tag):
+    """DRAM bytes per launch from the committed ncu summary of `kernel` on
+    this workload, if the kernel sources are unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, tag))
+    if not os.path.exists(path):
+        return None
+    want = sources_digest()
+    traffic, digest = None, None
+    for line in open(path):
+        if line.startswith("traffic_bytes_per_launch:"):
+            traffic = float(line.split(":", 1)[1])
+        if line.startswith("sources_sha256:"):
+            digest = line.split(":", 1)[1].strip()
+    return traffic if digest == want else None
+
+
+def sources_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1106_0557_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.gpu_id is not None:
+            cmd.insert(1, "--id=%s" % self.gpu_id)
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (replicas only: a barrier and a max of times)
+# ---------------------------------------------------------------------------
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "isofft" else "gloo"
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(value, ws, device=None):
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(value, ws, device=None):
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline field)
+# ---------------------------------------------------------------------------
+def time_oracle(n, steps, budget_s):
+    import oracle
+    from paper_1106_0557_gb300 import sources
+    w = sources.multi_sphere(n, seed=0)
+    src = w.source()
+    M = oracle.doubled_mesh(w.N)
+    Gt = oracle.green_spectrum(M, w.h)
+    times = []
+    t_start = time.perf_counter()
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        oracle.solve_with_spectrum(src, M, Gt)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start > budget_s:
+            break
+    return len(times), sum(times), oracle.num_threads()
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    n = args.n
+    done, secs, cores = time_oracle(n, max(1, args.steps), budget_s=150.0)
+    value = done / secs
+    sample = ("%d full %d^3 FP64 oracle solve(s) (doubled mesh %d^3, recursive FFT), Green's spectrum "
+              "built before timing; capped at 150 s of CPU work" % (done, n, 2 * n))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": done, "warmup": 0, "ms_per_step": 1e3 * secs / done, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": [n, n, n], "M": [2 * n] * 3},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def run_isofft(args, ws, rank, local):
+    import torch
+
+    from paper_1106_0557_gb300 import native, sources
+    from paper_1106_0557_gb300.solver import Plan
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    native.lib()
+    n = args.n
+    w = sources.multi_sphere(n, seed=0)
+    src64 = w.source()
+    N = w.N
+    stream = torch.cuda.current_stream()
+
+    def timed_solves(dtype, steps, warmup, pool=4):
+        tdt = torch.float32 if dtype == "f32" else torch.float64
+        plan = Plan(N, w.h, dtype, flags=native.IPF_FLAG_PASS_EVENTS)
+        base = torch.from_numpy(src64).to(dev, tdt)
+        srcs = [base.clone() for _ in range(pool)]
+        outs = [torch.empty_like(base) for _ in range(pool)]
+        for i in range(warmup):
+            plan.solve(srcs[i % pool], outs[i % pool])
+        torch.cuda.synchronize()
+        plan.pass_times()  # reset the accumulated pass means
+        barrier(ws)
+        torch.cuda.synchronize()
+        l0 = native.ipf_launch_count()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for i in range(steps):
+            plan.solve(srcs[i % pool], outs[i % pool])
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+        ms = ev0.elapsed_time(ev1)
+        launches = native.ipf_launch_count() - l0
+        passes = plan.pass_times()
+        M = plan.padded_shape
+        phi = outs[(steps - 1) % pool]
+        finite = bool(torch.isfinite(phi).all().item())
+        plan.close()
+        del srcs, outs
+        torch.cuda.empty_cache()
+        return ms, launches, passes, M, finite
+
+    peak, peak_kind = measured_peaks()
+    gpu_uuid = None
+    try:
+        gpu_uuid = torch.cuda.get_device_properties(local).uuid
+        gpu_uuid = "GPU-" + str(gpu_uuid)
+    except Exception:
+        gpu_uuid = str(local)
+
+    # FP32: the headline
+    with ClockSampler(gpu_uuid) as clk:
+        ms32, launches, passes32, M, finite32 = timed_solves("f32", args.steps, args.warmup)
+    clocks = clk.summary()
+    ms32 = reduce_max(ms32, ws, dev)
+    total = reduce_sum(args.steps, ws, dev)
+    value = total / (ms32 / 1e3)
+    bytes32 = pass_bytes(N, M, 4)
+    gbs32 = sum(bytes32.values()) / (ms32 / args.steps / 1e3) / 1e9
+
+    # FP64 (fewer steps: the FP64 units of this part are a small fraction of FP32)
+    steps64 = max(3, args.steps // 10)
+    ms64, _, passes64, _, finite64 = timed_solves("f64", steps64, max(3, args.warmup // 4))
+    ms64 = reduce_max(ms64, ws, dev)
+    value64 = reduce_sum(steps64, ws, dev) / (ms64 / 1e3)
+    bytes64 = pass_bytes(N, M, 8)
+    gbs64 = sum(bytes64.values()) / (ms64 / steps64 / 1e3) / 1e9
+
+    # end to end through the public host-buffer entry point
+    plan = Plan(N, w.h, "f32")
+    hsrc = torch.from_numpy(src64.astype(np.float32)).pin_memory()
+    hphi = torch.empty_like(hsrc).pin_memory()
+    sh = stream.cuda_stream
+    for _ in range(3):
+        native.ipf_solve_host(plan.handle, hsrc.data_ptr(), hphi.data_ptr(), sh)
+    e2e_steps = max(3, min(args.steps, 200))
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        native.ipf_solve_host(plan.handle, hsrc.data_ptr(), hphi.data_ptr(), sh)
+    t_e2e = time.perf_counter() - t0
+    barrier(ws)
+    plan.close()
+    t_e2e = reduce_max(t_e2e, ws, dev)
+    e2e_value = reduce_sum(e2e_steps, ws, dev) / t_e2e
+    io_bytes = hsrc.numel() * hsrc.element_size()
+
+    # roofline of the dominant pass (the longest mean device time)
+    dom = max(range(5), key=lambda i: passes32[i])
+    dname = PASSES[dom]
+    achieved = bytes32[dname] / (passes32[dom] / 1e3) / 1e9
+    traffic = profile_traffic(KERNELS[dname], "f32_%d" % n)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        done, secs, cores = time_oracle(n, 1, budget_s=60.0)
+        cpu = {"value": done / secs, "unit": "solves/s", "cores": cores, "kind": "oracle",
+               "sample": "%d full %d^3 FP64 oracle solve (doubled mesh %d^3), Green's spectrum built "
+                         "before timing" % (done, n, 2 * n)}
+
+    if rank != 0:
+        return
+    per_pass = {}
+    for i, p in enumerate(PASSES):
+        per_pass[p] = {"ms_f32": round(passes32[i], 5), "gbs_f32": round(bytes32[p] / (passes32[i] / 1e3) / 1e9, 1),
+                       "ms_f64": round(passes64[i], 5), "gbs_f64": round(bytes64[p] / (passes64[i] / 1e3) / 1e9, 1)}
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": list(N), "M": list(M), "h": w.h[0],
+                   "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": "4 rotating src/phi pairs (%d MB) > 129 MB L2" % (8 * 4 * n ** 3 // 2 ** 20)},
+        "hbm_gbs": round(gbs32, 1),
+        "fp64": {"value": value64, "unit": "solves/s", "ms_per_step": ms64 / steps64, "steps": steps64,
+                 "hbm_gbs": round(gbs64, 1)},
+        "passes": per_pass,
+        "roofline": {"bound": "hbm", "kernel": KERNELS[dname], "achieved": round(achieved, 1), "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": traffic, "algorithmic_bytes": bytes32[dname]},
+        "e2e": {"value": e2e_value, "unit": "solves/s", "steps": e2e_steps, "h2d_bytes_per_step": io_bytes,
+                "d2h_bytes_per_step": io_bytes},
+        "cpu_baseline": cpu,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "finite": finite32 and finite64,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_isofft(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

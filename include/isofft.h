@@ -1,0 +1,152 @@
+/*
+ * isofft.h -- C ABI of the GB300 isolated-system Poisson solver.
+ *
+ * The library solves Poisson's equation  lap(Phi) = S  on a regular mesh of
+ * N = (Nx, Ny, Nz) cells with widths h = (hx, hy, hz) and the boundary
+ * condition Phi -> 0 at infinity (paper Sec. 2.1, Eq. 1), by Hockney's mesh
+ * doubling: the source is zero-padded to a doubled mesh M >= 2N per axis, a
+ * real-to-complex 3-D DFT is taken, the result is multiplied by the transform
+ * of the doubled-mesh Green's function of Eq. 9 (built from Eq. 6), and the
+ * inverse DFT is cropped back to the N active cells (Sec. 2.2.2).
+ * The result is the discrete aperiodic convolution
+ *     Phi[i,j,k] = sum_{i',j',k'} G(i-i', j-j', k-k') S[i',j',k']
+ * with G(d) = -hx hy hz / (4 pi |(hx dx, hy dy, hz dz)|) for d != 0 and
+ * G(0) = -hx hy hz / (4 pi min(h)); Phi <= 0 where S >= 0 (Eq. 2 sign).
+ * For gravity with Newton's constant 1 pass S = 4 pi rho.
+ *
+ * Conventions shared by every entry point:
+ *   - Arrays are C order [z][y][x], x contiguous (the paper's first Fortran
+ *     index is x, Sec. 3.2), of `float` for IPF_F32 plans and `double` for
+ *     IPF_F64 plans.  Device buffers must be 16-byte aligned.
+ *   - Device pointers are CUDA device (or managed) memory of the calling
+ *     thread's current device; host pointers are ordinary host memory
+ *     (pinned memory makes the copies faster but is not required).
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Work is enqueued asynchronously on it unless stated otherwise.
+ *   - Every call returns an int status (ipf_status below); nothing throws
+ *     across the ABI.  ipf_status_string() names a status.
+ *   - A plan is used by one stream at a time (it owns one workspace).
+ *   - The caller owns its buffers.  A plan owns its workspace; the library
+ *     owns the cache of Green's spectra, shared by plans of equal doubled
+ *     mesh, width ratios and dtype.
+ */
+#ifndef ISOFFT_H
+#define ISOFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ipf_plan_s *ipf_plan_t;
+
+/* arithmetic type of a plan's buffers and butterflies */
+typedef enum { IPF_F32 = 0, IPF_F64 = 1 } ipf_dtype;
+
+typedef enum {
+    IPF_OK = 0,
+    IPF_INVALID_ARG = 1,      /* null pointer, bad size/width/dtype/flag */
+    IPF_UNSUPPORTED_SIZE = 2, /* a doubled mesh beyond the largest kernel */
+    IPF_OUT_OF_MEMORY = 3,    /* a device or host allocation failed */
+    IPF_CUDA_ERROR = 4,       /* a CUDA runtime call failed; see ipf_last_cuda_error */
+    IPF_TIMEOUT = 5,          /* a bounded device wait gave up */
+    IPF_BUDGET_EXCEEDED = 6,  /* the request does not fit the memory budget */
+    IPF_NOT_READY = 7         /* asynchronous work has not finished */
+} ipf_status;
+
+/* Verbosity levels, in decreasing order of output (paper Sec. 3.2:
+ * CONSOLE_INFO_2 > CONSOLE_INFO_1 > CONSOLE_WARNING > CONSOLE_ERROR, the
+ * last being the default).  Messages go to stderr. */
+enum { IPF_CONSOLE_ERROR = 0, IPF_CONSOLE_WARNING = 1, IPF_CONSOLE_INFO_1 = 2, IPF_CONSOLE_INFO_2 = 3 };
+
+/* Plan flags. */
+enum {
+    IPF_FLAG_PASS_EVENTS = 1u << 0 /* record CUDA events around each pass so
+                                      ipf_plan_pass_times can report them */
+};
+
+/* Create a solver for an Nx x Ny x Nz mesh of widths h (paper Sec. 3.2,
+ * `Create(PoissonSolver, CellWidth, nTotalCells, ...)`).
+ *   out        receives the plan handle (NULL on failure).
+ *   n          {Nx, Ny, Nz}, each >= 1; the doubled mesh 2N must fit the
+ *              largest supported length (1024), else IPF_UNSUPPORTED_SIZE.
+ *   h          {hx, hy, hz}, each finite and > 0.
+ *   dtype      IPF_F32 or IPF_F64.  The Green's spectrum is always built in
+ *              FP64 and rounded to the plan's dtype.
+ *   flags      a bitwise OR of IPF_FLAG_*.
+ *   verbosity  an IPF_CONSOLE_* level.
+ *   stream     stream used for the one-off set-up work (Green's spectrum
+ *              build, table uploads); the call synchronises on it before
+ *              returning.
+ * Allocates the plan's workspace (complex Nz x My x Mx/2) on the current
+ * device and, on a cache miss, the Green's spectrum. */
+int ipf_plan_create(ipf_plan_t *out, const int64_t n[3], const double h[3], int dtype,
+                    uint32_t flags, int verbosity, void *stream);
+
+/* Release a plan, its workspace and its reference to the cached spectrum.
+ * Waits for nothing: the caller must not destroy a plan with work still in
+ * flight.  NULL is accepted and ignored. */
+int ipf_plan_destroy(ipf_plan_t plan);
+
+/* The doubled mesh M = {Mx, My, Mz} the plan transforms on (>= 2N, a
+ * supported length; any M >= 2N - 1 gives the same cropped result). */
+int ipf_plan_padded_shape(const ipf_plan_t plan, int64_t m[3]);
+
+/* Device bytes the plan owns (its workspace), and the bytes of the cached
+ * Green's spectrum it references, for admission against a memory budget. */
+int ipf_plan_workspace_bytes(const ipf_plan_t plan, size_t *bytes);
+int ipf_plan_spectrum_bytes(const ipf_plan_t plan, size_t *bytes);
+
+/* Device bytes a plan of this shape and dtype would need (workspace plus the
+ * spectrum if it is not cached yet), without creating it. */
+int ipf_estimate_bytes(const int64_t n[3], const double h[3], int dtype, size_t *bytes);
+
+/* One solve (paper Sec. 3.2, `Solve(PoissonSolver, SourceSolution)`):
+ * d_src and d_phi are device arrays of Nz*Ny*Nx elements of the plan's
+ * dtype; d_phi may equal d_src (the paper overwrites the source with the
+ * potential).  Enqueues the five passes on `stream` and returns without
+ * waiting. */
+int ipf_solve(ipf_plan_t plan, const void *d_src, void *d_phi, void *stream);
+
+/* One solve from and to HOST memory: copies h_src to a device staging
+ * buffer owned by the plan, solves, copies the potential back to h_phi and
+ * synchronises `stream` before returning. */
+int ipf_solve_host(ipf_plan_t plan, const void *h_src, void *h_phi, void *stream);
+
+/* Submit `count` independent solves, possibly of different shapes and
+ * dtypes, on one stream; plans[i] solves d_src[i] into d_phi[i].  A plan may
+ * appear only once per batch (each owns one workspace).  Asynchronous. */
+int ipf_submit_batch(const ipf_plan_t *plans, int count, const void *const *d_src,
+                     void *const *d_phi, void *stream);
+
+/* With IPF_FLAG_PASS_EVENTS: mean device milliseconds of each of the five
+ * passes (x forward, y forward, z forward x spectrum x z inverse, y inverse,
+ * x inverse) over the solves made on this plan since the previous call, then
+ * a reset.  Events are recorded on the solving stream between the passes;
+ * the call waits for them.  IPF_NOT_READY if no solve was made since the
+ * previous call; IPF_INVALID_ARG without the flag. */
+int ipf_plan_pass_times(ipf_plan_t plan, float ms[5]);
+
+/* Bytes held by the library's cache of Green's spectra, and a trim of
+ * unreferenced entries (least recently used first) until the cache holds
+ * at most `budget` bytes. */
+int ipf_greens_cache_bytes(size_t *bytes);
+int ipf_greens_cache_trim(size_t budget);
+
+/* Number of kernel launches made by this process so far (all entry points),
+ * for checking that the GPU path ran. */
+int ipf_launch_count(uint64_t *count);
+
+/* The last CUDA error code seen by the library on this thread (0 if none). */
+int ipf_last_cuda_error(void);
+
+/* Static description of a status code; never NULL. */
+const char *ipf_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISOFFT_H */

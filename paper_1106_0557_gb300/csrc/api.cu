@@ -1,0 +1,539 @@
+// api.cu -- the C ABI of include/isofft.h: plans, the Green's-spectrum
+// cache, and the enqueueing of the five passes of a solve.
+//
+// Create / Solve / Destroy follow the paper's usage (Sec. 3.2).  The
+// transform of the Green's function is computed once per (doubled mesh,
+// width ratios, dtype) and kept on the device (Sec. 2.2.2, "computed only
+// once ... stored permanently"); plans of equal doubled mesh and ratios share
+// it, scaled by min(h)^2 (the Green's function of Eq. 6 scales as h^2).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "../../include/isofft.h"
+#include "launch.h"
+
+namespace isofft {
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+static thread_local int g_last_cuda = 0;
+
+static int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return IPF_OK;
+    g_last_cuda = (int)e;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();  // allocation failures are not sticky; clear them
+        return IPF_OUT_OF_MEMORY;
+    }
+    return IPF_CUDA_ERROR;
+}
+
+static void logf(int level, int verbosity, const char *fmt, ...)
+{
+    if (level > verbosity) return;
+    va_list ap;
+    va_start(ap, fmt);
+    fprintf(stderr, "[isofft] ");
+    vfprintf(stderr, fmt, ap);
+    fprintf(stderr, "\n");
+    va_end(ap);
+}
+
+static int env_verbosity()
+{
+    const char *s = getenv("ISOFFT_VERBOSITY");
+    if (!s) return -1;
+    int v = atoi(s);
+    return v < 0 ? 0 : (v > 3 ? 3 : v);
+}
+
+// ----------------------------------------------------------------------
+// Green's spectrum cache
+// ----------------------------------------------------------------------
+struct SpecKey {
+    int device, dtype;
+    int64_t M[3];
+    double hn[3];
+    bool operator<(const SpecKey &o) const
+    {
+        return std::tie(device, dtype, M[0], M[1], M[2], hn[0], hn[1], hn[2]) <
+               std::tie(o.device, o.dtype, o.M[0], o.M[1], o.M[2], o.hn[0], o.hn[1], o.hn[2]);
+    }
+};
+struct SpecEntry {
+    void *G = nullptr;   // [My/2+1][Mz/2+1][Mx/2]
+    void *Gs = nullptr;  // [My/2+1][Mz/2+1]
+    size_t bytes = 0;
+    int refs = 0;
+    uint64_t last_use = 0;
+};
+
+static std::mutex g_cache_mu;
+static std::map<SpecKey, SpecEntry> g_cache;
+static uint64_t g_clock = 0;
+
+static size_t spectrum_bytes(const int64_t M[3], int dtype)
+{
+    const size_t es = dtype == IPF_F32 ? 4 : 8;
+    const size_t Y = M[1] / 2 + 1, Z = M[2] / 2 + 1, K = M[0] / 2;
+    return es * Y * Z * (K + 1);
+}
+
+static void free_entry(SpecEntry &e)
+{
+    if (e.G) cudaFree(e.G);
+    e.G = e.Gs = nullptr;
+}
+
+}  // namespace isofft
+
+using namespace isofft;
+
+struct ipf_plan_s {
+    int64_t N[3];
+    int64_t M[3];
+    double h[3];
+    int dtype;
+    uint32_t flags;
+    int verbosity;
+    int device;
+    SpecKey key;
+    SpecEntry *spec;  // owned by the cache, referenced
+    double gscale;
+    void *W = nullptr;
+    size_t W_bytes = 0;
+    void *tables = nullptr;  // tw_x | rtw | tw_y | tw_z
+    const void *tw_x = nullptr, *rtw = nullptr, *tw_y = nullptr, *tw_z = nullptr;
+    void *stage = nullptr;  // device staging for ipf_solve_host
+    // IPF_FLAG_PASS_EVENTS: a ring of event sets, one per recent solve; a
+    // slot is folded into the running sums before it is reused, so timing
+    // many back-to-back solves never waits on the device.
+    static constexpr int kSlots = 64;
+    cudaEvent_t ev[kSlots][6] = {};
+    bool have_events = false;
+    uint64_t solves = 0, folded = 0;
+    double pass_sum[5] = {0, 0, 0, 0, 0};
+    uint64_t pass_n = 0;
+};
+
+namespace {
+
+int64_t choose_mesh(int64_t n)
+{
+    for (int m : kSupportedM)
+        if (m >= 2 * n) return m;
+    return -1;
+}
+
+size_t elem_size(int dtype) { return dtype == IPF_F32 ? 4 : 8; }
+
+int validate(const int64_t n[3], const double h[3], int dtype)
+{
+    if (!n || !h) return IPF_INVALID_ARG;
+    if (dtype != IPF_F32 && dtype != IPF_F64) return IPF_INVALID_ARG;
+    for (int a = 0; a < 3; ++a) {
+        if (n[a] < 1) return IPF_INVALID_ARG;
+        if (!(h[a] > 0.0) || !isfinite(h[a])) return IPF_INVALID_ARG;
+    }
+    for (int a = 0; a < 3; ++a)
+        if (choose_mesh(n[a]) < 0) return IPF_UNSUPPORTED_SIZE;
+    return IPF_OK;
+}
+
+void normalized_widths(const double h[3], double hn[3], double *hmin)
+{
+    double m = h[0];
+    if (h[1] < m) m = h[1];
+    if (h[2] < m) m = h[2];
+    for (int a = 0; a < 3; ++a) hn[a] = h[a] / m;
+    *hmin = m;
+}
+
+// Upload e^{-2 pi i k / n} tables in the plan's dtype.
+template <typename T>
+void fill_roots(std::vector<T> &dst, size_t off, int64_t n, int64_t count)
+{
+    std::vector<double> re(count), im(count);
+    host_roots(n, count, re.data(), im.data());
+    for (int64_t k = 0; k < count; ++k) {
+        dst[off + 2 * k] = (T)re[k];
+        dst[off + 2 * k + 1] = (T)im[k];
+    }
+}
+
+template <typename T>
+int upload_tables(ipf_plan_s *p, cudaStream_t st)
+{
+    const int64_t Lx = p->M[0] / 2, My = p->M[1], Mz = p->M[2];
+    // tw_x: W_Lx^k (k < Lx); rtw: W_Mx^k (k < Lx); tw_y: W_My^k; tw_z: W_Mz^k
+    const size_t ox = 0, orr = 2 * Lx, oy = 4 * Lx, oz = 4 * Lx + 2 * My, tot = 4 * Lx + 2 * My + 2 * Mz;
+    std::vector<T> h(tot);
+    fill_roots<T>(h, ox, Lx, Lx);
+    fill_roots<T>(h, orr, p->M[0], Lx);
+    fill_roots<T>(h, oy, My, My);
+    fill_roots<T>(h, oz, Mz, Mz);
+    cudaError_t e = cudaMalloc(&p->tables, tot * sizeof(T));
+    if (e != cudaSuccess) return cuda_status(e);
+    e = cudaMemcpyAsync(p->tables, h.data(), tot * sizeof(T), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
+    T *b = (T *)p->tables;
+    p->tw_x = b + ox;
+    p->rtw = b + orr;
+    p->tw_y = b + oy;
+    p->tw_z = b + oz;
+    return IPF_OK;
+}
+
+int acquire_spectrum(ipf_plan_s *p, cudaStream_t st)
+{
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = g_cache.find(p->key);
+    if (it == g_cache.end()) {
+        SpecEntry e;
+        e.bytes = spectrum_bytes(p->M, p->dtype);
+        cudaError_t ce = cudaMalloc(&e.G, e.bytes);
+        if (ce != cudaSuccess) return cuda_status(ce);
+        const size_t es = elem_size(p->dtype);
+        const size_t Y = p->M[1] / 2 + 1, Z = p->M[2] / 2 + 1, K = p->M[0] / 2;
+        e.Gs = (char *)e.G + es * Y * Z * K;
+        logf(IPF_CONSOLE_INFO_1, p->verbosity, "building Green's spectrum for mesh %lldx%lldx%lld (%s)",
+             (long long)p->M[0], (long long)p->M[1], (long long)p->M[2], p->dtype == IPF_F32 ? "f32" : "f64");
+        if (p->dtype == IPF_F32)
+            ce = build_green_spectrum<float>(p->M, p->key.hn, (float *)e.G, (float *)e.Gs, st);
+        else
+            ce = build_green_spectrum<double>(p->M, p->key.hn, (double *)e.G, (double *)e.Gs, st);
+        if (ce != cudaSuccess) {
+            free_entry(e);
+            return cuda_status(ce);
+        }
+        it = g_cache.emplace(p->key, e).first;
+    }
+    it->second.refs += 1;
+    it->second.last_use = ++g_clock;
+    p->spec = &it->second;
+    return IPF_OK;
+}
+
+void release_spectrum(ipf_plan_s *p)
+{
+    if (!p->spec) return;
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = g_cache.find(p->key);
+    if (it != g_cache.end()) it->second.refs -= 1;
+    p->spec = nullptr;
+}
+
+// Fold the pass times of solve number `i` (its events have completed or are
+// waited for) into the plan's running sums.
+cudaError_t fold_slot(ipf_plan_s *p, uint64_t i)
+{
+    cudaEvent_t *e = p->ev[i % ipf_plan_s::kSlots];
+    cudaError_t r = cudaEventSynchronize(e[5]);
+    if (r != cudaSuccess) return r;
+    for (int k = 0; k < 5; ++k) {
+        float ms = 0.f;
+        r = cudaEventElapsedTime(&ms, e[k], e[k + 1]);
+        if (r != cudaSuccess) return r;
+        p->pass_sum[k] += ms;
+    }
+    p->pass_n += 1;
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t enqueue_solve(ipf_plan_s *p, const void *src, void *phi, cudaStream_t st)
+{
+    const int Nx = (int)p->N[0], Ny = (int)p->N[1], Nz = (int)p->N[2];
+    const int Lx = (int)(p->M[0] / 2), My = (int)p->M[1], Mz = (int)p->M[2];
+    const int64_t nrows = (int64_t)Ny * Nz;
+    const bool ev_on = p->have_events;
+    cudaEvent_t *ev = nullptr;
+    cudaError_t e;
+    if (ev_on) {
+        if (p->solves - p->folded == (uint64_t)ipf_plan_s::kSlots) {
+            e = fold_slot(p, p->folded);
+            if (e != cudaSuccess) return e;
+            p->folded += 1;
+        }
+        ev = p->ev[p->solves % ipf_plan_s::kSlots];
+        p->solves += 1;
+    }
+    if (ev_on) cudaEventRecord(ev[0], st);
+    e = launch_x_forward<T>(Lx, (const T *)src, p->W, p->tw_x, p->rtw, Nx, Ny, My, nrows, st);
+    if (e != cudaSuccess) return e;
+    if (ev_on) cudaEventRecord(ev[1], st);
+    e = launch_y_forward<T>(My, p->W, p->tw_y, Ny, Lx, Nz, st);
+    if (e != cudaSuccess) return e;
+    if (ev_on) cudaEventRecord(ev[2], st);
+    e = launch_z_convolve<T>(Mz, p->W, p->tw_z, (const T *)p->spec->G, (const T *)p->spec->Gs,
+                             (T)p->gscale, Nz, My, Lx, st);
+    if (e != cudaSuccess) return e;
+    if (ev_on) cudaEventRecord(ev[3], st);
+    e = launch_y_inverse<T>(My, p->W, p->tw_y, Ny, Lx, Nz, st);
+    if (e != cudaSuccess) return e;
+    if (ev_on) cudaEventRecord(ev[4], st);
+    e = launch_x_inverse<T>(Lx, p->W, (T *)phi, p->tw_x, p->rtw, Nx, Ny, My, nrows, st);
+    if (e != cudaSuccess) return e;
+    if (ev_on) cudaEventRecord(ev[5], st);
+    return cudaSuccess;
+}
+
+int solve_impl(ipf_plan_s *p, const void *src, void *phi, cudaStream_t st)
+{
+    cudaError_t e = p->dtype == IPF_F32 ? enqueue_solve<float>(p, src, phi, st)
+                                        : enqueue_solve<double>(p, src, phi, st);
+    return cuda_status(e);
+}
+
+bool aligned16(const void *ptr) { return ((uintptr_t)ptr & 15u) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+int ipf_plan_create(ipf_plan_t *out, const int64_t n[3], const double h[3], int dtype, uint32_t flags,
+                    int verbosity, void *stream)
+{
+    if (!out) return IPF_INVALID_ARG;
+    *out = nullptr;
+    int rc = validate(n, h, dtype);
+    if (rc) return rc;
+    if (flags & ~(uint32_t)IPF_FLAG_PASS_EVENTS) return IPF_INVALID_ARG;
+    if (verbosity < IPF_CONSOLE_ERROR || verbosity > IPF_CONSOLE_INFO_2) return IPF_INVALID_ARG;
+    const int ev = env_verbosity();
+    if (ev >= 0) verbosity = ev;
+    cudaStream_t st = (cudaStream_t)stream;
+    ipf_plan_s *p = new (std::nothrow) ipf_plan_s();
+    if (!p) return IPF_OUT_OF_MEMORY;
+    for (int a = 0; a < 3; ++a) {
+        p->N[a] = n[a];
+        p->M[a] = choose_mesh(n[a]);
+        p->h[a] = h[a];
+    }
+    p->dtype = dtype;
+    p->flags = flags;
+    p->verbosity = verbosity;
+    p->spec = nullptr;
+    cudaError_t ce = cudaGetDevice(&p->device);
+    if (ce != cudaSuccess) {
+        delete p;
+        return cuda_status(ce);
+    }
+    double hmin;
+    normalized_widths(h, p->key.hn, &hmin);
+    p->gscale = hmin * hmin;
+    p->key.device = p->device;
+    p->key.dtype = dtype;
+    for (int a = 0; a < 3; ++a) p->key.M[a] = p->M[a];
+
+    p->W_bytes = 2 * elem_size(dtype) * (size_t)p->N[2] * (size_t)p->M[1] * (size_t)(p->M[0] / 2);
+    ce = cudaMalloc(&p->W, p->W_bytes);
+    if (ce != cudaSuccess) {
+        rc = cuda_status(ce);
+        ipf_plan_destroy(p);
+        return rc;
+    }
+    rc = dtype == IPF_F32 ? upload_tables<float>(p, st) : upload_tables<double>(p, st);
+    if (!rc) rc = acquire_spectrum(p, st);
+    if (!rc && (flags & IPF_FLAG_PASS_EVENTS)) {
+        for (int s = 0; s < ipf_plan_s::kSlots && !rc; ++s)
+            for (int i = 0; i < 6 && !rc; ++i) rc = cuda_status(cudaEventCreate(&p->ev[s][i]));
+        p->have_events = !rc;
+    }
+    if (rc) {
+        ipf_plan_destroy(p);
+        return rc;
+    }
+    logf(IPF_CONSOLE_INFO_2, p->verbosity, "plan %lldx%lldx%lld on mesh %lldx%lldx%lld, workspace %zu bytes",
+         (long long)n[0], (long long)n[1], (long long)n[2], (long long)p->M[0], (long long)p->M[1],
+         (long long)p->M[2], p->W_bytes);
+    *out = p;
+    return IPF_OK;
+}
+
+int ipf_plan_destroy(ipf_plan_t p)
+{
+    if (!p) return IPF_OK;
+    release_spectrum(p);
+    if (p->W) cudaFree(p->W);
+    if (p->tables) cudaFree(p->tables);
+    if (p->stage) cudaFree(p->stage);
+    for (int s = 0; s < ipf_plan_s::kSlots; ++s)
+        for (int i = 0; i < 6; ++i)
+            if (p->ev[s][i]) cudaEventDestroy(p->ev[s][i]);
+    delete p;
+    return IPF_OK;
+}
+
+int ipf_plan_padded_shape(const ipf_plan_t p, int64_t m[3])
+{
+    if (!p || !m) return IPF_INVALID_ARG;
+    for (int a = 0; a < 3; ++a) m[a] = p->M[a];
+    return IPF_OK;
+}
+
+int ipf_plan_workspace_bytes(const ipf_plan_t p, size_t *bytes)
+{
+    if (!p || !bytes) return IPF_INVALID_ARG;
+    *bytes = p->W_bytes;
+    return IPF_OK;
+}
+
+int ipf_plan_spectrum_bytes(const ipf_plan_t p, size_t *bytes)
+{
+    if (!p || !bytes || !p->spec) return IPF_INVALID_ARG;
+    *bytes = p->spec->bytes;
+    return IPF_OK;
+}
+
+int ipf_estimate_bytes(const int64_t n[3], const double h[3], int dtype, size_t *bytes)
+{
+    if (!bytes) return IPF_INVALID_ARG;
+    int rc = validate(n, h, dtype);
+    if (rc) return rc;
+    int64_t M[3];
+    for (int a = 0; a < 3; ++a) M[a] = choose_mesh(n[a]);
+    size_t w = 2 * elem_size(dtype) * (size_t)n[2] * (size_t)M[1] * (size_t)(M[0] / 2);
+    SpecKey key;
+    double hmin;
+    normalized_widths(h, key.hn, &hmin);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaGetLastError();
+    key.device = dev;
+    key.dtype = dtype;
+    for (int a = 0; a < 3; ++a) key.M[a] = M[a];
+    bool cached;
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        cached = g_cache.count(key) != 0;
+    }
+    *bytes = w + (cached ? 0 : spectrum_bytes(M, dtype));
+    return IPF_OK;
+}
+
+int ipf_solve(ipf_plan_t p, const void *d_src, void *d_phi, void *stream)
+{
+    if (!p || !d_src || !d_phi) return IPF_INVALID_ARG;
+    if (!aligned16(d_src) || !aligned16(d_phi)) return IPF_INVALID_ARG;
+    return solve_impl(p, d_src, d_phi, (cudaStream_t)stream);
+}
+
+int ipf_solve_host(ipf_plan_t p, const void *h_src, void *h_phi, void *stream)
+{
+    if (!p || !h_src || !h_phi) return IPF_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = elem_size(p->dtype) * (size_t)p->N[0] * (size_t)p->N[1] * (size_t)p->N[2];
+    if (!p->stage) {
+        cudaError_t e = cudaMalloc(&p->stage, bytes);
+        if (e != cudaSuccess) {
+            p->stage = nullptr;
+            return cuda_status(e);
+        }
+    }
+    cudaError_t e = cudaMemcpyAsync(p->stage, h_src, bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    int rc = solve_impl(p, p->stage, p->stage, st);
+    if (rc) return rc;
+    e = cudaMemcpyAsync(h_phi, p->stage, bytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return cuda_status(e);
+}
+
+int ipf_submit_batch(const ipf_plan_t *plans, int count, const void *const *d_src, void *const *d_phi,
+                     void *stream)
+{
+    if (count < 0 || (count > 0 && (!plans || !d_src || !d_phi))) return IPF_INVALID_ARG;
+    for (int i = 0; i < count; ++i) {
+        if (!plans[i] || !d_src[i] || !d_phi[i]) return IPF_INVALID_ARG;
+        if (!aligned16(d_src[i]) || !aligned16(d_phi[i])) return IPF_INVALID_ARG;
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == plans[i]) return IPF_INVALID_ARG;
+    }
+    for (int i = 0; i < count; ++i) {
+        int rc = solve_impl(plans[i], d_src[i], d_phi[i], (cudaStream_t)stream);
+        if (rc) return rc;
+    }
+    return IPF_OK;
+}
+
+int ipf_plan_pass_times(ipf_plan_t p, float ms[5])
+{
+    if (!p || !ms || !p->have_events) return IPF_INVALID_ARG;
+    while (p->folded < p->solves) {
+        cudaError_t e = fold_slot(p, p->folded);
+        if (e != cudaSuccess) return cuda_status(e);
+        p->folded += 1;
+    }
+    if (p->pass_n == 0) return IPF_NOT_READY;
+    for (int i = 0; i < 5; ++i) ms[i] = (float)(p->pass_sum[i] / (double)p->pass_n);
+    for (int i = 0; i < 5; ++i) p->pass_sum[i] = 0.0;
+    p->pass_n = 0;
+    return IPF_OK;
+}
+
+int ipf_greens_cache_bytes(size_t *bytes)
+{
+    if (!bytes) return IPF_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    size_t b = 0;
+    for (auto &kv : g_cache) b += kv.second.bytes;
+    *bytes = b;
+    return IPF_OK;
+}
+
+int ipf_greens_cache_trim(size_t budget)
+{
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    size_t b = 0;
+    for (auto &kv : g_cache) b += kv.second.bytes;
+    while (b > budget) {
+        auto victim = g_cache.end();
+        for (auto it = g_cache.begin(); it != g_cache.end(); ++it)
+            if (it->second.refs == 0 && (victim == g_cache.end() || it->second.last_use < victim->second.last_use))
+                victim = it;
+        if (victim == g_cache.end()) break;
+        b -= victim->second.bytes;
+        free_entry(victim->second);
+        g_cache.erase(victim);
+    }
+    return IPF_OK;
+}
+
+int ipf_launch_count(uint64_t *count)
+{
+    if (!count) return IPF_INVALID_ARG;
+    *count = g_launches.load();
+    return IPF_OK;
+}
+
+int ipf_last_cuda_error(void) { return g_last_cuda; }
+
+const char *ipf_status_string(int s)
+{
+    switch (s) {
+    case IPF_OK: return "ok";
+    case IPF_INVALID_ARG: return "invalid argument";
+    case IPF_UNSUPPORTED_SIZE: return "unsupported size";
+    case IPF_OUT_OF_MEMORY: return "out of memory";
+    case IPF_CUDA_ERROR: return "CUDA error";
+    case IPF_TIMEOUT: return "timeout";
+    case IPF_BUDGET_EXCEEDED: return "memory budget exceeded";
+    case IPF_NOT_READY: return "not ready";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,356 @@
+// fft_engine.cuh -- register-resident Stockham FFT building blocks for sm_103a.
+//
+// One line of L complex points is spread over NT = L / E threads, each thread
+// holding E points in registers.  Thread t always holds the points at
+// positions t + m * NT (m < E) before a stage; the stage multiplies by the
+// Stockham twiddles, runs E / R radix-R butterflies in registers, and the
+// outputs are exchanged through shared memory so that every thread again
+// holds positions t + m * NT.  After the last stage thread t holds output
+// bins t + m * NT in natural order, so global loads and stores of a line are
+// coalesced along the line for row passes and along the tile for column
+// passes, and the spectrum multiply of the z pass needs no exchange at all.
+//
+// The forward transform is X[k] = sum_j x[j] e^{-2 pi i jk/L} (unnormalised).
+// The inverse is obtained as swap(FFT(swap(x))), swap exchanging real and
+// imaginary parts, which costs nothing in registers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace isofft {
+
+// Building blocks are host-callable too, so a host harness can run the
+// exact stage code against a direct DFT.
+#define ISOFFT_HD __host__ __device__ __forceinline__
+
+template <typename T>
+struct alignas(2 * sizeof(T)) Cx {
+    T x, y;
+};
+
+template <typename T>
+ISOFFT_HD Cx<T> cadd(Cx<T> a, Cx<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename T>
+ISOFFT_HD Cx<T> csub(Cx<T> a, Cx<T> b) { return {a.x - b.x, a.y - b.y}; }
+template <typename T>
+ISOFFT_HD Cx<T> cmul(Cx<T> a, Cx<T> b)
+{
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename T>
+ISOFFT_HD Cx<T> cscale(Cx<T> a, T s) { return {a.x * s, a.y * s}; }
+template <typename T>
+ISOFFT_HD Cx<T> cconj(Cx<T> a) { return {a.x, -a.y}; }
+// multiply by -i
+template <typename T>
+ISOFFT_HD Cx<T> cmul_mi(Cx<T> a) { return {a.y, -a.x}; }
+// exchange real and imaginary parts
+template <typename T>
+ISOFFT_HD Cx<T> cswap(Cx<T> a) { return {a.y, a.x}; }
+
+// cos(2 pi j / 48) for j in [0, 12] (first quadrant); other angles follow by
+// exact symmetry so that W and its mirror images round identically.
+__host__ __device__ constexpr double cos48_base(int j)
+{
+    constexpr double b[13] = {1.0, 0.9914448613738104, 0.9659258262890683, 0.9238795325112867,
+                              0.8660254037844387, 0.7933533402912352, 0.7071067811865476,
+                              0.6087614290087207, 0.5, 0.3826834323650898, 0.25881904510252074,
+                              0.13052619222005157, 0.0};
+    return b[j];
+}
+__host__ __device__ constexpr double cos48(int j)
+{
+    j %= 48;
+    if (j < 0) j += 48;
+    if (j > 24) j = 48 - j;
+    return j > 12 ? -cos48_base(24 - j) : cos48_base(j);
+}
+__host__ __device__ constexpr double sin48(int j) { return cos48(12 - j); }
+
+// Multiply by the compile-time root W_R^e = e^{-2 pi i e / R} (48 % R == 0).
+template <typename T, int R, int e>
+ISOFFT_HD Cx<T> mul_root(Cx<T> a)
+{
+    constexpr int ee = ((e % R) + R) % R;
+    constexpr int j = ee * (48 / R);  // angle in units of 2 pi / 48
+    if constexpr (j == 0) {
+        return a;
+    } else if constexpr (j == 12) {
+        return cmul_mi(a);  // -i
+    } else if constexpr (j == 24) {
+        return {-a.x, -a.y};
+    } else if constexpr (j == 36) {
+        return {-a.y, a.x};  // +i
+    } else if constexpr (j == 6 || j == 18 || j == 30 || j == 42) {
+        // |cos| = |sin| = 1/sqrt(2): a * (c - i s) with only the signs differing
+        constexpr T r = (T)0.7071067811865476;
+        constexpr T sc = cos48(j) > 0 ? (T)1 : (T)-1;
+        constexpr T ss = sin48(j) > 0 ? (T)1 : (T)-1;
+        return {(sc * a.x + ss * a.y) * r, (sc * a.y - ss * a.x) * r};
+    } else {
+        constexpr T c = (T)cos48(j);
+        constexpr T s = (T)sin48(j);
+        return {a.x * c + a.y * s, a.y * c - a.x * s};
+    }
+}
+
+// ---------------------------------------------------------------------
+// Small DFTs in registers: a[k] <- sum_r a[r] e^{-2 pi i r k / R}.
+// ---------------------------------------------------------------------
+template <typename T, int R>
+struct Dft;
+
+template <typename T>
+struct Dft<T, 2> {
+    static ISOFFT_HD void run(Cx<T> (&a)[2])
+    {
+        Cx<T> t = a[0];
+        a[0] = cadd(t, a[1]);
+        a[1] = csub(t, a[1]);
+    }
+};
+
+template <typename T>
+struct Dft<T, 3> {
+    static ISOFFT_HD void run(Cx<T> (&a)[3])
+    {
+        constexpr T s3 = (T)0.8660254037844387;  // sin(2 pi / 3)
+        Cx<T> sum = cadd(a[1], a[2]);
+        Cx<T> dif = csub(a[1], a[2]);
+        Cx<T> t = {a[0].x - (T)0.5 * sum.x, a[0].y - (T)0.5 * sum.y};
+        Cx<T> u = {dif.y * s3, -dif.x * s3};  // -i s3 (a1 - a2)
+        a[0] = cadd(a[0], sum);
+        a[1] = cadd(t, u);
+        a[2] = csub(t, u);
+    }
+};
+
+template <typename T>
+struct Dft<T, 4> {
+    static ISOFFT_HD void run(Cx<T> (&a)[4])
+    {
+        Cx<T> s02 = cadd(a[0], a[2]), d02 = csub(a[0], a[2]);
+        Cx<T> s13 = cadd(a[1], a[3]), d13 = cmul_mi(csub(a[1], a[3]));
+        a[0] = cadd(s02, s13);
+        a[2] = csub(s02, s13);
+        a[1] = cadd(d02, d13);
+        a[3] = csub(d02, d13);
+    }
+};
+
+template <typename T>
+struct Dft<T, 5> {
+    static ISOFFT_HD void run(Cx<T> (&a)[5])
+    {
+        constexpr T c1 = (T)0.30901699437494745, c2 = (T)-0.8090169943749473;
+        constexpr T s1 = (T)0.9510565162951535, s2 = (T)0.5877852522924732;
+        Cx<T> b1 = cadd(a[1], a[4]), b2 = cadd(a[2], a[3]);
+        Cx<T> d1 = csub(a[1], a[4]), d2 = csub(a[2], a[3]);
+        Cx<T> t1 = {a[0].x + c1 * b1.x + c2 * b2.x, a[0].y + c1 * b1.y + c2 * b2.y};
+        Cx<T> t2 = {a[0].x + c2 * b1.x + c1 * b2.x, a[0].y + c2 * b1.y + c1 * b2.y};
+        Cx<T> u1 = {s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y};
+        Cx<T> u2 = {s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y};
+        a[0] = cadd(a[0], cadd(b1, b2));
+        a[1] = cadd(t1, cmul_mi(u1));
+        a[4] = csub(t1, cmul_mi(u1));
+        a[2] = cadd(t2, cmul_mi(u2));
+        a[3] = csub(t2, cmul_mi(u2));
+    }
+};
+
+// Composite length R = R1 * R2 by one Cooley-Tukey step:
+// X[k1 + R1 k2] = sum_n2 W_R2^{n2 k2} W_R^{n2 k1} sum_n1 a[R2 n1 + n2] W_R1^{n1 k1}.
+template <typename T, int R1, int R2>
+struct DftCT {
+    static constexpr int R = R1 * R2;
+    template <int n2, int k1>
+    static ISOFFT_HD void twiddle(Cx<T> (&b)[R])
+    {
+        b[k1 * R2 + n2] = mul_root<T, R, n2 * k1>(b[k1 * R2 + n2]);
+        if constexpr (k1 + 1 < R1) twiddle<n2, k1 + 1>(b);
+    }
+    template <int n2>
+    static ISOFFT_HD void inner(const Cx<T> (&a)[R], Cx<T> (&b)[R])
+    {
+        Cx<T> t[R1];
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1) t[n1] = a[R2 * n1 + n2];
+        Dft<T, R1>::run(t);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) b[k1 * R2 + n2] = t[k1];
+        twiddle<n2, 0>(b);
+        if constexpr (n2 + 1 < R2) inner<n2 + 1>(a, b);
+    }
+    static ISOFFT_HD void run(Cx<T> (&a)[R])
+    {
+        Cx<T> b[R];
+        inner<0>(a, b);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) {
+            Cx<T> t[R2];
+#pragma unroll
+            for (int n2 = 0; n2 < R2; ++n2) t[n2] = b[k1 * R2 + n2];
+            Dft<T, R2>::run(t);
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2) a[k1 + R1 * k2] = t[k2];
+        }
+    }
+};
+
+template <typename T>
+struct Dft<T, 8> {
+    static ISOFFT_HD void run(Cx<T> (&a)[8]) { DftCT<T, 2, 4>::run(a); }
+};
+template <typename T>
+struct Dft<T, 6> {
+    static ISOFFT_HD void run(Cx<T> (&a)[6]) { DftCT<T, 2, 3>::run(a); }
+};
+template <typename T>
+struct Dft<T, 12> {
+    static ISOFFT_HD void run(Cx<T> (&a)[12]) { DftCT<T, 4, 3>::run(a); }
+};
+template <typename T>
+struct Dft<T, 16> {
+    static ISOFFT_HD void run(Cx<T> (&a)[16]) { DftCT<T, 4, 4>::run(a); }
+};
+
+// DFT of R inputs whose upper half a[R/2..R) is zero (first stage of a line
+// that is half zero padding): even bins are the length-R/2 DFT of a, odd bins
+// the length-R/2 DFT of a[r] W_R^r.
+template <typename T, int R>
+struct DftHalf {
+    template <int r>
+    static ISOFFT_HD void tw(Cx<T> (&o)[R / 2])
+    {
+        o[r] = mul_root<T, R, r>(o[r]);
+        if constexpr (r + 1 < R / 2) tw<r + 1>(o);
+    }
+    static ISOFFT_HD void run(Cx<T> (&a)[R])
+    {
+        Cx<T> e[R / 2], o[R / 2];
+#pragma unroll
+        for (int r = 0; r < R / 2; ++r) e[r] = o[r] = a[r];
+        tw<1>(o);
+        Dft<T, R / 2>::run(e);
+        Dft<T, R / 2>::run(o);
+#pragma unroll
+        for (int k = 0; k < R / 2; ++k) {
+            a[2 * k] = e[k];
+            a[2 * k + 1] = o[k];
+        }
+    }
+};
+template <typename T>
+struct DftHalf<T, 2> {
+    static ISOFFT_HD void run(Cx<T> (&a)[2]) { a[1] = a[0]; }
+};
+
+// ---------------------------------------------------------------------
+// Radix plans and stages
+// ---------------------------------------------------------------------
+template <int... Rs>
+struct Radices {};
+
+template <int L, int E, int NS, int R>
+struct StageGeom {
+    static constexpr int NT = L / E;  // threads per line
+    static constexpr int B = E / R;   // butterflies per thread
+    static_assert(E % R == 0, "radix must divide the points per thread");
+    static_assert(L % (NS * R) == 0, "radices must multiply to L");
+    // Stockham output position of butterfly q, output r, for thread t
+    static ISOFFT_HD int out_pos(int t, int q, int r)
+    {
+        const int j = t + q * NT;
+        return (j / NS) * NS * R + (j % NS) + r * NS;
+    }
+};
+
+// One Stockham stage in registers.  HALF: the stage's inputs at positions
+// >= L/2 are known zero (only legal as the first stage, NS == 1).
+template <typename T, int L, int E, int NS, int R, bool HALF>
+ISOFFT_HD void stage(Cx<T> (&v)[E], int t, const Cx<T> *__restrict__ tw)
+{
+    using G = StageGeom<L, E, NS, R>;
+#pragma unroll
+    for (int q = 0; q < G::B; ++q) {
+        Cx<T> a[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) a[r] = v[q + r * G::B];
+        if constexpr (NS > 1) {
+            const int k = (t + q * G::NT) % NS;
+            constexpr int step = L / (NS * R);
+#pragma unroll
+            for (int r = 1; r < R; ++r) a[r] = cmul(a[r], tw[r * k * step]);
+        }
+        if constexpr (HALF) {
+            static_assert(NS == 1, "pruned butterflies only in the first stage");
+            DftHalf<T, R>::run(a);
+        } else {
+            Dft<T, R>::run(a);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[q + r * G::B] = a[r];
+    }
+}
+
+// Runs the stages of a Radices<...> plan.  Xch is an exchanger providing
+//   template <int NS, int R> void exchange(Cx<T>(&)[E], int t)
+// that writes register (q, r) to StageGeom::out_pos(t, q, r) and reads back
+// positions t + m * NT.
+template <typename T, int L, int E, int NS, bool HALF, typename Xch, int R, int... Rest>
+ISOFFT_HD void run_stages_impl(Cx<T> (&v)[E], int t, const Cx<T> *__restrict__ tw,
+                                                Xch &xch)
+{
+    stage<T, L, E, NS, R, HALF>(v, t, tw);
+    if constexpr (sizeof...(Rest) > 0) {
+        xch.template exchange<NS, R>(v, t);
+        run_stages_impl<T, L, E, NS * R, false, Xch, Rest...>(v, t, tw, xch);
+    }
+}
+
+template <typename T, int L, int E, bool HALF, typename Xch, int... Rs>
+ISOFFT_HD void run_stages(Cx<T> (&v)[E], int t, const Cx<T> *__restrict__ tw, Xch &xch,
+                                           Radices<Rs...>)
+{
+    run_stages_impl<T, L, E, 1, HALF, Xch, Rs...>(v, t, tw, xch);
+}
+
+// Per-length configuration: points per thread E and the radix sequence.
+// FP32 lines of 512+ points keep 16-24 points per thread (fewer threads per
+// line, fewer exchanges); FP64 keeps at most 12 to stay clear of spills.
+template <int L>
+struct Shape32;
+template <int L>
+struct Shape64 : Shape32<L> {};
+#define ISOFFT_SHAPE(S, L_, E_, ...)                       \
+    template <>                                           \
+    struct S<L_> {                                        \
+        static constexpr int E = E_;                      \
+        using Rad = Radices<__VA_ARGS__>;                 \
+    };
+ISOFFT_SHAPE(Shape32, 16, 8, 8, 2)
+ISOFFT_SHAPE(Shape32, 24, 12, 12, 2)
+ISOFFT_SHAPE(Shape32, 32, 8, 8, 4)
+ISOFFT_SHAPE(Shape32, 48, 12, 12, 4)
+ISOFFT_SHAPE(Shape32, 64, 8, 8, 8)
+ISOFFT_SHAPE(Shape32, 96, 12, 12, 4, 2)
+ISOFFT_SHAPE(Shape32, 128, 8, 8, 8, 2)
+ISOFFT_SHAPE(Shape32, 192, 12, 12, 4, 4)
+ISOFFT_SHAPE(Shape32, 256, 8, 8, 8, 4)
+ISOFFT_SHAPE(Shape32, 384, 12, 12, 4, 4, 2)
+ISOFFT_SHAPE(Shape32, 512, 16, 8, 8, 8)
+ISOFFT_SHAPE(Shape32, 768, 24, 12, 8, 8)
+ISOFFT_SHAPE(Shape32, 1024, 16, 16, 8, 8)
+ISOFFT_SHAPE(Shape64, 512, 8, 8, 8, 8)
+ISOFFT_SHAPE(Shape64, 768, 12, 12, 4, 4, 4)
+ISOFFT_SHAPE(Shape64, 1024, 8, 8, 8, 8, 2)
+#undef ISOFFT_SHAPE
+
+template <typename T, int L>
+struct Shape;
+template <int L>
+struct Shape<float, L> : Shape32<L> {};
+template <int L>
+struct Shape<double, L> : Shape64<L> {};
+
+}  // namespace isofft

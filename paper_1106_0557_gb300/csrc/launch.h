@@ -1,0 +1,48 @@
+// launch.h -- host-side launchers of the device passes (internal to the
+// library; the public surface is include/isofft.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace isofft {
+
+// Doubled-mesh lengths the kernels are instantiated for (any M >= 2N - 1
+// gives the same cropped result, so a plan rounds 2N up to the next one).
+constexpr int kSupportedM[] = {32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024};
+constexpr int kMaxM = 1024;
+
+// Counts every kernel launch the library makes (ipf_launch_count).
+void count_launch();
+
+// All pointers are device pointers of the current device; complex buffers
+// are interleaved (re, im) of the real type.
+template <typename T>
+cudaError_t launch_x_forward(int L, const T *src, void *W, const void *tw, const void *rtw, int Nx,
+                             int Ny, int My, int64_t nrows, cudaStream_t st);
+template <typename T>
+cudaError_t launch_x_inverse(int L, const void *W, T *phi, const void *tw, const void *rtw, int Nx,
+                             int Ny, int My, int64_t nrows, cudaStream_t st);
+template <typename T>
+cudaError_t launch_y_forward(int L, void *W, const void *tw, int Ny, int Kx, int Nz, cudaStream_t st);
+template <typename T>
+cudaError_t launch_y_inverse(int L, void *W, const void *tw, int Ny, int Kx, int Nz, cudaStream_t st);
+template <typename T>
+cudaError_t launch_z_convolve(int L, void *W, const void *tw, const T *G, const T *Gs, T gscale, int Nz,
+                              int My, int Kx, cudaStream_t st);
+
+// Green's spectrum (FP64 build).  M = doubled mesh, hn = widths divided by
+// their minimum.  Writes G [My/2+1][Mz/2+1][Mx/2] and Gs [My/2+1][Mz/2+1] of
+// type T, pre-divided by 2 Mx My Mz (see passes.cuh).  Allocates and frees
+// its FP64 scratch; synchronises `st` before returning.
+template <typename T>
+cudaError_t build_green_spectrum(const int64_t M[3], const double hn[3], T *G, T *Gs, cudaStream_t st);
+
+// Device bytes of the FP64 scratch build_green_spectrum needs for mesh M.
+size_t green_build_scratch_bytes(const int64_t M[3]);
+
+// e^{-2 pi i k / n} for 0 <= k < count, by exact reduction to the first
+// octant (host, libm in double).
+void host_roots(int64_t n, int64_t count, double *re, double *im);
+
+}  // namespace isofft

@@ -1,0 +1,173 @@
+// passes_inst.cu -- instantiates and launches the pass kernels for one real
+// type and one group of passes.  The build compiles this file several times:
+//   -DISOFFT_REAL=float|double   the arithmetic type
+//   -DISOFFT_GROUP=1|2|3         1: x passes (K1, K5), 2: y passes (K2, K4),
+//                                3: z pass (K3)
+// so that the instantiations compile in parallel.
+#include <atomic>
+
+#include "launch.h"
+#include "passes.cuh"
+
+#ifndef ISOFFT_REAL
+#error "define ISOFFT_REAL"
+#endif
+#ifndef ISOFFT_GROUP
+#error "define ISOFFT_GROUP"
+#endif
+
+namespace isofft {
+
+using Real = ISOFFT_REAL;
+
+// Raise a kernel's dynamic shared memory limit once per device.
+template <typename F>
+static cudaError_t ensure_smem(F *func, size_t bytes, std::atomic<uint64_t> &done)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
+
+#define ISOFFT_ROW_LENGTHS(X) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512)
+#define ISOFFT_COL_LENGTHS(X) \
+    X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768) X(1024)
+
+#if ISOFFT_GROUP == 1
+template <typename T, int L>
+static cudaError_t run_x_forward(const T *src, void *W, const void *tw, const void *rtw, int Nx, int Ny,
+                                 int My, int64_t nrows, cudaStream_t st)
+{
+    using C = RowCfg<T, L>;
+    static std::atomic<uint64_t> done{0};
+    cudaError_t e = ensure_smem(k_x_forward<T, L>, C::SMEM, done);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)((nrows + C::NL - 1) / C::NL);
+    k_x_forward<T, L><<<grid, C::THREADS, C::SMEM, st>>>(src, (Cx<T> *)W, (const Cx<T> *)tw,
+                                                        (const Cx<T> *)rtw, Nx, Ny, My, nrows);
+    count_launch();
+    return cudaGetLastError();
+}
+template <typename T, int L>
+static cudaError_t run_x_inverse(const void *W, T *phi, const void *tw, const void *rtw, int Nx, int Ny,
+                                 int My, int64_t nrows, cudaStream_t st)
+{
+    using C = RowCfg<T, L>;
+    static std::atomic<uint64_t> done{0};
+    cudaError_t e = ensure_smem(k_x_inverse<T, L>, C::SMEM, done);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)((nrows + C::NL - 1) / C::NL);
+    k_x_inverse<T, L><<<grid, C::THREADS, C::SMEM, st>>>((const Cx<T> *)W, phi, (const Cx<T> *)tw,
+                                                        (const Cx<T> *)rtw, Nx, Ny, My, nrows);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <typename R_>
+cudaError_t launch_x_forward(int L, const R_ *src, void *W, const void *tw, const void *rtw, int Nx,
+                                 int Ny, int My, int64_t nrows, cudaStream_t st)
+{
+    switch (L) {
+#define X_(n) \
+    case n: return run_x_forward<R_, n>(src, W, tw, rtw, Nx, Ny, My, nrows, st);
+        ISOFFT_ROW_LENGTHS(X_)
+#undef X_
+    default: return cudaErrorInvalidValue;
+    }
+}
+template <typename R_>
+cudaError_t launch_x_inverse(int L, const void *W, R_ *phi, const void *tw, const void *rtw, int Nx,
+                                 int Ny, int My, int64_t nrows, cudaStream_t st)
+{
+    switch (L) {
+#define X_(n) \
+    case n: return run_x_inverse<R_, n>(W, phi, tw, rtw, Nx, Ny, My, nrows, st);
+        ISOFFT_ROW_LENGTHS(X_)
+#undef X_
+    default: return cudaErrorInvalidValue;
+    }
+}
+template cudaError_t launch_x_forward<Real>(int, const Real *, void *, const void *, const void *, int, int,
+                                            int, int64_t, cudaStream_t);
+template cudaError_t launch_x_inverse<Real>(int, const void *, Real *, const void *, const void *, int, int,
+                                            int, int64_t, cudaStream_t);
+#endif
+
+#if ISOFFT_GROUP == 2
+template <typename T, int L, bool FWD>
+static cudaError_t run_y(void *W, const void *tw, int Ny, int Kx, int Nz, cudaStream_t st)
+{
+    using C = ColCfg<T, L>;
+    static std::atomic<uint64_t> done{0};
+    auto *k = FWD ? k_y_forward<T, L> : k_y_inverse<T, L>;
+    cudaError_t e = ensure_smem(k, C::SMEM, done);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((Kx + C::TX - 1) / C::TX), (unsigned)Nz);
+    k<<<grid, C::THREADS, C::SMEM, st>>>((Cx<T> *)W, (const Cx<T> *)tw, Ny, Kx);
+    count_launch();
+    return cudaGetLastError();
+}
+template <typename R_>
+cudaError_t launch_y_forward(int L, void *W, const void *tw, int Ny, int Kx, int Nz, cudaStream_t st)
+{
+    switch (L) {
+#define X_(n) \
+    case n: return run_y<R_, n, true>(W, tw, Ny, Kx, Nz, st);
+        ISOFFT_COL_LENGTHS(X_)
+#undef X_
+    default: return cudaErrorInvalidValue;
+    }
+}
+template <typename R_>
+cudaError_t launch_y_inverse(int L, void *W, const void *tw, int Ny, int Kx, int Nz, cudaStream_t st)
+{
+    switch (L) {
+#define X_(n) \
+    case n: return run_y<R_, n, false>(W, tw, Ny, Kx, Nz, st);
+        ISOFFT_COL_LENGTHS(X_)
+#undef X_
+    default: return cudaErrorInvalidValue;
+    }
+}
+template cudaError_t launch_y_forward<Real>(int, void *, const void *, int, int, int, cudaStream_t);
+template cudaError_t launch_y_inverse<Real>(int, void *, const void *, int, int, int, cudaStream_t);
+#endif
+
+#if ISOFFT_GROUP == 3
+template <typename T, int L>
+static cudaError_t run_z(void *W, const void *tw, const T *G, const T *Gs, T gscale, int Nz, int My, int Kx,
+                         cudaStream_t st)
+{
+    using C = ZCfg<T, L>;
+    static std::atomic<uint64_t> done{0};
+    cudaError_t e = ensure_smem(k_z_convolve<T, L>, C::SMEM, done);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((Kx + C::TX - 1) / C::TX), (unsigned)(My / 2));
+    k_z_convolve<T, L><<<grid, C::THREADS, C::SMEM, st>>>((Cx<T> *)W, (const Cx<T> *)tw, G, Gs, gscale, Nz,
+                                                         My, Kx);
+    count_launch();
+    return cudaGetLastError();
+}
+template <typename R_>
+cudaError_t launch_z_convolve(int L, void *W, const void *tw, const R_ *G, const R_ *Gs, R_ gscale,
+                                  int Nz, int My, int Kx, cudaStream_t st)
+{
+    switch (L) {
+#define X_(n) \
+    case n: return run_z<R_, n>(W, tw, G, Gs, gscale, Nz, My, Kx, st);
+        ISOFFT_COL_LENGTHS(X_)
+#undef X_
+    default: return cudaErrorInvalidValue;
+    }
+}
+template cudaError_t launch_z_convolve<Real>(int, void *, const void *, const Real *, const Real *, Real, int,
+                                             int, int, cudaStream_t);
+#endif
+
+}  // namespace isofft

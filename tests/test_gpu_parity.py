@@ -1,0 +1,183 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (normwise max relative error, max|phi - ref| / max|ref|):
+FP64 path 1e-12, FP32 path 1e-5; the FP32 source is cast to FP64 before the
+oracle runs, so input quantisation is not counted.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1106_0557_gb300 import native, sources
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f32": 1e-5, "f64": 1e-12}
+NP = {"f32": np.float32, "f64": np.float64}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    native.lib()
+
+
+def gpu_solve(src, h, dtype, flags=0):
+    from paper_1106_0557_gb300 import Plan
+    s = np.ascontiguousarray(src, dtype=NP[dtype])
+    nz, ny, nx = s.shape
+    with Plan((nx, ny, nz), h, dtype, flags=flags) as p:
+        d = torch.from_numpy(s).cuda()
+        out = p.solve(d)
+        torch.cuda.synchronize()
+        return out.cpu().numpy().astype(np.float64), s.astype(np.float64)
+
+
+def rand_src(N, seed, frac=0.6):
+    g = np.random.default_rng(seed)
+    s = g.uniform(0.0, 1.0, (N[2], N[1], N[0]))
+    s[g.uniform(size=s.shape) > frac] = 0.0
+    return s
+
+
+SHAPES = [
+    ((32, 32, 32), (1 / 32, 1 / 32, 1 / 32)),
+    ((1, 1, 1), (1.0, 1.0, 1.0)),
+    ((13, 17, 11), (1.0, 1.0, 1.0)),
+    ((5, 40, 3), (0.5, 0.25, 1.0)),
+    ((48, 24, 16), (1.0, 1.0, 2.0)),
+    ((33, 64, 20), (0.3, 0.2, 0.5)),
+    ((64, 48, 96), (1.0, 1.0, 1.0)),
+    ((100, 70, 30), (0.01, 0.01, 0.02)),
+    ((7, 130, 9), (1.0, 1.0, 1.0)),
+]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("N,h", SHAPES)
+def test_random_sources_match_oracle(N, h, dtype):
+    src = rand_src(N, seed=sum(N))
+    phi, s64 = gpu_solve(src, h, dtype)
+    ref = oracle.solve(s64, h)
+    assert oracle.max_rel_error(phi, ref) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_sphere_32_matches_oracle_and_direct_sum(dtype):
+    w = sources.single_sphere(32)
+    phi, s64 = gpu_solve(w.source(), w.h, dtype)
+    assert oracle.max_rel_error(phi, oracle.solve(s64, w.h)) <= TOL[dtype]
+    # 16^3 sub-case against the definition itself
+    w16 = sources.single_sphere(16)
+    phi16, s16 = gpu_solve(w16.source(), w16.h, dtype)
+    assert oracle.max_rel_error(phi16, oracle.direct_sum(s16, w16.h)) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("N,h", [((256, 256, 256), (1.0, 1.0, 1.0)), ((100, 60, 130), (0.5, 0.25, 1.0))])
+def test_impulse_response_is_green_table(N, h, dtype):
+    """A unit source at a corner gives the Green's function itself at every
+    cell (closed form, Eq. 6 / Eq. 9), at full size with no FFT oracle."""
+    Nx, Ny, Nz = N
+    M = tuple(2 * n for n in N)
+    T = oracle.green_table(M, h)
+    for corner in [(0, 0, 0), (Nx - 1, Ny - 1, Nz - 1)]:
+        src = np.zeros((Nz, Ny, Nx))
+        src[corner[2], corner[1], corner[0]] = 1.0
+        phi, _ = gpu_solve(src, h, dtype)
+        if corner == (0, 0, 0):
+            want = T[:Nz, :Ny, :Nx]
+        else:
+            want = T[:Nz, :Ny, :Nx][::-1, ::-1, ::-1]
+        assert np.max(np.abs(phi - want)) / np.max(np.abs(want)) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_multisphere_256_sampled_direct_sum(dtype):
+    """The 256^3 multi-sphere workload: sampled cells against route 1 (the
+    definition, summed over all 16.7 M source cells per sample)."""
+    w = sources.multi_sphere(256, seed=0)
+    phi, s64 = gpu_solve(w.source(), w.h, dtype)
+    g = np.random.default_rng(5)
+    cells = np.concatenate([g.integers(0, s64.size, 24), [0, s64.size - 1, s64.size // 2]])
+    ref = oracle.direct_points(s64, w.h, cells)
+    scale = np.max(np.abs(phi))
+    assert np.max(np.abs(phi.ravel()[cells] - ref)) / scale <= TOL[dtype]
+
+
+def test_linearity_translation_on_gpu():
+    N, h = (96, 80, 64), (1.0, 1.0, 1.0)
+    a, b = rand_src(N, 1), rand_src(N, 2)
+    pa, _ = gpu_solve(a, h, "f64")
+    pb, _ = gpu_solve(b, h, "f64")
+    pab, _ = gpu_solve(2.0 * a - 0.5 * b, h, "f64")
+    assert oracle.max_rel_error(pab, 2.0 * pa - 0.5 * pb) < 1e-12
+    src = np.zeros((64, 80, 96))
+    src[10:20, 5:30, 3:40] = rand_src((37, 25, 10), 3, 1.0)
+    moved = np.roll(src, (7, 11, 13), axis=(0, 1, 2))
+    p0, _ = gpu_solve(src, h, "f64")
+    p1, _ = gpu_solve(moved, h, "f64")
+    assert np.max(np.abs(p1[7:, 11:, 13:] - p0[:-7, :-11, :-13])) < 1e-12 * np.max(np.abs(p0))
+
+
+def test_in_place_host_and_events():
+    from paper_1106_0557_gb300 import Plan
+    N, h = (40, 36, 24), (1.0, 0.5, 1.0)
+    src = rand_src(N, 9).astype(np.float32)
+    with Plan(N, h, "f32", flags=native.IPF_FLAG_PASS_EVENTS) as p:
+        d = torch.from_numpy(src).cuda()
+        ref = p.solve(d).clone()
+        before = native.ipf_launch_count()
+        inplace = d.clone()
+        p.solve(inplace, out=inplace)
+        torch.cuda.synchronize()
+        assert native.ipf_launch_count() - before == 5
+        assert torch.equal(inplace, ref)
+        times = p.pass_times()
+        assert len(times) == 5 and all(t > 0 for t in times)
+        host = p.solve_host(src)
+        assert np.array_equal(host, ref.cpu().numpy())
+
+
+def test_batch_matches_single_solves():
+    from paper_1106_0557_gb300 import Plan, submit_batch
+    wl = sources.ragged_batch(count=6)
+    plans, srcs, outs, singles = [], [], [], []
+    for w in wl:
+        p = Plan(w.N, w.h, "f32")
+        s = torch.from_numpy(w.source(np.float32)).cuda()
+        singles.append(p.solve(s).clone())
+        plans.append(p)
+        srcs.append(s)
+        outs.append(torch.empty_like(s))
+    submit_batch(plans, srcs, outs)
+    torch.cuda.synchronize()
+    for w, s, o, r in zip(wl, srcs, outs, singles):
+        assert torch.equal(o, r)
+        ref = oracle.solve(s.cpu().numpy().astype(np.float64), w.h)
+        assert oracle.max_rel_error(o.cpu().numpy(), ref) <= TOL["f32"]
+    for p in plans:
+        p.close()
+
+
+def test_spectrum_cache_shared_across_widths():
+    """Plans whose widths differ by a common factor s share one cached
+    spectrum; their potentials differ by s^2 (G scales as h^2)."""
+    from paper_1106_0557_gb300 import Plan
+    N = (24, 20, 16)
+    src = rand_src(N, 4)
+    native.ipf_greens_cache_trim(0)
+    with Plan(N, (1.0, 2.0, 1.5), "f64") as p1:
+        b1 = native.ipf_greens_cache_bytes()
+        with Plan(N, (0.1, 0.2, 0.15), "f64") as p2:
+            assert native.ipf_greens_cache_bytes() == b1
+            d = torch.from_numpy(src).cuda()
+            r1 = p1.solve(d).cpu().numpy()
+            r2 = p2.solve(d).cpu().numpy()
+    assert oracle.max_rel_error(r2, 0.01 * r1) < 1e-13
+    native.ipf_greens_cache_trim(0)
+    assert native.ipf_greens_cache_bytes() == 0
