@@ -85,9 +85,7 @@ static uint64_t g_clock = 0;
 
 static size_t spectrum_bytes(const int64_t M[3], int dtype)
 {
-    const size_t es = dtype == IPF_F32 ? 4 : 8;
-    const size_t Y = M[1] / 2 + 1, Z = M[2] / 2 + 1, K = M[0] / 2;
-    return es * Y * Z * (K + 1);
+    return dtype == IPF_F32 ? 4 * spectrum_elems<float>(M) : 8 * spectrum_elems<double>(M);
 }
 
 static void free_entry(SpecEntry &e)
@@ -151,12 +149,17 @@ int validate(const int64_t n[3], const double h[3], int dtype)
     return IPF_OK;
 }
 
+// Widths divided by their minimum, rounded to a multiple of 2^-44 so that
+// width sets that differ only by a common factor (0.1, 0.2, 0.15 and 1, 2,
+// 1.5) share one cached spectrum; the rounding moves a ratio by at most
+// 3e-14 relative, far below the FP64 tolerance.
 void normalized_widths(const double h[3], double hn[3], double *hmin)
 {
     double m = h[0];
     if (h[1] < m) m = h[1];
     if (h[2] < m) m = h[2];
-    for (int a = 0; a < 3; ++a) hn[a] = h[a] / m;
+    const double q = 17592186044416.0;  // 2^44
+    for (int a = 0; a < 3; ++a) hn[a] = nearbyint(h[a] / m * q) / q;
     *hmin = m;
 }
 
@@ -206,8 +209,8 @@ int acquire_spectrum(ipf_plan_s *p, cudaStream_t st)
         cudaError_t ce = cudaMalloc(&e.G, e.bytes);
         if (ce != cudaSuccess) return cuda_status(ce);
         const size_t es = elem_size(p->dtype);
-        const size_t Y = p->M[1] / 2 + 1, Z = p->M[2] / 2 + 1, K = p->M[0] / 2;
-        e.Gs = (char *)e.G + es * Y * Z * K;
+        const size_t Y = p->M[1] / 2 + 1, Z = p->M[2] / 2 + 1;
+        e.Gs = (char *)e.G + e.bytes - es * Y * Z;
         logf(IPF_CONSOLE_INFO_1, p->verbosity, "building Green's spectrum for mesh %lldx%lldx%lld (%s)",
              (long long)p->M[0], (long long)p->M[1], (long long)p->M[2], p->dtype == IPF_F32 ? "f32" : "f64");
         if (p->dtype == IPF_F32)

@@ -316,8 +316,9 @@ ISOFFT_HD void run_stages(Cx<T> (&v)[E], int t, const Cx<T> *__restrict__ tw, Xc
 }
 
 // Per-length configuration: points per thread E and the radix sequence.
-// FP32 lines of 512+ points keep 16-24 points per thread (fewer threads per
-// line, fewer exchanges); FP64 keeps at most 12 to stay clear of spills.
+// Eight (or twelve for lengths with a factor 3) points per thread keep the
+// register footprint small enough for a next-tile prefetch; 1024-point
+// lines take sixteen so a line needs no more than 64 threads.
 template <int L>
 struct Shape32;
 template <int L>
@@ -338,11 +339,9 @@ ISOFFT_SHAPE(Shape32, 128, 8, 8, 8, 2)
 ISOFFT_SHAPE(Shape32, 192, 12, 12, 4, 4)
 ISOFFT_SHAPE(Shape32, 256, 8, 8, 8, 4)
 ISOFFT_SHAPE(Shape32, 384, 12, 12, 4, 4, 2)
-ISOFFT_SHAPE(Shape32, 512, 16, 8, 8, 8)
-ISOFFT_SHAPE(Shape32, 768, 24, 12, 8, 8)
+ISOFFT_SHAPE(Shape32, 512, 8, 8, 8, 8)
+ISOFFT_SHAPE(Shape32, 768, 12, 12, 4, 4, 4)
 ISOFFT_SHAPE(Shape32, 1024, 16, 16, 8, 8)
-ISOFFT_SHAPE(Shape64, 512, 8, 8, 8, 8)
-ISOFFT_SHAPE(Shape64, 768, 12, 12, 4, 4, 4)
 ISOFFT_SHAPE(Shape64, 1024, 8, 8, 8, 8, 2)
 #undef ISOFFT_SHAPE
 
@@ -352,5 +351,16 @@ template <int L>
 struct Shape<float, L> : Shape32<L> {};
 template <int L>
 struct Shape<double, L> : Shape64<L> {};
+
+// The z pass holds two lines groups per tile and stages its prefetches in
+// shared memory; for 512-point FP32 lines it runs 16 points per thread on
+// 512 threads so the transform never competes with a 64-register cap.
+template <typename T, int L>
+struct ZShape : Shape<T, L> {};
+template <>
+struct ZShape<float, 512> {
+    static constexpr int E = 16;
+    using Rad = Radices<8, 8, 8>;
+};
 
 }  // namespace isofft

@@ -55,20 +55,26 @@ static __global__ void k_cos_axis(const double *__restrict__ in, double *__restr
     }
 }
 
-// oct [Z][Y][X] (X = Mx/2 + 1) -> G [Y][Z][Kx], Gs [Y][Z] of type T.
+// oct [Z][Y][X] (X = Mx/2 + 1) -> G in the z pass's tiled layout
+// [Y][ntx][Z][tx] (kx = xt * tx + c, zero past Kx = Mx/2) and Gs [Y][Z], of
+// type T; column kx = 0 packs the kx = 0 and kx = Mx/2 planes.
 template <typename T>
 static __global__ void k_pack(const double *__restrict__ oct, T *__restrict__ G, T *__restrict__ Gs, int X,
-                              int Y, int Z, double scale)
+                              int Y, int Z, int tx, int ntx, double scale)
 {
     const int Kx = X - 1;
-    const int64_t tot = (int64_t)Y * Z * Kx;
+    const int64_t tot = (int64_t)Y * ntx * Z * tx;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int kx = (int)(i % Kx);
-        const int64_t kz = (i / Kx) % Z;
-        const int64_t ky = i / ((int64_t)Kx * Z);
+        const int c = (int)(i % tx);
+        const int64_t kz = (i / tx) % Z;
+        const int xt = (int)((i / ((int64_t)tx * Z)) % ntx);
+        const int64_t ky = i / ((int64_t)tx * Z * ntx);
+        const int kx = xt * tx + c;
         const double *o = oct + (kz * Y + ky) * X;
-        if (kx == 0) {
+        if (kx >= Kx) {
+            G[i] = (T)0;
+        } else if (kx == 0) {
             const double g0 = o[0], gn = o[Kx];
             G[i] = (T)(0.5 * (g0 + gn) * scale);
             Gs[ky * Z + kz] = (T)(0.5 * (g0 - gn) * scale);
@@ -77,6 +83,17 @@ static __global__ void k_pack(const double *__restrict__ oct, T *__restrict__ G,
         }
     }
 }
+
+template <typename T>
+size_t spectrum_elems(const int64_t M[3])
+{
+    const int tx = z_tile_for<T>((int)M[2]);
+    const size_t Y = M[1] / 2 + 1, Z = M[2] / 2 + 1, Kx = M[0] / 2;
+    const size_t ntx = (Kx + tx - 1) / tx;
+    return Y * ntx * Z * tx + Y * Z;
+}
+template size_t spectrum_elems<float>(const int64_t *);
+template size_t spectrum_elems<double>(const int64_t *);
 
 void host_roots(int64_t n, int64_t count, double *re, double *im)
 {
@@ -173,7 +190,9 @@ cudaError_t build_green_spectrum(const int64_t M[3], const double hn[3], T *G, T
         k_cos_axis<<<grid_for(n), 256, 0, st>>>(o0, o1, ct + off[2], 1, Z, (int64_t)Y * X);
         count_launch();
         const double scale = 1.0 / (2.0 * (double)M[0] * (double)M[1] * (double)M[2]);
-        k_pack<T><<<grid_for(n), 256, 0, st>>>(o1, G, Gs, X, Y, Z, scale);
+        const int tx = z_tile_for<T>((int)M[2]);
+        const int ntx = (int)((M[0] / 2 + tx - 1) / tx);
+        k_pack<T><<<grid_for((int64_t)Y * ntx * Z * tx), 256, 0, st>>>(o1, G, Gs, X, Y, Z, tx, ntx, scale);
         count_launch();
         e = cudaGetLastError();
     }

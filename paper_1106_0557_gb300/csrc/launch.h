@@ -31,9 +31,19 @@ template <typename T>
 cudaError_t launch_z_convolve(int L, void *W, const void *tw, const T *G, const T *Gs, T gscale, int Nz,
                               int My, int Kx, cudaStream_t st);
 
+// Width (kx columns per tile) of the z pass for line length L; the cached
+// Green's spectrum is stored in tiles of this width (0: unsupported L).
+template <typename T>
+int z_tile_for(int L);
+
+// Device bytes of the cached Green's spectrum of a doubled mesh M.
+template <typename T>
+size_t spectrum_elems(const int64_t M[3]);
+
 // Green's spectrum (FP64 build).  M = doubled mesh, hn = widths divided by
 // their minimum.  Writes G [My/2+1][Mz/2+1][Mx/2] and Gs [My/2+1][Mz/2+1] of
-// type T, pre-divided by 2 Mx My Mz (see passes.cuh).  Allocates and frees
+// type T in the z pass's tiled layout, pre-divided by 2 Mx My Mz (see
+// passes.cuh).  Allocates and frees
 // its FP64 scratch; synchronises `st` before returning.
 template <typename T>
 cudaError_t build_green_spectrum(const int64_t M[3], const double hn[3], T *G, T *Gs, cudaStream_t st);

@@ -7,8 +7,9 @@
 //   W        : complex [Nz][My][Kx], Kx = Mx / 2, the plan's workspace.  The
 //              z padding is never stored: the z pass reads z < Nz, treats the
 //              rest of its line as zero, and writes back only z < Nz.
-//   G        : real [My/2 + 1][Mz/2 + 1][Kx], the transform of the Eq. 9
-//              table on the even octant (it is real and even in every axis),
+//   G        : real, the transform of the Eq. 9 table on the even octant (it
+//              is real and even in every axis) in the tiled order of
+//              ZSpecLayout, [My/2 + 1][kx tiles][Mz/2 + 1][tile width],
 //              pre-divided by 2 Mx My Mz (the factor 2 undoes the packed x
 //              spectra, which carry 2X); column kx = 0 holds (G0 + GN) / 2,
 //   Gs       : real [My/2 + 1][Mz/2 + 1], (G0 - GN) / 2, where G0 and GN are
@@ -31,12 +32,42 @@
 
 namespace isofft {
 
+// Asynchronous global -> shared copies (cp.async): BYTES = 4, 8 or 16;
+// when `valid` is false nothing is read and the slot is zero-filled.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem_dst, const void *gsrc, bool valid)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    const int n = valid ? BYTES : 0;
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gsrc), "r"(n) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(s), "l"(gsrc), "n"(BYTES), "r"(n)
+                     : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 // Shared-memory exchange for column passes: lines are the COLS columns of a
-// tile, stored [position][column] so a warp touches whole 128-byte rows.
-template <typename T, int L, int E, int COLS>
+// tile, stored [position][column].  A warp covers 32 / COLS' positions; when
+// a position row is only 64 bytes (SWZ), rows are swizzled by position bits
+// 3 and 4 so that the strided first-stage writes (position stride 8 or 16)
+// still alternate between the two halves of a 128-byte bank row.
+template <typename T, int L, int E, int COLS, bool SWZ = false>
 struct ColXch {
     Cx<T> *s;
     int c;
+    static __device__ __forceinline__ int row(int p)
+    {
+        if constexpr (SWZ)
+            return p ^ (((p >> 3) ^ (p >> 4)) & 1);
+        else
+            return p;
+    }
     template <int NS, int R>
     __device__ __forceinline__ void exchange(Cx<T> (&v)[E], int t)
     {
@@ -44,10 +75,10 @@ struct ColXch {
 #pragma unroll
         for (int q = 0; q < G::B; ++q)
 #pragma unroll
-            for (int r = 0; r < R; ++r) s[G::out_pos(t, q, r) * COLS + c] = v[q + r * G::B];
+            for (int r = 0; r < R; ++r) s[row(G::out_pos(t, q, r)) * COLS + c] = v[q + r * G::B];
         __syncthreads();
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = s[(t + m * G::NT) * COLS + c];
+        for (int m = 0; m < E; ++m) v[m] = s[row(t + m * G::NT) * COLS + c];
         __syncthreads();
     }
 };
@@ -87,30 +118,60 @@ struct RowCfg {
     static constexpr size_t SMEM = (size_t)NL * RowPad<L>::LP * sizeof(Cx<T>);
 };
 
-// Column tile width: 128 bytes of complex per row (16 FP32 or 8 FP64 lines).
+// Column tiles of the y passes: up to 128 bytes of complex per row and at
+// most 512 threads, so two tiles are resident per SM and one tile's global
+// loads overlap the other's butterflies.
 template <typename T, int L>
 struct ColCfg {
     static constexpr int E = Shape<T, L>::E;
     static constexpr int NT = L / E;
-    static constexpr int TX = 128 / (int)sizeof(Cx<T>);
+    static constexpr int TX0 = 128 / (int)sizeof(Cx<T>);
+    static constexpr int TX = TX0 * NT <= 512 ? TX0 : (512 / NT >= 1 ? 512 / NT : 1);
     static constexpr int THREADS = TX * NT;
     static constexpr size_t SMEM = (size_t)L * TX * sizeof(Cx<T>);
     static_assert(THREADS <= 1024, "column tile too large");
 };
 
-// The z pass processes two lines groups (ky and My - ky) per tile.
+// z pass tiles: TX columns of the two lines ky and My - ky (2 TX lines),
+// processed by a persistent CTA.  While it transforms one tile, cp.async
+// copies the next tile's non-zero half (z < Mz/2) and the spectrum values
+// into shared staging slots, so loads never wait in registers.  FP64 tiles
+// are narrower: FP64 arithmetic, not memory, bounds that path.
+constexpr size_t z_smem(int tx, int nt, int L, int e, int rb)
+{
+    return (size_t)L * 2 * tx * 2 * rb       // exchange buffer
+           + (size_t)2 * tx * nt * (e / 2) * 2 * rb  // staged input
+           + (size_t)2 * tx * nt * e * rb;     // staged spectrum
+}
+constexpr int z_tile_width(int rb, int nt, int L, int e)
+{
+    int tx = rb == 4 ? 8 : 4;
+    while (tx > 1 && (2 * tx * nt > (e > 8 ? 512 : 1024) || z_smem(tx, nt, L, e, rb) > 200 * 1024)) tx /= 2;
+    return tx;
+}
+
 template <typename T, int L>
 struct ZCfg {
-    static constexpr int E = Shape<T, L>::E;
+    static constexpr int E = ZShape<T, L>::E;
     static constexpr int NT = L / E;
-    static constexpr int TX0 = 128 / (int)sizeof(Cx<T>);
-    static constexpr int TX = (2 * TX0 * NT <= 1024 && (size_t)L * 2 * TX0 * sizeof(Cx<T>) <= 200 * 1024)
-                                  ? TX0
-                                  : TX0 / 2;
+    static constexpr int TX = z_tile_width((int)sizeof(T), NT, L, E);
     static constexpr int COLS = 2 * TX;
     static constexpr int THREADS = COLS * NT;
-    static constexpr size_t SMEM = (size_t)L * COLS * sizeof(Cx<T>);
+    static constexpr size_t XCH = (size_t)L * COLS * sizeof(Cx<T>);
+    static constexpr size_t STAGE_IN = (size_t)THREADS * (E / 2) * sizeof(Cx<T>);
+    static constexpr size_t SMEM = z_smem(TX, NT, L, E, (int)sizeof(T));
     static_assert(THREADS <= 1024, "z tile too large");
+};
+
+// Layout of the Green's spectrum read by the z pass: [ky'][kx tile][kz'][TX]
+// with ky' <= My/2, kz' <= Mz/2 and kx = tile * TX + c (padded with zeros
+// past Mx/2), so the TX x (Mz/2 + 1) block of one tile is contiguous.
+struct ZSpecLayout {
+    int tx, ntx, nkz;  // tile width, kx tiles, Mz/2 + 1
+    __host__ __device__ size_t at(int kyp, int xt, int kzp, int c) const
+    {
+        return (((size_t)kyp * ntx + xt) * nkz + kzp) * tx + c;
+    }
 };
 
 // ---------------------------------------------------------------------
@@ -260,7 +321,7 @@ k_y_forward(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx)
         const int y = t + m * NT;
         v[m] = (m < E / 2 && active && y < Ny) ? base[(size_t)y * Kx] : Cx<T>{(T)0, (T)0};
     }
-    ColXch<T, L, E, TX> xch{reinterpret_cast<Cx<T> *>(smem_raw), c};
+    ColXch<T, L, E, TX, TX * sizeof(Cx<T>) == 64> xch{reinterpret_cast<Cx<T> *>(smem_raw), c};
     run_stages<T, L, E, true>(v, t, tw, xch, typename Shape<T, L>::Rad{});
     if (active) {
 #pragma unroll
@@ -286,7 +347,7 @@ k_y_inverse(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx)
 #pragma unroll
     for (int m = 0; m < E; ++m)
         v[m] = active ? cswap(base[(size_t)(t + m * NT) * Kx]) : Cx<T>{(T)0, (T)0};
-    ColXch<T, L, E, TX> xch{reinterpret_cast<Cx<T> *>(smem_raw), c};
+    ColXch<T, L, E, TX, TX * sizeof(Cx<T>) == 64> xch{reinterpret_cast<Cx<T> *>(smem_raw), c};
     run_stages<T, L, E, false>(v, t, tw, xch, typename Shape<T, L>::Rad{});
     if (active) {
 #pragma unroll
@@ -299,85 +360,137 @@ k_y_inverse(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx)
 
 // ---------------------------------------------------------------------
 // K3: z forward, multiply by the Green's spectrum, z inverse.
-// grid (ceil(Kx / TX), My / 2); CTA y index p handles the line pair
-// (ky, My - ky) = (p, My - p) for p > 0 and (0, My/2) for p = 0.
+// Tiles: (pair p, kx tile xt), tile = p * ntx + xt; pair p holds the lines
+// (ky, My - ky) = (p, My - p) for p > 0 and (0, My/2) for p = 0.  A
+// persistent grid walks the tiles; each CTA keeps the next tile's loads in
+// flight during the current tile's transforms.
 // gscale multiplies the cached spectrum (the cache stores it for widths
 // divided by min(h); G scales as h^2).
 // ---------------------------------------------------------------------
 template <typename T, int L>
-__global__ void __launch_bounds__(ZCfg<T, L>::THREADS)
+__global__ void __launch_bounds__(ZCfg<T, L>::THREADS, 1)
 k_z_convolve(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, const T *__restrict__ G,
-             const T *__restrict__ Gs, T gscale, int Nz, int My, int Kx)
+             const T *__restrict__ Gs, T gscale, int Nz, int My, int Kx, int ntiles)
 {
     using C = ZCfg<T, L>;
-    constexpr int E = C::E, NT = C::NT, TX = C::TX, COLS = C::COLS;
+    constexpr int E = C::E, NT = C::NT, TX = C::TX, COLS = C::COLS, TH = C::THREADS;
     constexpr int Lh = L / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<T> *sm = reinterpret_cast<Cx<T> *>(smem_raw);
-    const int c = threadIdx.x % TX;
-    const int rest = threadIdx.x / TX;
-    const int t = rest % NT, g = rest / NT;
-    const int pr = blockIdx.y;
-    const int ky = g == 0 ? pr : (pr == 0 ? My / 2 : My - pr);
-    const int kyp = ky <= My - ky ? ky : My - ky;
-    const int kx = blockIdx.x * TX + c;
-    const bool active = kx < Kx;
+    Cx<T> *st_in = reinterpret_cast<Cx<T> *>(smem_raw + C::XCH);          // [E/2][TH]
+    T *st_g = reinterpret_cast<T *>(smem_raw + C::XCH + C::STAGE_IN);     // [E][TH]
+    // thread -> (column c, group g, position t): a warp holds both groups of
+    // a few positions, so each position row of the exchange buffer is written
+    // whole and the warp's shared-memory accesses are conflict-free
+    const int tid = threadIdx.x;
+    const int c = tid % TX;
+    const int g = (tid / TX) & 1;
+    const int t = tid / COLS;
     const int col = g * TX + c;
+    const int ntx = (Kx + TX - 1) / TX;
     const size_t zstride = (size_t)My * Kx;
-    Cx<T> *base = W + (size_t)ky * Kx + (active ? kx : 0);
+    const ZSpecLayout lay{TX, ntx, Lh + 1};
 
-    Cx<T> v[E];
+    auto line_of = [&](int tile, int &ky, int &kx, int &pr, int &xt) {
+        pr = tile / ntx;
+        xt = tile - pr * ntx;
+        ky = g == 0 ? pr : (pr == 0 ? My / 2 : My - pr);
+        kx = xt * TX + c;
+    };
+    // stage the non-zero half of this thread's line of `tile`
+    auto stage_input = [&](int tile) {
+        int ky, kx, pr, xt;
+        line_of(tile, ky, kx, pr, xt);
+        const bool active = kx < Kx;
+        const Cx<T> *base = W + (size_t)ky * Kx + (active ? kx : 0);
 #pragma unroll
-    for (int m = 0; m < E; ++m) {
-        const int z = t + m * NT;
-        v[m] = (m < E / 2 && active && z < Nz) ? base[(size_t)z * zstride] : Cx<T>{(T)0, (T)0};
-    }
-    ColXch<T, L, E, COLS> xch{sm, col};
-    run_stages<T, L, E, true>(v, t, tw, xch, typename Shape<T, L>::Rad{});
-
-    const T *grow = G + (size_t)kyp * (Lh + 1) * Kx;
-    const bool packed = blockIdx.x == 0 && c == 0;  // the kx = 0 / Mx/2 column
-    if (blockIdx.x == 0) {
-        // the packed column needs the partner bin (-ky, -kz)
-        if (c == 0) {
-#pragma unroll
-            for (int m = 0; m < E; ++m) sm[(t + m * NT) * COLS + col] = v[m];
+        for (int m = 0; m < E / 2; ++m) {
+            const int z = t + m * NT;
+            const bool ok = active && z < Nz;
+            cp_async<sizeof(Cx<T>)>(&st_in[m * TH + tid], ok ? base + (size_t)z * zstride : W, ok);
         }
-        __syncthreads();
-        if (c == 0) {
-            const int gp = pr == 0 ? g : 1 - g;
-            const T *gsrow = Gs + (size_t)kyp * (Lh + 1);
-#pragma unroll
-            for (int m = 0; m < E; ++m) {
-                const int kz = t + m * NT;
-                const int kzp = kz <= L - kz ? kz : L - kz;
-                const Cx<T> partner = cconj(sm[(kz == 0 ? 0 : L - kz) * COLS + gp * TX]);
-                const T gp_ = grow[(size_t)kzp * Kx] * gscale;
-                const T gm_ = gsrow[kzp] * gscale;
-                v[m] = {v[m].x * gp_ + partner.x * gm_, v[m].y * gp_ + partner.y * gm_};
-            }
-        }
-        __syncthreads();
-    }
-    if (!packed) {
+    };
+    // stage the spectrum values at this thread's bins of `tile`
+    auto stage_spectrum = [&](int tile) {
+        int ky, kx, pr, xt;
+        line_of(tile, ky, kx, pr, xt);
+        const int kyp = ky <= My - ky ? ky : My - ky;
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int kz = t + m * NT;
             const int kzp = kz <= L - kz ? kz : L - kz;
-            const T gv = active ? grow[(size_t)kzp * Kx + kx] * gscale : (T)0;
-            v[m] = cscale(v[m], gv);
+            cp_async<sizeof(T)>(&st_g[m * TH + tid], G + lay.at(kyp, xt, kzp, c), true);
+        }
+    };
+
+    ColXch<T, L, E, COLS> xch{sm, col};
+    int tile = blockIdx.x;
+    if (tile < ntiles) {
+        stage_input(tile);
+        cp_async_commit();
+        stage_spectrum(tile);
+        cp_async_commit();
+    }
+    for (; tile < ntiles; tile += gridDim.x) {
+        const int next = tile + gridDim.x;
+        int ky, kx, pr, xt;
+        line_of(tile, ky, kx, pr, xt);
+        const bool active = kx < Kx;
+        const int kyp = ky <= My - ky ? ky : My - ky;
+
+        cp_async_wait<1>();  // this tile's input has landed (its spectrum may not have)
+        Cx<T> v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = m < E / 2 ? st_in[m * TH + tid] : Cx<T>{(T)0, (T)0};
+        if (next < ntiles) stage_input(next);
+        cp_async_commit();
+
+        run_stages<T, L, E, true>(v, t, tw, xch, typename ZShape<T, L>::Rad{});
+
+        cp_async_wait<1>();  // this tile's spectrum has landed
+        const bool packed = xt == 0 && c == 0;  // the kx = 0 / Mx/2 column
+        if (xt == 0) {
+            // the packed column needs the partner bin (-ky, -kz)
+            if (c == 0) {
+#pragma unroll
+                for (int m = 0; m < E; ++m) sm[(t + m * NT) * COLS + col] = v[m];
+            }
+            __syncthreads();
+            if (c == 0) {
+                const int gp = pr == 0 ? g : 1 - g;
+                const T *gsrow = Gs + (size_t)kyp * (Lh + 1);
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    const int kz = t + m * NT;
+                    const int kzp = kz <= L - kz ? kz : L - kz;
+                    const Cx<T> partner = cconj(sm[(kz == 0 ? 0 : L - kz) * COLS + gp * TX]);
+                    const T gp_ = st_g[m * TH + tid] * gscale;
+                    const T gm_ = gsrow[kzp] * gscale;
+                    v[m] = {v[m].x * gp_ + partner.x * gm_, v[m].y * gp_ + partner.y * gm_};
+                }
+            }
+            __syncthreads();
+        }
+        if (!packed) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = cscale(v[m], st_g[m * TH + tid] * gscale);
+        }
+        if (next < ntiles) stage_spectrum(next);
+        cp_async_commit();
+
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = cswap(v[m]);
+        run_stages<T, L, E, false>(v, t, tw, xch, typename ZShape<T, L>::Rad{});
+        if (active) {
+            Cx<T> *base = W + (size_t)ky * Kx + kx;
+#pragma unroll
+            for (int m = 0; m < E / 2; ++m) {
+                const int z = t + m * NT;
+                if (z < Nz) base[(size_t)z * zstride] = cswap(v[m]);
+            }
         }
     }
-#pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = cswap(v[m]);
-    run_stages<T, L, E, false>(v, t, tw, xch, typename Shape<T, L>::Rad{});
-    if (active) {
-#pragma unroll
-        for (int m = 0; m < E / 2; ++m) {
-            const int z = t + m * NT;
-            if (z < Nz) base[(size_t)z * zstride] = cswap(v[m]);
-        }
-    }
+    cp_async_wait<0>();
 }
 
 }  // namespace isofft

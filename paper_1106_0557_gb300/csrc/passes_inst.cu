@@ -140,17 +140,37 @@ template cudaError_t launch_y_inverse<Real>(int, void *, const void *, int, int,
 #endif
 
 #if ISOFFT_GROUP == 3
+// Resident CTAs per SM of a kernel on the current device (queried once).
+template <typename F>
+static int resident_ctas(F *func, int threads, size_t smem, std::atomic<int> &cache)
+{
+    int v = cache.load(std::memory_order_acquire);
+    if (v > 0) return v;
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, func, threads, smem) != cudaSuccess) return 0;
+    v = sms * (per > 0 ? per : 1);
+    cache.store(v, std::memory_order_release);
+    return v;
+}
+
 template <typename T, int L>
 static cudaError_t run_z(void *W, const void *tw, const T *G, const T *Gs, T gscale, int Nz, int My, int Kx,
                          cudaStream_t st)
 {
     using C = ZCfg<T, L>;
     static std::atomic<uint64_t> done{0};
+    static std::atomic<int> slots{0};
     cudaError_t e = ensure_smem(k_z_convolve<T, L>, C::SMEM, done);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)((Kx + C::TX - 1) / C::TX), (unsigned)(My / 2));
-    k_z_convolve<T, L><<<grid, C::THREADS, C::SMEM, st>>>((Cx<T> *)W, (const Cx<T> *)tw, G, Gs, gscale, Nz,
-                                                         My, Kx);
+    const int ntx = (Kx + C::TX - 1) / C::TX;
+    const int ntiles = ntx * (My / 2);
+    int grid = resident_ctas(k_z_convolve<T, L>, C::THREADS, C::SMEM, slots);
+    if (grid <= 0) return cudaErrorInvalidConfiguration;
+    if (grid > ntiles) grid = ntiles;
+    k_z_convolve<T, L><<<grid, C::THREADS, C::SMEM, st>>>((Cx<T> *)W, (const Cx<T> *)tw, G, Gs, gscale, Nz, My,
+                                                         Kx, ntiles);
     count_launch();
     return cudaGetLastError();
 }
@@ -166,8 +186,20 @@ cudaError_t launch_z_convolve(int L, void *W, const void *tw, const R_ *G, const
     default: return cudaErrorInvalidValue;
     }
 }
+template <typename R_>
+int z_tile_for(int L)
+{
+    switch (L) {
+#define X_(n) \
+    case n: return ZCfg<R_, n>::TX;
+        ISOFFT_COL_LENGTHS(X_)
+#undef X_
+    default: return 0;
+    }
+}
 template cudaError_t launch_z_convolve<Real>(int, void *, const void *, const Real *, const Real *, Real, int,
                                              int, int, cudaStream_t);
+template int z_tile_for<Real>(int);
 #endif
 
 }  // namespace isofft
