@@ -115,6 +115,28 @@ int ipf_solve(ipf_plan_t plan, const void *d_src, void *d_phi, void *stream);
  * synchronises `stream` before returning. */
 int ipf_solve_host(ipf_plan_t plan, const void *h_src, void *h_phi, void *stream);
 
+/* One solve that allocates no memory, for callers that cannot call
+ * cudaMalloc: a code that has given all device memory to its own pool, a
+ * solve issued while a stream is being captured into a CUDA graph, or a
+ * time-step loop that must not take the device-wide synchronisation an
+ * allocation or free may imply.  The paper has no counterpart; it is a
+ * deployment variant of ipf_solve.
+ *   n, h, dtype  as for ipf_plan_create (no plan is needed).
+ *   d_src, d_phi device arrays as for ipf_solve (d_phi may equal d_src).
+ * Twiddle tables, the Green's spectrum and the workspace are all carved out
+ * of one static device array of 64 MiB that the library holds on every
+ * device it is loaded on until the process exits; the spectrum is rebuilt on
+ * every call.  A mesh whose tables, spectrum and workspace exceed 64 MiB is
+ * rejected with IPF_BUDGET_EXCEEDED before any device work (FP32 fits up to
+ * about 128^3 cells, FP64 up to about 96^3).  Every call overwrites the whole
+ * array (nothing in it needs to start at zero), so calls whose work overlaps
+ * on the GPU -- on different streams, or from different threads -- race and
+ * must be serialised by the caller.  The first call on each device looks up
+ * the array's device address and sets kernel attributes; make that first
+ * call before any stream capture.  Asynchronous on `stream`. */
+int ipf_solve_noalloc(const int64_t n[3], const double h[3], int dtype, const void *d_src, void *d_phi,
+                      void *stream);
+
 /* Submit `count` independent solves, possibly of different shapes and
  * dtypes, on one stream; plans[i] solves d_src[i] into d_phi[i].  A plan may
  * appear only once per batch (each owns one workspace).  Asynchronous. */

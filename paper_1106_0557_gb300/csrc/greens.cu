@@ -202,6 +202,73 @@ cudaError_t build_green_spectrum(const int64_t M[3], const double hn[3], T *G, T
     return e;
 }
 
+// Same spectrum as build_green_spectrum, enqueued on `st` without allocating
+// or synchronising: the FP64 octants live in the caller's `oct` scratch
+// (green_octant_elems(M) doubles each, two of them), the cosine tables in
+// `ct` (green_cos_elems(M) doubles, filled on the device by k_cos_tables).
+static __global__ void k_cos_tables(double *__restrict__ ct, int mx, int my, int mz)
+{
+    const int X = mx / 2 + 1, Y = my / 2 + 1, Z = mz / 2 + 1;
+    const int64_t tot = (int64_t)X * X + (int64_t)Y * Y + (int64_t)Z * Z;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t j = i;
+        int n, m;
+        if (j < (int64_t)X * X) {
+            n = X, m = mx;
+        } else if ((j -= (int64_t)X * X) < (int64_t)Y * Y) {
+            n = Y, m = my;
+        } else {
+            j -= (int64_t)Y * Y;
+            n = Z, m = mz;
+        }
+        const int64_t p = j / n, k = j % n;
+        const double w = (p == 0 || 2 * p == m) ? 1.0 : 2.0;
+        ct[i] = w * cospi(2.0 * (double)((k * p) % m) / (double)m);
+    }
+}
+
+int64_t green_octant_elems(const int64_t M[3])
+{
+    return (M[0] / 2 + 1) * (M[1] / 2 + 1) * (M[2] / 2 + 1);
+}
+int64_t green_cos_elems(const int64_t M[3])
+{
+    int64_t t = 0;
+    for (int a = 0; a < 3; ++a) t += (M[a] / 2 + 1) * (M[a] / 2 + 1);
+    return t;
+}
+
+template <typename T>
+cudaError_t enqueue_green_spectrum(const int64_t M[3], const double hn[3], T *G, T *Gs, double *oct,
+                                   double *ct, cudaStream_t st)
+{
+    const int X = (int)(M[0] / 2 + 1), Y = (int)(M[1] / 2 + 1), Z = (int)(M[2] / 2 + 1);
+    const int64_t n = (int64_t)X * Y * Z;
+    double *o0 = oct, *o1 = oct + n;
+    double *ctx = ct, *cty = ct + (int64_t)X * X, *ctz = cty + (int64_t)Y * Y;
+    k_cos_tables<<<grid_for(green_cos_elems(M)), 256, 0, st>>>(ct, (int)M[0], (int)M[1], (int)M[2]);
+    count_launch();
+    k_green_octant<<<grid_for(n), 256, 0, st>>>(o0, X, Y, Z, hn[0], hn[1], hn[2]);
+    count_launch();
+    k_cos_axis<<<grid_for(n), 256, 0, st>>>(o0, o1, ctx, (int64_t)Z * Y, X, 1);
+    count_launch();
+    k_cos_axis<<<grid_for(n), 256, 0, st>>>(o1, o0, cty, Z, Y, X);
+    count_launch();
+    k_cos_axis<<<grid_for(n), 256, 0, st>>>(o0, o1, ctz, 1, Z, (int64_t)Y * X);
+    count_launch();
+    const double scale = 1.0 / (2.0 * (double)M[0] * (double)M[1] * (double)M[2]);
+    const int tx = z_tile_for<T>((int)M[2]);
+    const int ntx = (int)((M[0] / 2 + tx - 1) / tx);
+    k_pack<T><<<grid_for((int64_t)Y * ntx * Z * tx), 256, 0, st>>>(o1, G, Gs, X, Y, Z, tx, ntx, scale);
+    count_launch();
+    return cudaGetLastError();
+}
+template cudaError_t enqueue_green_spectrum<float>(const int64_t *, const double *, float *, float *, double *,
+                                                   double *, cudaStream_t);
+template cudaError_t enqueue_green_spectrum<double>(const int64_t *, const double *, double *, double *,
+                                                    double *, double *, cudaStream_t);
+
 template cudaError_t build_green_spectrum<float>(const int64_t *, const double *, float *, float *,
                                                  cudaStream_t);
 template cudaError_t build_green_spectrum<double>(const int64_t *, const double *, double *, double *,

@@ -48,6 +48,15 @@ size_t spectrum_elems(const int64_t M[3]);
 template <typename T>
 cudaError_t build_green_spectrum(const int64_t M[3], const double hn[3], T *G, T *Gs, cudaStream_t st);
 
+// The same spectrum enqueued without allocating or synchronising, in caller
+// scratch: `oct` holds 2 * green_octant_elems(M) doubles, `ct` holds
+// green_cos_elems(M) doubles (cosine tables, computed on the device).
+template <typename T>
+cudaError_t enqueue_green_spectrum(const int64_t M[3], const double hn[3], T *G, T *Gs, double *oct,
+                                   double *ct, cudaStream_t st);
+int64_t green_octant_elems(const int64_t M[3]);
+int64_t green_cos_elems(const int64_t M[3]);
+
 // Device bytes of the FP64 scratch build_green_spectrum needs for mesh M.
 size_t green_build_scratch_bytes(const int64_t M[3]);
 

@@ -54,6 +54,7 @@ def _declare(L):
         "ipf_estimate_bytes": [i64p, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
         "ipf_solve": [vp, vp, vp, vp],
         "ipf_solve_host": [vp, vp, vp, vp],
+        "ipf_solve_noalloc": [i64p, dp, ctypes.c_int, vp, vp, vp],
         "ipf_submit_batch": [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), vp],
         "ipf_plan_pass_times": [vp, ctypes.POINTER(ctypes.c_float)],
         "ipf_greens_cache_bytes": [ctypes.POINTER(ctypes.c_size_t)],
@@ -150,6 +151,13 @@ def ipf_solve(plan, d_src, d_phi, stream=0):
 def ipf_solve_host(plan, h_src, h_phi, stream=0):
     _check(lib().ipf_solve_host(ctypes.c_void_p(plan), ctypes.c_void_p(int(h_src)), ctypes.c_void_p(int(h_phi)),
                                 ctypes.c_void_p(int(stream))), "ipf_solve_host")
+
+
+def ipf_solve_noalloc(n, h, dtype, d_src, d_phi, stream=0):
+    """Plan-free solve whose scratch is the library's static device array
+    (no allocation); see include/isofft.h for its limits."""
+    _check(lib().ipf_solve_noalloc(_i64x3(n), _f64x3(h), DTYPES[dtype], ctypes.c_void_p(int(d_src)),
+                                   ctypes.c_void_p(int(d_phi)), ctypes.c_void_p(int(stream))), "ipf_solve_noalloc")
 
 
 def ipf_submit_batch(plans, d_srcs, d_phis, stream=0):
