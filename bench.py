@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--impl", default="isofft", choices=["isofft", "reference"])
     ap.add_argument("--n", type=int, default=N_BENCH)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-slots", type=int, default=8)
     return ap.parse_args()
 
 
@@ -248,6 +252,99 @@ def run_reference(args, ws, rank):
 
 
 # ---------------------------------------------------------------------------
+# batched and served solves
+# ---------------------------------------------------------------------------
+def run_batch(steps=50, count=64):
+    """64 independent grids (each axis from {32,48,64,96,128}), FP32, as one
+    batch captured in a CUDA graph and replayed; also the same batch
+    submitted without a graph."""
+    import torch
+
+    from paper_1106_0557_gb300 import sources
+    from paper_1106_0557_gb300.solver import BatchGraph, Plan, submit_batch
+    wl = sources.ragged_batch(count)
+    plans = [Plan(w.N, w.h, "f32") for w in wl]
+    srcs = [torch.from_numpy(w.source(np.float32)).cuda() for w in wl]
+    outs = [torch.empty_like(x) for x in srcs]
+    nbytes = 0
+    for p, w in zip(plans, wl):
+        nbytes += sum(pass_bytes(w.N, p.padded_shape, 4).values())
+    res = {"grids": count, "workload": "ragged batch, each axis from {32,48,64,96,128}, seed = grid index"}
+    for mode in ("graph", "submit"):
+        if mode == "graph":
+            bg = BatchGraph(plans, srcs, outs)
+            run = bg.replay
+        else:
+            def run():
+                submit_batch(plans, srcs, outs)
+        for _ in range(3):
+            run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            run()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        res[mode] = {"ms_per_batch": round(ms, 4), "solves_per_s": round(count / (ms / 1e3), 1),
+                     "hbm_gbs_algorithmic": round(nbytes / (ms / 1e3) / 1e9, 1)}
+    for p in plans:
+        p.close()
+    return res
+
+
+def run_serving(n_requests, slots):
+    """Config-5 style serving: cubic N log-uniform in [32, 384], 70 % FP32 /
+    30 % FP64, HBM budget 120 GB.  Saturated throughput (all requests at t=0),
+    then Poisson arrivals at 0.8 x that rate for p50/p99 latency; and the FP32
+    class served vs the same shapes solved one at a time in FP64."""
+    import torch
+
+    from paper_1106_0557_gb300 import native, serving, sources
+    spec = sources.serving_requests(count=n_requests, seed=0)
+    mk = lambda arr: [serving.Request(r["id"], r["n"], r["dtype"], r["seed"], a) for r, a in zip(spec, arr)]
+    be = serving.TorchBackend(slots=slots)
+    reqs = mk(np.zeros(len(spec)))
+    be.prepare(reqs)
+    be.warm_spectra(reqs)
+    srv = serving.Server(be, budget_bytes=120e9, slots=slots)
+    sat = serving.saturated_throughput(srv, be, reqs)
+    rate = 0.8 * sat["solves_per_s"]
+    reqs2 = mk(serving.poisson_arrivals(len(spec), rate, seed=1))
+    srv.run(reqs2)
+    lat = serving.latency_stats(reqs2)
+    # FP32 class served (saturated) vs plain unbatched FP64 on the same shapes
+    sub = [r for r in reqs if r.dtype == "f32"][:300]
+    served32 = serving.saturated_throughput(srv, be, sub)
+    srv.close()
+    # plain path: one FP64 solve at a time on one stream, plan set-up excluded
+    shapes = [r.n for r in sub]
+    plain_s = 0.0
+    stream = torch.cuda.current_stream().cuda_stream
+    for n in shapes:
+        p = native.ipf_plan_create((n,) * 3, (1.0 / n,) * 3, "f64")
+        src = be.source(n, "f64")
+        out = torch.empty_like(src)
+        torch.cuda.synchronize()
+        ts = time.perf_counter()
+        native.ipf_solve(p, src.data_ptr(), out.data_ptr(), stream)
+        torch.cuda.synchronize()
+        plain_s += time.perf_counter() - ts
+        native.ipf_plan_destroy(p)
+    plain64 = len(shapes) / plain_s
+    return {"requests": len(spec), "slots": slots, "budget_gb": 120,
+            "mix": "cubic N log-uniform [32,384], 70% f32 / 30% f64",
+            "saturated_solves_per_s": round(sat["solves_per_s"], 1),
+            "poisson_rate": round(rate, 1), "p50_ms": round(lat["p50_ms"], 3), "p99_ms": round(lat["p99_ms"], 3),
+            "solves_per_s": round(lat["solves_per_s"], 1),
+            "f32_served_solves_per_s": round(served32["solves_per_s"], 1),
+            "f64_plain_unbatched_solves_per_s": round(plain64, 1),
+            "f32_served_over_f64_plain": round(served32["solves_per_s"] / plain64, 2),
+            "peak_bytes": int(srv.peak_bytes)}
+
+
+# ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
 def run_isofft(args, ws, rank, local):
@@ -347,6 +444,9 @@ def run_isofft(args, ws, rank, local):
     achieved = bytes32[dname] / (passes32[dom] / 1e3) / 1e9
     traffic = profile_traffic(KERNELS[dname], "f32_%d" % n)
 
+    batch = None if args.no_batch else run_batch()
+    serve = None if args.no_serve else run_serving(args.serve_requests, args.serve_slots)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         done, secs, cores = time_oracle(n, 1, budget_s=60.0)
@@ -376,6 +476,8 @@ def run_isofft(args, ws, rank, local):
                      "traffic": traffic, "algorithmic_bytes": bytes32[dname]},
         "e2e": {"value": e2e_value, "unit": "solves/s", "steps": e2e_steps, "h2d_bytes_per_step": io_bytes,
                 "d2h_bytes_per_step": io_bytes},
+        "batch": batch,
+        "serving": serve,
         "cpu_baseline": cpu,
         "gpu_launches": launches,
         "clocks": clocks,

@@ -138,8 +138,15 @@ int ipf_solve_noalloc(const int64_t n[3], const double h[3], int dtype, const vo
                       void *stream);
 
 /* Submit `count` independent solves, possibly of different shapes and
- * dtypes, on one stream; plans[i] solves d_src[i] into d_phi[i].  A plan may
- * appear only once per batch (each owns one workspace).  Asynchronous. */
+ * dtypes; plans[i] solves d_src[i] into d_phi[i].  A plan may appear only
+ * once per batch (each owns one workspace).  The solves are spread over up to
+ * 8 internal streams of the library that fork from and join back into
+ * `stream`: the batch starts after the work already enqueued on `stream`, and
+ * work enqueued on `stream` afterwards starts after the whole batch.  The
+ * first batch of two or more solves on a device creates those streams; make
+ * it before capturing `stream` into a CUDA graph (a capture then records the
+ * batch as parallel branches).  Results are bitwise those of ipf_solve.
+ * Asynchronous. */
 int ipf_submit_batch(const ipf_plan_t *plans, int count, const void *const *d_src,
                      void *const *d_phi, void *stream);
 

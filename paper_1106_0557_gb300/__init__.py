@@ -10,11 +10,11 @@ Importing the package loads nothing; the CUDA library is built/loaded at the
 first call and every entry point raises if it is unavailable.
 """
 
-__all__ = ["native", "solver", "sources", "build", "Plan", "solve", "submit_batch"]
+__all__ = ["native", "solver", "sources", "build", "Plan", "solve", "submit_batch", "BatchGraph"]
 
 
 def __getattr__(name):
-    if name in ("Plan", "solve", "submit_batch"):
+    if name in ("Plan", "solve", "submit_batch", "BatchGraph"):
         from . import solver
         return getattr(solver, name)
     if name in ("native", "solver", "sources", "build"):

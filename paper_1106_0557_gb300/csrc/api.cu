@@ -11,6 +11,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -302,6 +303,39 @@ int solve_impl(ipf_plan_s *p, const void *src, void *phi, cudaStream_t st)
 
 bool aligned16(const void *ptr) { return ((uintptr_t)ptr & 15u) == 0; }
 
+// Internal streams a batch is spread over, created once per device on the
+// first multi-solve batch (so that first batch should precede any capture).
+struct BatchLanes {
+    static constexpr int kLanes = 8;
+    cudaStream_t lane[kLanes] = {};
+    cudaEvent_t fork = nullptr, join[kLanes] = {};
+    std::mutex mu;
+};
+std::mutex g_lanes_mu;
+BatchLanes *g_lanes[64] = {};
+
+int batch_lanes(BatchLanes **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (dev < 0 || dev >= 64) return IPF_CUDA_ERROR;
+    std::lock_guard<std::mutex> lk(g_lanes_mu);
+    if (!g_lanes[dev]) {
+        BatchLanes *b = new (std::nothrow) BatchLanes();
+        if (!b) return IPF_OUT_OF_MEMORY;
+        e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+        for (int l = 0; l < BatchLanes::kLanes && e == cudaSuccess; ++l) {
+            e = cudaStreamCreateWithFlags(&b->lane[l], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[l], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return cuda_status(e);  // leaked on failure: creation of streams is not retried
+        g_lanes[dev] = b;
+    }
+    *out = g_lanes[dev];
+    return IPF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -465,9 +499,41 @@ int ipf_submit_batch(const ipf_plan_t *plans, int count, const void *const *d_sr
         for (int j = 0; j < i; ++j)
             if (plans[j] == plans[i]) return IPF_INVALID_ARG;
     }
+    if (count == 0) return IPF_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (count == 1) return solve_impl(plans[0], d_src[0], d_phi[0], st);
+    BatchLanes *bl = nullptr;
+    int rc = batch_lanes(&bl);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(bl->mu);
+    // fork: every lane waits for the work already on the caller's stream
+    cudaError_t e = cudaEventRecord(bl->fork, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    const int lanes = count < BatchLanes::kLanes ? count : BatchLanes::kLanes;
+    for (int l = 0; l < lanes; ++l) {
+        e = cudaStreamWaitEvent(bl->lane[l], bl->fork, 0);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    // longest solves first, each to the least-loaded lane
+    std::vector<int> order(count);
+    std::vector<double> cost(count), load(lanes, 0.0);
     for (int i = 0; i < count; ++i) {
-        int rc = solve_impl(plans[i], d_src[i], d_phi[i], (cudaStream_t)stream);
+        order[i] = i;
+        const ipf_plan_s *p = plans[i];
+        cost[i] = (double)p->M[0] * p->M[1] * p->N[2] * (p->dtype == IPF_F64 ? 16.0 : 1.0);
+    }
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    for (int i : order) {
+        int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        load[l] += cost[i];
+        rc = solve_impl(plans[i], d_src[i], d_phi[i], bl->lane[l]);
         if (rc) return rc;
+    }
+    // join: the caller's stream waits for every lane
+    for (int l = 0; l < lanes; ++l) {
+        e = cudaEventRecord(bl->join[l], bl->lane[l]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, bl->join[l], 0);
+        if (e != cudaSuccess) return cuda_status(e);
     }
     return IPF_OK;
 }

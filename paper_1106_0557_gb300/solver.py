@@ -109,3 +109,26 @@ def submit_batch(plans, srcs, outs, stream=None):
     native.ipf_submit_batch([p.handle for p in plans], [s.data_ptr() for s in srcs],
                             [o.data_ptr() for o in outs], _stream_handle(stream))
     return outs
+
+
+class BatchGraph:
+    """A fixed batch of solves captured once into a CUDA graph.
+
+    The batch's sources and outputs are the given tensors: refill the sources
+    in place and ``replay()`` re-runs every solve (the library's internal
+    streams appear in the graph as parallel branches).  The constructor runs
+    the batch once outside capture so every one-off set-up (internal streams,
+    kernel attributes) happens before the capture."""
+
+    def __init__(self, plans, srcs, outs):
+        self.plans, self.srcs, self.outs = list(plans), list(srcs), list(outs)
+        submit_batch(self.plans, self.srcs, self.outs)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            submit_batch(self.plans, self.srcs, self.outs)
+        torch.cuda.synchronize()
+
+    def replay(self):
+        self.graph.replay()
+        return self.outs

@@ -57,6 +57,32 @@ def rasterize(bodies, N, h, lo=(0.0, 0.0, 0.0), dtype=np.float64):
     return S.astype(dtype, copy=False)
 
 
+def rasterize_torch(bodies, N, h, lo=(0.0, 0.0, 0.0), device="cuda", dtype=None):
+    """The same point sampling as `rasterize`, evaluated with torch on a
+    device (for large sources made in bulk, e.g. a serving source bank)."""
+    import torch
+    dtype = dtype or torch.float64
+    Nx, Ny, Nz = N
+    x = (lo[0] + (torch.arange(Nx, device=device, dtype=torch.float64) + 0.5) * h[0]).view(1, 1, Nx)
+    y = (lo[1] + (torch.arange(Ny, device=device, dtype=torch.float64) + 0.5) * h[1]).view(1, Ny, 1)
+    z = (lo[2] + (torch.arange(Nz, device=device, dtype=torch.float64) + 0.5) * h[2]).view(Nz, 1, 1)
+    S = torch.zeros((Nz, Ny, Nx), dtype=torch.float64, device=device)
+    for bd in bodies:
+        c = bd["center"]
+        if bd["kind"] == "sphere":
+            r2 = (x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2
+            S += (r2 <= bd["radius"] ** 2).to(torch.float64) * (FOUR_PI * bd["rho"])
+        elif bd["kind"] == "spheroid":
+            q = ((x - c[0]) ** 2 + (y - c[1]) ** 2) / bd["a"] ** 2 + (z - c[2]) ** 2 / bd["b"] ** 2
+            S += (q <= 1.0).to(torch.float64) * (FOUR_PI * bd["rho"])
+        elif bd["kind"] == "gaussian":
+            r2 = (x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2
+            S += FOUR_PI * bd["amp"] * torch.exp(-r2 / (2.0 * bd["sigma"] ** 2))
+        else:
+            raise ValueError(bd["kind"])
+    return S.to(dtype)
+
+
 class Workload:
     """A seeded problem: mesh shape N = (Nx, Ny, Nz), cell widths h, the box
     origin and the bodies that make the source."""
