@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="isofft", choices=["isofft", "reference"])
-    ap.add_argument("--n", type=int, default=N_BENCH)
+    ap.add_argument("--cells", type=int, default=N_BENCH, help="cells per axis of the workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
@@ -235,7 +235,7 @@ def time_oracle(n, steps, budget_s):
 def run_reference(args, ws, rank):
     if rank != 0:
         return
-    n = args.n
+    n = args.cells
     done, secs, cores = time_oracle(n, max(1, args.steps), budget_s=150.0)
     value = done / secs
     sample = ("%d full %d^3 FP64 oracle solve(s) (doubled mesh %d^3, recursive FFT), Green's spectrum "
@@ -356,7 +356,7 @@ def run_isofft(args, ws, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     native.lib()
-    n = args.n
+    n = args.cells
     w = sources.multi_sphere(n, seed=0)
     src64 = w.source()
     N = w.N
