@@ -121,6 +121,8 @@ struct ipf_plan_s {
     static constexpr int kSlots = 64;
     cudaEvent_t ev[kSlots][6] = {};
     bool have_events = false;
+    // x and y passes fused per z plane (square xy mesh; opt-in with ISOFFT_FUSE_XY=1)
+    bool fuse_xy = false;
     uint64_t solves = 0, folded = 0;
     double pass_sum[5] = {0, 0, 0, 0, 0};
     uint64_t pass_n = 0;
@@ -275,21 +277,42 @@ cudaError_t enqueue_solve(ipf_plan_s *p, const void *src, void *phi, cudaStream_
         p->solves += 1;
     }
     if (ev_on) cudaEventRecord(ev[0], st);
-    e = launch_x_forward<T>(Lx, (const T *)src, p->W, p->tw_x, p->rtw, Nx, Ny, My, nrows, st);
-    if (e != cudaSuccess) return e;
+    bool fused = false;
+    if (p->fuse_xy) {
+        e = launch_xy_forward<T>(Lx, (const T *)src, p->W, p->tw_x, p->rtw, p->tw_y, Nx, Ny, Nz, st);
+        if (e == cudaSuccess) {
+            fused = true;
+        } else {
+            cudaGetLastError();  // the cluster launch was refused: use the separate passes from now on
+            p->fuse_xy = false;
+        }
+    }
+    if (!fused) {
+        e = launch_x_forward<T>(Lx, (const T *)src, p->W, p->tw_x, p->rtw, Nx, Ny, My, nrows, st);
+        if (e != cudaSuccess) return e;
+    }
     if (ev_on) cudaEventRecord(ev[1], st);
-    e = launch_y_forward<T>(My, p->W, p->tw_y, Ny, Lx, Nz, st);
-    if (e != cudaSuccess) return e;
+    if (!fused) {
+        e = launch_y_forward<T>(My, p->W, p->tw_y, Ny, Lx, Nz, st);
+        if (e != cudaSuccess) return e;
+    }
     if (ev_on) cudaEventRecord(ev[2], st);
     e = launch_z_convolve<T>(Mz, p->W, p->tw_z, (const T *)p->spec->G, (const T *)p->spec->Gs,
                              (T)p->gscale, Nz, My, Lx, st);
     if (e != cudaSuccess) return e;
     if (ev_on) cudaEventRecord(ev[3], st);
-    e = launch_y_inverse<T>(My, p->W, p->tw_y, Ny, Lx, Nz, st);
-    if (e != cudaSuccess) return e;
+    if (fused) {
+        e = launch_yx_inverse<T>(Lx, p->W, (T *)phi, p->tw_x, p->rtw, p->tw_y, Nx, Ny, Nz, st);
+        if (e != cudaSuccess) return e;
+    } else {
+        e = launch_y_inverse<T>(My, p->W, p->tw_y, Ny, Lx, Nz, st);
+        if (e != cudaSuccess) return e;
+    }
     if (ev_on) cudaEventRecord(ev[4], st);
-    e = launch_x_inverse<T>(Lx, p->W, (T *)phi, p->tw_x, p->rtw, Nx, Ny, My, nrows, st);
-    if (e != cudaSuccess) return e;
+    if (!fused) {
+        e = launch_x_inverse<T>(Lx, p->W, (T *)phi, p->tw_x, p->rtw, Nx, Ny, My, nrows, st);
+        if (e != cudaSuccess) return e;
+    }
     if (ev_on) cudaEventRecord(ev[5], st);
     return cudaSuccess;
 }
@@ -361,6 +384,10 @@ int ipf_plan_create(ipf_plan_t *out, const int64_t n[3], const double h[3], int 
     }
     p->dtype = dtype;
     p->flags = flags;
+    {
+        const char *fz = getenv("ISOFFT_FUSE_XY");
+        p->fuse_xy = p->M[0] == p->M[1] && fz && fz[0] == '1';
+    }
     p->verbosity = verbosity;
     p->spec = nullptr;
     cudaError_t ce = cudaGetDevice(&p->device);

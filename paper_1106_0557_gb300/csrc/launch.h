@@ -31,6 +31,15 @@ template <typename T>
 cudaError_t launch_z_convolve(int L, void *W, const void *tw, const T *G, const T *Gs, T gscale, int Nz,
                               int My, int Kx, cudaStream_t st);
 
+// Fused x+y forward / y+x inverse for planes with My = Mx = 2 LX: one
+// cluster of 4 CTAs per z plane (see passes.cuh).
+template <typename T>
+cudaError_t launch_xy_forward(int LX, const T *src, void *W, const void *twx, const void *rtw, const void *twy,
+                              int Nx, int Ny, int Nz, cudaStream_t st);
+template <typename T>
+cudaError_t launch_yx_inverse(int LX, void *W, T *phi, const void *twx, const void *rtw, const void *twy, int Nx,
+                              int Ny, int Nz, cudaStream_t st);
+
 // Width (kx columns per tile) of the z pass for line length L; the cached
 // Green's spectrum is stored in tiles of this width (0: unsupported L).
 template <typename T>

@@ -175,22 +175,35 @@ struct ZSpecLayout {
 };
 
 // ---------------------------------------------------------------------
-// K1: x forward, real rows -> packed half spectra.
-// tw: W_L^k (k < L), rtw: W_{2L}^k (k < L), L = Mx / 2.
+// Pass bodies.  Each works on one row (x passes) or one column tile (y
+// passes) and contains CTA-wide barriers, so every thread of the CTA calls it
+// the same number of times.  CG selects L2-only global loads, for data that
+// other SMs of a cluster wrote moments earlier.
 // ---------------------------------------------------------------------
-template <typename T, int L>
-__global__ void __launch_bounds__(RowCfg<T, L>::THREADS)
-k_x_forward(const T *__restrict__ src, Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw,
-            const Cx<T> *__restrict__ rtw, int Nx, int Ny, int My, int64_t nrows)
+template <bool CG, typename T>
+__device__ __forceinline__ Cx<T> ld_cx(const Cx<T> *p)
 {
-    using C = RowCfg<T, L>;
-    constexpr int E = C::E, NT = C::NT;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int t = threadIdx.x % NT, l = threadIdx.x / NT;
-    Cx<T> *line = reinterpret_cast<Cx<T> *>(smem_raw) + l * RowPad<L>::LP;
-    const int64_t row = (int64_t)blockIdx.x * C::NL + l;  // row = z * Ny + y
-    const bool active = row < nrows;
-    const int64_t rr = active ? row : 0;
+    if constexpr (CG) {
+        if constexpr (sizeof(T) == 4) {
+            const float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+            return {v.x, v.y};
+        } else {
+            const double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
+            return {v.x, v.y};
+        }
+    } else {
+        return *p;
+    }
+}
+
+// K1 body: row rr = z * Ny + y of the source, real -> packed half spectrum.
+// tw: W_L^k (k < L), rtw: W_{2L}^k (k < L), L = Mx / 2.
+template <typename T, int L>
+__device__ __forceinline__ void x_forward_row(const T *__restrict__ src, Cx<T> *__restrict__ W,
+                                              const Cx<T> *__restrict__ tw, const Cx<T> *__restrict__ rtw, int Nx,
+                                              int Ny, int My, int64_t rr, bool active, Cx<T> *line, int t)
+{
+    constexpr int E = Shape<T, L>::E, NT = L / E;
     const T *in = src + rr * Nx;
 
     // pairs (x[2p], x[2p+1]) as one complex point; p >= L/2 is padding
@@ -234,22 +247,13 @@ k_x_forward(const T *__restrict__ src, Cx<T> *__restrict__ W, const Cx<T> *__res
     }
 }
 
-// ---------------------------------------------------------------------
-// K5: x inverse, packed half spectra -> real rows, cropped to x < Nx.
-// ---------------------------------------------------------------------
-template <typename T, int L>
-__global__ void __launch_bounds__(RowCfg<T, L>::THREADS)
-k_x_inverse(const Cx<T> *__restrict__ W, T *__restrict__ phi, const Cx<T> *__restrict__ tw,
-            const Cx<T> *__restrict__ rtw, int Nx, int Ny, int My, int64_t nrows)
+// K5 body: packed half spectrum of row rr -> real row, cropped to x < Nx.
+template <typename T, int L, bool CG = false>
+__device__ __forceinline__ void x_inverse_row(const Cx<T> *__restrict__ W, T *__restrict__ phi,
+                                              const Cx<T> *__restrict__ tw, const Cx<T> *__restrict__ rtw, int Nx,
+                                              int Ny, int My, int64_t rr, bool active, Cx<T> *line, int t)
 {
-    using C = RowCfg<T, L>;
-    constexpr int E = C::E, NT = C::NT;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int t = threadIdx.x % NT, l = threadIdx.x / NT;
-    Cx<T> *line = reinterpret_cast<Cx<T> *>(smem_raw) + l * RowPad<L>::LP;
-    const int64_t row = (int64_t)blockIdx.x * C::NL + l;
-    const bool active = row < nrows;
-    const int64_t rr = active ? row : 0;
+    constexpr int E = Shape<T, L>::E, NT = L / E;
     const int y = (int)(rr % Ny);
     const int64_t z = rr / Ny;
     const Cx<T> *in = W + ((size_t)z * My + y) * L;
@@ -257,7 +261,7 @@ k_x_inverse(const Cx<T> *__restrict__ W, T *__restrict__ phi, const Cx<T> *__res
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         const int k = t + m * NT;
-        line[RowPad<L>::at(k)] = active ? in[k] : Cx<T>{(T)0, (T)0};
+        line[RowPad<L>::at(k)] = active ? ld_cx<CG>(in + k) : Cx<T>{(T)0, (T)0};
     }
     __syncthreads();
     // rebuild the half-length spectrum of z[m] = y[2m] + i y[2m+1]:
@@ -300,28 +304,23 @@ k_x_inverse(const Cx<T> *__restrict__ W, T *__restrict__ phi, const Cx<T> *__res
     }
 }
 
-// ---------------------------------------------------------------------
-// K2: y forward on columns; grid (ceil(Kx / TX), Nz).  Rows y >= Ny are zero
-// padding and are not read.
-// ---------------------------------------------------------------------
-template <typename T, int L>
-__global__ void __launch_bounds__(ColCfg<T, L>::THREADS)
-k_y_forward(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx)
+// K2 body: y forward of columns kx0 .. kx0 + TX - 1 of plane z.  Rows
+// y >= Ny are zero padding and are not read.
+template <typename T, int L, int TX, bool CG = false>
+__device__ __forceinline__ void y_forward_tile(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx,
+                                               int z, int kx0, Cx<T> *smem, int c, int t)
 {
-    using C = ColCfg<T, L>;
-    constexpr int E = C::E, NT = C::NT, TX = C::TX;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int c = threadIdx.x % TX, t = threadIdx.x / TX;
-    const int kx = blockIdx.x * TX + c;
+    constexpr int E = Shape<T, L>::E, NT = L / E;
+    const int kx = kx0 + c;
     const bool active = kx < Kx;
-    Cx<T> *base = W + (size_t)blockIdx.y * L * Kx + (active ? kx : 0);
+    Cx<T> *base = W + (size_t)z * L * Kx + (active ? kx : 0);
     Cx<T> v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         const int y = t + m * NT;
-        v[m] = (m < E / 2 && active && y < Ny) ? base[(size_t)y * Kx] : Cx<T>{(T)0, (T)0};
+        v[m] = (m < E / 2 && active && y < Ny) ? ld_cx<CG>(base + (size_t)y * Kx) : Cx<T>{(T)0, (T)0};
     }
-    ColXch<T, L, E, TX, TX * sizeof(Cx<T>) == 64> xch{reinterpret_cast<Cx<T> *>(smem_raw), c};
+    ColXch<T, L, E, TX, TX * sizeof(Cx<T>) == 64> xch{smem, c};
     run_stages<T, L, E, true>(v, t, tw, xch, typename Shape<T, L>::Rad{});
     if (active) {
 #pragma unroll
@@ -329,31 +328,182 @@ k_y_forward(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx)
     }
 }
 
-// ---------------------------------------------------------------------
-// K4: y inverse on columns, keeping rows y < Ny.
-// ---------------------------------------------------------------------
-template <typename T, int L>
-__global__ void __launch_bounds__(ColCfg<T, L>::THREADS)
-k_y_inverse(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx)
+// K4 body: y inverse of a column tile of plane z, keeping rows y < Ny.
+template <typename T, int L, int TX>
+__device__ __forceinline__ void y_inverse_tile(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx,
+                                               int z, int kx0, Cx<T> *smem, int c, int t)
 {
-    using C = ColCfg<T, L>;
-    constexpr int E = C::E, NT = C::NT, TX = C::TX;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int c = threadIdx.x % TX, t = threadIdx.x / TX;
-    const int kx = blockIdx.x * TX + c;
+    constexpr int E = Shape<T, L>::E, NT = L / E;
+    const int kx = kx0 + c;
     const bool active = kx < Kx;
-    Cx<T> *base = W + (size_t)blockIdx.y * L * Kx + (active ? kx : 0);
+    Cx<T> *base = W + (size_t)z * L * Kx + (active ? kx : 0);
     Cx<T> v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m)
         v[m] = active ? cswap(base[(size_t)(t + m * NT) * Kx]) : Cx<T>{(T)0, (T)0};
-    ColXch<T, L, E, TX, TX * sizeof(Cx<T>) == 64> xch{reinterpret_cast<Cx<T> *>(smem_raw), c};
+    ColXch<T, L, E, TX, TX * sizeof(Cx<T>) == 64> xch{smem, c};
     run_stages<T, L, E, false>(v, t, tw, xch, typename Shape<T, L>::Rad{});
     if (active) {
 #pragma unroll
         for (int m = 0; m < E / 2; ++m) {
             const int y = t + m * NT;
             if (y < Ny) base[(size_t)y * Kx] = cswap(v[m]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------
+// K1 / K5: x passes, RowCfg::NL rows per CTA.
+// ---------------------------------------------------------------------
+template <typename T, int L>
+__global__ void __launch_bounds__(RowCfg<T, L>::THREADS)
+k_x_forward(const T *__restrict__ src, Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw,
+            const Cx<T> *__restrict__ rtw, int Nx, int Ny, int My, int64_t nrows)
+{
+    using C = RowCfg<T, L>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int t = threadIdx.x % C::NT, l = threadIdx.x / C::NT;
+    Cx<T> *line = reinterpret_cast<Cx<T> *>(smem_raw) + l * RowPad<L>::LP;
+    const int64_t row = (int64_t)blockIdx.x * C::NL + l;  // row = z * Ny + y
+    const bool active = row < nrows;
+    x_forward_row<T, L>(src, W, tw, rtw, Nx, Ny, My, active ? row : 0, active, line, t);
+}
+
+template <typename T, int L>
+__global__ void __launch_bounds__(RowCfg<T, L>::THREADS)
+k_x_inverse(const Cx<T> *__restrict__ W, T *__restrict__ phi, const Cx<T> *__restrict__ tw,
+            const Cx<T> *__restrict__ rtw, int Nx, int Ny, int My, int64_t nrows)
+{
+    using C = RowCfg<T, L>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int t = threadIdx.x % C::NT, l = threadIdx.x / C::NT;
+    Cx<T> *line = reinterpret_cast<Cx<T> *>(smem_raw) + l * RowPad<L>::LP;
+    const int64_t row = (int64_t)blockIdx.x * C::NL + l;
+    const bool active = row < nrows;
+    x_inverse_row<T, L>(W, phi, tw, rtw, Nx, Ny, My, active ? row : 0, active, line, t);
+}
+
+// ---------------------------------------------------------------------
+// K2 / K4: y passes on column tiles; grid (ceil(Kx / TX), Nz).
+// ---------------------------------------------------------------------
+template <typename T, int L>
+__global__ void __launch_bounds__(ColCfg<T, L>::THREADS)
+k_y_forward(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx)
+{
+    using C = ColCfg<T, L>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    y_forward_tile<T, L, C::TX>(W, tw, Ny, Kx, blockIdx.y, blockIdx.x * C::TX, reinterpret_cast<Cx<T> *>(smem_raw),
+                                threadIdx.x % C::TX, threadIdx.x / C::TX);
+}
+
+template <typename T, int L>
+__global__ void __launch_bounds__(ColCfg<T, L>::THREADS)
+k_y_inverse(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx)
+{
+    using C = ColCfg<T, L>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    y_inverse_tile<T, L, C::TX>(W, tw, Ny, Kx, blockIdx.y, blockIdx.x * C::TX, reinterpret_cast<Cx<T> *>(smem_raw),
+                                threadIdx.x % C::TX, threadIdx.x / C::TX);
+}
+
+// ---------------------------------------------------------------------
+// Fused x+y forward (K12) and y+x inverse (K45) for planes with My = Mx:
+// a cluster of XY_CLUSTER CTAs owns one z plane.  Forward: each CTA
+// transforms its share of the plane's rows along x and writes them to W; a
+// cluster barrier (release/acquire at cluster scope) makes those rows
+// visible; each CTA then transforms its share of the plane's columns along y,
+// in place.  The x spectra of a plane are overwritten by the y pass
+// microseconds after they are written, so they live in L2 instead of making
+// an HBM round trip.  The inverse runs the same in reverse.
+// ---------------------------------------------------------------------
+constexpr int XY_CLUSTER = 4;
+
+template <typename T, int LX>
+struct XYCfg {
+    static constexpr int LY = 2 * LX;
+    static constexpr int THREADS = 512;
+    static constexpr int MIN_BLOCKS = sizeof(T) == 4 ? 2 : 1;  // FP32: two CTAs per SM
+    static constexpr int NTX = LX / Shape<T, LX>::E;
+    static constexpr int NL = THREADS / NTX;  // rows per round
+    static constexpr int NTY = LY / Shape<T, LY>::E;
+    static constexpr int TX = THREADS / NTY;  // columns per round
+    static constexpr size_t SMEM_X = (size_t)NL * RowPad<LX>::LP * sizeof(Cx<T>);
+    static constexpr size_t SMEM_Y = (size_t)LY * TX * sizeof(Cx<T>);
+    static constexpr size_t SMEM = SMEM_X > SMEM_Y ? SMEM_X : SMEM_Y;
+    static_assert(NTX <= THREADS && NTY <= THREADS, "line too long for a fused tile");
+};
+
+__device__ __forceinline__ void cluster_sync_release_acquire()
+{
+    __threadfence();
+    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+template <typename T, int LX>
+__global__ void __launch_bounds__(XYCfg<T, LX>::THREADS, XYCfg<T, LX>::MIN_BLOCKS)
+k_xy_forward(const T *__restrict__ src, Cx<T> *__restrict__ W, const Cx<T> *__restrict__ twx,
+             const Cx<T> *__restrict__ rtw, const Cx<T> *__restrict__ twy, int Nx, int Ny)
+{
+    using C = XYCfg<T, LX>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx<T> *sm = reinterpret_cast<Cx<T> *>(smem_raw);
+    const int z = blockIdx.x / XY_CLUSTER, r = blockIdx.x % XY_CLUSTER;
+    // rows of this CTA
+    {
+        const int t = threadIdx.x % C::NTX, l = threadIdx.x / C::NTX;
+        const int per = (Ny + XY_CLUSTER - 1) / XY_CLUSTER;
+        const int y_lo = r * per, y_hi = min(Ny, y_lo + per);
+        for (int y0 = y_lo; y0 < y_hi; y0 += C::NL) {
+            const int y = y0 + l;
+            const bool active = y < y_hi;
+            x_forward_row<T, LX>(src, W, twx, rtw, Nx, Ny, C::LY, (int64_t)z * Ny + (active ? y : y_lo), active,
+                                 sm + l * RowPad<LX>::LP, t);
+            __syncthreads();
+        }
+    }
+    cluster_sync_release_acquire();
+    // columns of this CTA
+    {
+        const int c = threadIdx.x % C::TX, t = threadIdx.x / C::TX;
+        const int tiles = (LX + C::TX - 1) / C::TX;
+        const int per = (tiles + XY_CLUSTER - 1) / XY_CLUSTER;
+        for (int xt = r * per; xt < min(tiles, (r + 1) * per); ++xt) {
+            y_forward_tile<T, C::LY, C::TX, true>(W, twy, Ny, LX, z, xt * C::TX, sm, c, t);
+            __syncthreads();
+        }
+    }
+}
+
+template <typename T, int LX>
+__global__ void __launch_bounds__(XYCfg<T, LX>::THREADS, XYCfg<T, LX>::MIN_BLOCKS)
+k_yx_inverse(Cx<T> *__restrict__ W, T *__restrict__ phi, const Cx<T> *__restrict__ twx,
+             const Cx<T> *__restrict__ rtw, const Cx<T> *__restrict__ twy, int Nx, int Ny)
+{
+    using C = XYCfg<T, LX>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx<T> *sm = reinterpret_cast<Cx<T> *>(smem_raw);
+    const int z = blockIdx.x / XY_CLUSTER, r = blockIdx.x % XY_CLUSTER;
+    {
+        const int c = threadIdx.x % C::TX, t = threadIdx.x / C::TX;
+        const int tiles = (LX + C::TX - 1) / C::TX;
+        const int per = (tiles + XY_CLUSTER - 1) / XY_CLUSTER;
+        for (int xt = r * per; xt < min(tiles, (r + 1) * per); ++xt) {
+            y_inverse_tile<T, C::LY, C::TX>(W, twy, Ny, LX, z, xt * C::TX, sm, c, t);
+            __syncthreads();
+        }
+    }
+    cluster_sync_release_acquire();
+    {
+        const int t = threadIdx.x % C::NTX, l = threadIdx.x / C::NTX;
+        const int per = (Ny + XY_CLUSTER - 1) / XY_CLUSTER;
+        const int y_lo = r * per, y_hi = min(Ny, y_lo + per);
+        for (int y0 = y_lo; y0 < y_hi; y0 += C::NL) {
+            const int y = y0 + l;
+            const bool active = y < y_hi;
+            x_inverse_row<T, LX, true>(W, phi, twx, rtw, Nx, Ny, C::LY, (int64_t)z * Ny + (active ? y : y_lo),
+                                       active, sm + l * RowPad<LX>::LP, t);
+            __syncthreads();
         }
     }
 }
