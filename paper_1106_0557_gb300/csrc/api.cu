@@ -303,8 +303,13 @@ cudaError_t enqueue_solve(ipf_plan_s *p, const void *src, void *phi, cudaStream_
     if (ev_on) cudaEventRecord(ev[3], st);
     if (fused) {
         e = launch_yx_inverse<T>(Lx, p->W, (T *)phi, p->tw_x, p->rtw, p->tw_y, Nx, Ny, Nz, st);
-        if (e != cudaSuccess) return e;
-    } else {
+        if (e != cudaSuccess) {
+            cudaGetLastError();  // refused: finish this solve, and later ones, with the separate passes
+            p->fuse_xy = false;
+            fused = false;
+        }
+    }
+    if (!fused) {
         e = launch_y_inverse<T>(My, p->W, p->tw_y, Ny, Lx, Nz, st);
         if (e != cudaSuccess) return e;
     }
@@ -386,7 +391,9 @@ int ipf_plan_create(ipf_plan_t *out, const int64_t n[3], const double h[3], int 
     p->flags = flags;
     {
         const char *fz = getenv("ISOFFT_FUSE_XY");
-        p->fuse_xy = p->M[0] == p->M[1] && fz && fz[0] == '1';
+        const int lx = (int)(p->M[0] / 2);
+        const bool fits = dtype == IPF_F32 ? xy_fusable<float>(lx) : xy_fusable<double>(lx);
+        p->fuse_xy = p->M[0] == p->M[1] && fits && fz && fz[0] == '1';
     }
     p->verbosity = verbosity;
     p->spec = nullptr;

@@ -315,6 +315,91 @@ ISOFFT_HD void run_stages(Cx<T> (&v)[E], int t, const Cx<T> *__restrict__ tw, Xc
     run_stages_impl<T, L, E, 1, HALF, Xch, Rs...>(v, t, tw, xch);
 }
 
+// ---------------------------------------------------------------------
+// Register-resident twiddles.  A thread's twiddles depend only on its line
+// position t, so a persistent kernel loads them once and reuses them for
+// every tile.  Stage s keeps w[q][r-1] = W_L^{r k step} for its butterflies
+// q; when every butterfly of the thread has the same k (NT a multiple of
+// NS) only one set is kept.
+// ---------------------------------------------------------------------
+template <typename T, int L, int E, int NS, int... Rs>
+struct TwRegs {
+    ISOFFT_HD void load(const Cx<T> *__restrict__, int) {}
+};
+template <typename T, int L, int E, int NS, int R, int... Rest>
+struct TwRegs<T, L, E, NS, R, Rest...> {
+    static constexpr int NT = L / E, B = E / R;
+    static constexpr bool SHARED = NS > 1 && NT % NS == 0;
+    static constexpr int NQ = NS == 1 ? 1 : (SHARED ? 1 : B);
+    Cx<T> w[NQ][R - 1];
+    TwRegs<T, L, E, NS * R, Rest...> next;
+    ISOFFT_HD void load(const Cx<T> *__restrict__ tw, int t)
+    {
+        if constexpr (NS > 1) {
+            constexpr int step = L / (NS * R);
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const int k = (t + q * NT) % NS;
+#pragma unroll
+                for (int r = 1; r < R; ++r) w[q][r - 1] = tw[r * k * step];
+            }
+        }
+        next.load(tw, t);
+    }
+    ISOFFT_HD Cx<T> get(int q, int r) const { return w[SHARED ? 0 : q][r - 1]; }
+};
+
+// Stage with twiddles from registers (same arithmetic as `stage`).
+template <typename T, int L, int E, int NS, int R, bool HALF, typename TWR>
+ISOFFT_HD void stage_reg(Cx<T> (&v)[E], const TWR &twr)
+{
+    using G = StageGeom<L, E, NS, R>;
+#pragma unroll
+    for (int q = 0; q < G::B; ++q) {
+        Cx<T> a[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) a[r] = v[q + r * G::B];
+        if constexpr (NS > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) a[r] = cmul(a[r], twr.get(q, r));
+        }
+        if constexpr (HALF) {
+            static_assert(NS == 1, "pruned butterflies only in the first stage");
+            DftHalf<T, R>::run(a);
+        } else {
+            Dft<T, R>::run(a);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[q + r * G::B] = a[r];
+    }
+}
+
+template <typename T, int L, int E, int NS, bool HALF, typename Xch, typename TWR, int R, int... Rest>
+ISOFFT_HD void run_stages_reg_impl(Cx<T> (&v)[E], int t, const TWR &twr, Xch &xch)
+{
+    stage_reg<T, L, E, NS, R, HALF>(v, twr);
+    if constexpr (sizeof...(Rest) > 0) {
+        xch.template exchange<NS, R>(v, t);
+        run_stages_reg_impl<T, L, E, NS * R, false, Xch, decltype(twr.next), Rest...>(v, t, twr.next, xch);
+    }
+}
+
+template <typename T, int L, int E, int... Rs>
+using TwRegsFor = TwRegs<T, L, E, 1, Rs...>;
+
+template <typename T, int L, int E, bool HALF, typename Xch, typename TWR, int... Rs>
+ISOFFT_HD void run_stages_reg(Cx<T> (&v)[E], int t, const TWR &twr, Xch &xch, Radices<Rs...>)
+{
+    run_stages_reg_impl<T, L, E, 1, HALF, Xch, TWR, Rs...>(v, t, twr, xch);
+}
+
+template <typename T, int L, int E, typename Rad>
+struct TwRegsOf;
+template <typename T, int L, int E, int... Rs>
+struct TwRegsOf<T, L, E, Radices<Rs...>> {
+    using type = TwRegs<T, L, E, 1, Rs...>;
+};
+
 // Per-length configuration: points per thread E and the radix sequence.
 // Eight (or twelve for lengths with a factor 3) points per thread keep the
 // register footprint small enough for a next-tile prefetch; 1024-point

@@ -34,6 +34,8 @@ cudaError_t launch_z_convolve(int L, void *W, const void *tw, const T *G, const 
 // Fused x+y forward / y+x inverse for planes with My = Mx = 2 LX: one
 // cluster of 4 CTAs per z plane (see passes.cuh).
 template <typename T>
+bool xy_fusable(int LX);  // both fused kernels exist and fit for this LX
+template <typename T>
 cudaError_t launch_xy_forward(int LX, const T *src, void *W, const void *twx, const void *rtw, const void *twy,
                               int Nx, int Ny, int Nz, cudaStream_t st);
 template <typename T>

@@ -199,12 +199,11 @@ __device__ __forceinline__ Cx<T> ld_cx(const Cx<T> *p)
 // K1 body: row rr = z * Ny + y of the source, real -> packed half spectrum.
 // tw: W_L^k (k < L), rtw: W_{2L}^k (k < L), L = Mx / 2.
 template <typename T, int L>
-__device__ __forceinline__ void x_forward_row(const T *__restrict__ src, Cx<T> *__restrict__ W,
-                                              const Cx<T> *__restrict__ tw, const Cx<T> *__restrict__ rtw, int Nx,
-                                              int Ny, int My, int64_t rr, bool active, Cx<T> *line, int t)
+__device__ __forceinline__ void x_forward_row_at(const T *in, Cx<T> *__restrict__ out, const Cx<T> *__restrict__ tw,
+                                                 const Cx<T> *__restrict__ rtw, int Nx, bool active, Cx<T> *line,
+                                                 int t)
 {
     constexpr int E = Shape<T, L>::E, NT = L / E;
-    const T *in = src + rr * Nx;
 
     // pairs (x[2p], x[2p+1]) as one complex point; p >= L/2 is padding
     Cx<T> v[E];
@@ -231,9 +230,6 @@ __device__ __forceinline__ void x_forward_row(const T *__restrict__ src, Cx<T> *
 #pragma unroll
     for (int m = 0; m < E; ++m) line[RowPad<L>::at(t + m * NT)] = v[m];
     __syncthreads();
-    const int y = (int)(rr % Ny);
-    const int64_t z = rr / Ny;
-    Cx<T> *out = W + ((size_t)z * My + y) * L;
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         const int k = t + m * NT;
@@ -247,17 +243,23 @@ __device__ __forceinline__ void x_forward_row(const T *__restrict__ src, Cx<T> *
     }
 }
 
-// K5 body: packed half spectrum of row rr -> real row, cropped to x < Nx.
-template <typename T, int L, bool CG = false>
-__device__ __forceinline__ void x_inverse_row(const Cx<T> *__restrict__ W, T *__restrict__ phi,
+template <typename T, int L>
+__device__ __forceinline__ void x_forward_row(const T *__restrict__ src, Cx<T> *__restrict__ W,
                                               const Cx<T> *__restrict__ tw, const Cx<T> *__restrict__ rtw, int Nx,
                                               int Ny, int My, int64_t rr, bool active, Cx<T> *line, int t)
 {
-    constexpr int E = Shape<T, L>::E, NT = L / E;
     const int y = (int)(rr % Ny);
     const int64_t z = rr / Ny;
-    const Cx<T> *in = W + ((size_t)z * My + y) * L;
+    x_forward_row_at<T, L>(src + rr * Nx, W + ((size_t)z * My + y) * L, tw, rtw, Nx, active, line, t);
+}
 
+// K5 body: packed half spectrum of row rr -> real row, cropped to x < Nx.
+template <typename T, int L, bool CG = false>
+__device__ __forceinline__ void x_inverse_row_at(const Cx<T> *in, T *__restrict__ out, const Cx<T> *__restrict__ tw,
+                                                 const Cx<T> *__restrict__ rtw, int Nx, bool active, Cx<T> *line,
+                                                 int t)
+{
+    constexpr int E = Shape<T, L>::E, NT = L / E;
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         const int k = t + m * NT;
@@ -288,7 +290,6 @@ __device__ __forceinline__ void x_inverse_row(const Cx<T> *__restrict__ W, T *__
     for (int m = 0; m < E; ++m) v[m] = cswap(v[m]);
     RowXch<T, L, E> xch{line};
     run_stages<T, L, E, false>(v, t, tw, xch, typename Shape<T, L>::Rad{});
-    T *out = phi + rr * Nx;
     const bool vec = (Nx & 1) == 0;
 #pragma unroll
     for (int m = 0; m < E / 2; ++m) {
@@ -304,11 +305,22 @@ __device__ __forceinline__ void x_inverse_row(const Cx<T> *__restrict__ W, T *__
     }
 }
 
+template <typename T, int L, bool CG = false>
+__device__ __forceinline__ void x_inverse_row(const Cx<T> *__restrict__ W, T *__restrict__ phi,
+                                              const Cx<T> *__restrict__ tw, const Cx<T> *__restrict__ rtw, int Nx,
+                                              int Ny, int My, int64_t rr, bool active, Cx<T> *line, int t)
+{
+    const int y = (int)(rr % Ny);
+    const int64_t z = rr / Ny;
+    x_inverse_row_at<T, L, CG>(W + ((size_t)z * My + y) * L, phi + rr * Nx, tw, rtw, Nx, active, line, t);
+}
+
 // K2 body: y forward of columns kx0 .. kx0 + TX - 1 of plane z.  Rows
 // y >= Ny are zero padding and are not read.
 template <typename T, int L, int TX, bool CG = false>
 __device__ __forceinline__ void y_forward_tile(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx,
-                                               int z, int kx0, Cx<T> *smem, int c, int t)
+                                               int z, int kx0, Cx<T> *smem, int c, int t,
+                                               const Cx<T> *staged = nullptr)
 {
     constexpr int E = Shape<T, L>::E, NT = L / E;
     const int kx = kx0 + c;
@@ -318,7 +330,11 @@ __device__ __forceinline__ void y_forward_tile(Cx<T> *__restrict__ W, const Cx<T
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         const int y = t + m * NT;
-        v[m] = (m < E / 2 && active && y < Ny) ? ld_cx<CG>(base + (size_t)y * Kx) : Cx<T>{(T)0, (T)0};
+        const bool ok = m < E / 2 && active && y < Ny;
+        if (staged)
+            v[m] = ok ? staged[y * TX + c] : Cx<T>{(T)0, (T)0};
+        else
+            v[m] = ok ? ld_cx<CG>(base + (size_t)y * Kx) : Cx<T>{(T)0, (T)0};
     }
     ColXch<T, L, E, TX, TX * sizeof(Cx<T>) == 64> xch{smem, c};
     run_stages<T, L, E, true>(v, t, tw, xch, typename Shape<T, L>::Rad{});
@@ -331,7 +347,8 @@ __device__ __forceinline__ void y_forward_tile(Cx<T> *__restrict__ W, const Cx<T
 // K4 body: y inverse of a column tile of plane z, keeping rows y < Ny.
 template <typename T, int L, int TX>
 __device__ __forceinline__ void y_inverse_tile(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx,
-                                               int z, int kx0, Cx<T> *smem, int c, int t)
+                                               int z, int kx0, Cx<T> *smem, int c, int t,
+                                               const Cx<T> *staged = nullptr)
 {
     constexpr int E = Shape<T, L>::E, NT = L / E;
     const int kx = kx0 + c;
@@ -339,8 +356,13 @@ __device__ __forceinline__ void y_inverse_tile(Cx<T> *__restrict__ W, const Cx<T
     Cx<T> *base = W + (size_t)z * L * Kx + (active ? kx : 0);
     Cx<T> v[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m)
-        v[m] = active ? cswap(base[(size_t)(t + m * NT) * Kx]) : Cx<T>{(T)0, (T)0};
+    for (int m = 0; m < E; ++m) {
+        const int y = t + m * NT;
+        if (staged)
+            v[m] = active ? cswap(staged[y * TX + c]) : Cx<T>{(T)0, (T)0};
+        else
+            v[m] = active ? cswap(base[(size_t)y * Kx]) : Cx<T>{(T)0, (T)0};
+    }
     ColXch<T, L, E, TX, TX * sizeof(Cx<T>) == 64> xch{smem, c};
     run_stages<T, L, E, false>(v, t, tw, xch, typename Shape<T, L>::Rad{});
     if (active) {
@@ -427,10 +449,22 @@ struct XYCfg {
     static constexpr int NL = THREADS / NTX;  // rows per round
     static constexpr int NTY = LY / Shape<T, LY>::E;
     static constexpr int TX = THREADS / NTY;  // columns per round
-    static constexpr size_t SMEM_X = (size_t)NL * RowPad<LX>::LP * sizeof(Cx<T>);
-    static constexpr size_t SMEM_Y = (size_t)LY * TX * sizeof(Cx<T>);
-    static constexpr size_t SMEM = SMEM_X > SMEM_Y ? SMEM_X : SMEM_Y;
     static_assert(NTX <= THREADS && NTY <= THREADS, "line too long for a fused tile");
+    static constexpr size_t CS = sizeof(Cx<T>);
+    // exchange buffers of the two phases
+    static constexpr size_t XCH_X = (size_t)NL * RowPad<LX>::LP * CS;
+    static constexpr size_t XCH_Y = (size_t)LY * TX * CS;
+    // one stage of prefetched input (each phase double-buffers its stage)
+    static constexpr size_t ROWS_F = (size_t)NL * LX * sizeof(T);  // real source rows
+    static constexpr size_t ROWS_I = (size_t)NL * LX * CS;         // packed half-spectrum rows
+    static constexpr size_t COLS_F = (size_t)LX * TX * CS;         // half columns (y < My/2)
+    static constexpr size_t COLS_I = (size_t)LY * TX * CS;         // whole columns
+    static constexpr size_t mx(size_t a, size_t b) { return a > b ? a : b; }
+    static constexpr size_t SMEM_F = mx(XCH_X + 2 * ROWS_F, XCH_Y + 2 * COLS_F);
+    static constexpr size_t SMEM_I = mx(XCH_Y + 2 * COLS_I, XCH_X + 2 * ROWS_I);
+    // fused only where both kernels fit one SM's shared memory and a round
+    // is not a crowd of tiny rows
+    static constexpr bool OK = LX >= 64 && SMEM_F <= 227 * 1024 && SMEM_I <= 227 * 1024;
 };
 
 __device__ __forceinline__ void cluster_sync_release_acquire()
@@ -440,38 +474,116 @@ __device__ __forceinline__ void cluster_sync_release_acquire()
     asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
 
+// Runs `rounds` rounds of `compute(j, buf)`, with round j + 1's inputs copied
+// by `issue(j + 1, buf')` into the other of two staging buffers while round j
+// computes.  All threads of the CTA call it with the same `rounds`.
+template <typename Issue, typename Compute>
+__device__ __forceinline__ void pipelined_rounds(int rounds, Issue issue, Compute compute)
+{
+    if (rounds > 0) issue(0, 0);
+    cp_async_commit();
+    for (int j = 0; j < rounds; ++j) {
+        if (j + 1 < rounds) issue(j + 1, (j + 1) & 1);
+        cp_async_commit();
+        cp_async_wait<1>();  // round j's copies have landed
+        __syncthreads();     // ... everyone's
+        compute(j, j & 1);
+        __syncthreads();     // buffer j & 1 is free for round j + 2
+    }
+    cp_async_wait<0>();
+}
+
+// Copy `rows` rows of `bytes` each (row r from src_row(r)) into consecutive
+// staging rows of `stride` bytes, 16 bytes per copy when every row start and
+// length allow it, else `es` bytes per copy.
+// A row whose source is null is zero-filled (nothing is read; `safe`, a
+// valid global address, stands in as the operand).
+template <int ES, typename SrcRow>
+__device__ __forceinline__ void stage_rows(unsigned char *dst, size_t stride, int rows, int bytes, SrcRow src_row,
+                                           bool vec16, const void *safe)
+{
+    const unsigned char *sf = reinterpret_cast<const unsigned char *>(safe);
+    if (vec16) {
+        const int per = bytes / 16;
+        for (int i = threadIdx.x; i < rows * per; i += blockDim.x) {
+            const int r = i / per, k = i - r * per;
+            const unsigned char *s = src_row(r);
+            cp_async<16>(dst + r * stride + 16 * k, s ? s + 16 * k : sf, s != nullptr);
+        }
+    } else {
+        const int per = bytes / ES;
+        for (int i = threadIdx.x; i < rows * per; i += blockDim.x) {
+            const int r = i / per, k = i - r * per;
+            const unsigned char *s = src_row(r);
+            cp_async<ES>(dst + r * stride + ES * k, s ? s + ES * k : sf, s != nullptr);
+        }
+    }
+}
+
 template <typename T, int LX>
 __global__ void __launch_bounds__(XYCfg<T, LX>::THREADS, XYCfg<T, LX>::MIN_BLOCKS)
 k_xy_forward(const T *__restrict__ src, Cx<T> *__restrict__ W, const Cx<T> *__restrict__ twx,
              const Cx<T> *__restrict__ rtw, const Cx<T> *__restrict__ twy, int Nx, int Ny)
 {
     using C = XYCfg<T, LX>;
+    constexpr int LY = C::LY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Cx<T> *sm = reinterpret_cast<Cx<T> *>(smem_raw);
+    Cx<T> *xch = reinterpret_cast<Cx<T> *>(smem_raw);
     const int z = blockIdx.x / XY_CLUSTER, r = blockIdx.x % XY_CLUSTER;
-    // rows of this CTA
+
+    // phase 1: this CTA's rows along x, source rows prefetched
     {
+        unsigned char *stage = smem_raw + C::XCH_X;
         const int t = threadIdx.x % C::NTX, l = threadIdx.x / C::NTX;
         const int per = (Ny + XY_CLUSTER - 1) / XY_CLUSTER;
         const int y_lo = r * per, y_hi = min(Ny, y_lo + per);
-        for (int y0 = y_lo; y0 < y_hi; y0 += C::NL) {
-            const int y = y0 + l;
+        const int rounds = y_hi > y_lo ? (y_hi - y_lo + C::NL - 1) / C::NL : 0;
+        const bool vec16 = ((size_t)Nx * sizeof(T)) % 16 == 0;
+        auto issue = [&](int j, int buf) {
+            const int y0 = y_lo + j * C::NL;
+            stage_rows<sizeof(T)>(
+                stage + buf * C::ROWS_F, LX * sizeof(T), C::NL, Nx * (int)sizeof(T),
+                [&](int rr) -> const unsigned char * {
+                    const int y = y0 + rr;
+                    return y < y_hi ? reinterpret_cast<const unsigned char *>(src + ((size_t)z * Ny + y) * Nx)
+                                    : nullptr;
+                },
+                vec16, src);
+        };
+        auto compute = [&](int j, int buf) {
+            const int y = y_lo + j * C::NL + l;
             const bool active = y < y_hi;
-            x_forward_row<T, LX>(src, W, twx, rtw, Nx, Ny, C::LY, (int64_t)z * Ny + (active ? y : y_lo), active,
-                                 sm + l * RowPad<LX>::LP, t);
-            __syncthreads();
-        }
+            const T *in = reinterpret_cast<const T *>(stage + buf * C::ROWS_F) + l * LX;
+            x_forward_row_at<T, LX>(in, W + ((size_t)z * LY + (active ? y : y_lo)) * LX, twx, rtw, Nx, active,
+                                    xch + l * RowPad<LX>::LP, t);
+        };
+        pipelined_rounds(rounds, issue, compute);
     }
     cluster_sync_release_acquire();
-    // columns of this CTA
+    // phase 2: this CTA's columns along y, half columns prefetched from L2
     {
+        unsigned char *stage = smem_raw + C::XCH_Y;
         const int c = threadIdx.x % C::TX, t = threadIdx.x / C::TX;
         const int tiles = (LX + C::TX - 1) / C::TX;
         const int per = (tiles + XY_CLUSTER - 1) / XY_CLUSTER;
-        for (int xt = r * per; xt < min(tiles, (r + 1) * per); ++xt) {
-            y_forward_tile<T, C::LY, C::TX, true>(W, twy, Ny, LX, z, xt * C::TX, sm, c, t);
-            __syncthreads();
-        }
+        const int xt_lo = r * per, xt_hi = min(tiles, xt_lo + per);
+        const int rounds = xt_hi > xt_lo ? xt_hi - xt_lo : 0;
+        const int kx_n = min(C::TX, LX);  // columns of a tile inside the mesh
+        const bool vec16 = (kx_n * C::CS) % 16 == 0;
+        auto issue = [&](int j, int buf) {
+            const int kx0 = (xt_lo + j) * C::TX;
+            stage_rows<sizeof(Cx<T>)>(
+                stage + buf * C::COLS_F, C::TX * C::CS, Ny, kx_n * (int)C::CS,
+                [&](int y) -> const unsigned char * {
+                    return reinterpret_cast<const unsigned char *>(W + ((size_t)z * LY + y) * LX + kx0);
+                },
+                vec16, W);
+        };
+        auto compute = [&](int j, int buf) {
+            y_forward_tile<T, LY, C::TX>(W, twy, Ny, LX, z, (xt_lo + j) * C::TX, xch, c, t,
+                                         reinterpret_cast<const Cx<T> *>(stage + buf * C::COLS_F));
+        };
+        pipelined_rounds(rounds, issue, compute);
     }
 }
 
@@ -481,30 +593,63 @@ k_yx_inverse(Cx<T> *__restrict__ W, T *__restrict__ phi, const Cx<T> *__restrict
              const Cx<T> *__restrict__ rtw, const Cx<T> *__restrict__ twy, int Nx, int Ny)
 {
     using C = XYCfg<T, LX>;
+    constexpr int LY = C::LY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Cx<T> *sm = reinterpret_cast<Cx<T> *>(smem_raw);
+    Cx<T> *xch = reinterpret_cast<Cx<T> *>(smem_raw);
     const int z = blockIdx.x / XY_CLUSTER, r = blockIdx.x % XY_CLUSTER;
+
+    // phase 1: this CTA's columns along y, whole columns prefetched
     {
+        unsigned char *stage = smem_raw + C::XCH_Y;
         const int c = threadIdx.x % C::TX, t = threadIdx.x / C::TX;
         const int tiles = (LX + C::TX - 1) / C::TX;
         const int per = (tiles + XY_CLUSTER - 1) / XY_CLUSTER;
-        for (int xt = r * per; xt < min(tiles, (r + 1) * per); ++xt) {
-            y_inverse_tile<T, C::LY, C::TX>(W, twy, Ny, LX, z, xt * C::TX, sm, c, t);
-            __syncthreads();
-        }
+        const int xt_lo = r * per, xt_hi = min(tiles, xt_lo + per);
+        const int rounds = xt_hi > xt_lo ? xt_hi - xt_lo : 0;
+        const int kx_n = min(C::TX, LX);
+        const bool vec16 = (kx_n * C::CS) % 16 == 0;
+        auto issue = [&](int j, int buf) {
+            const int kx0 = (xt_lo + j) * C::TX;
+            stage_rows<sizeof(Cx<T>)>(
+                stage + buf * C::COLS_I, C::TX * C::CS, LY, kx_n * (int)C::CS,
+                [&](int y) -> const unsigned char * {
+                    return reinterpret_cast<const unsigned char *>(W + ((size_t)z * LY + y) * LX + kx0);
+                },
+                vec16, W);
+        };
+        auto compute = [&](int j, int buf) {
+            y_inverse_tile<T, LY, C::TX>(W, twy, Ny, LX, z, (xt_lo + j) * C::TX, xch, c, t,
+                                         reinterpret_cast<const Cx<T> *>(stage + buf * C::COLS_I));
+        };
+        pipelined_rounds(rounds, issue, compute);
     }
     cluster_sync_release_acquire();
+    // phase 2: this CTA's rows along x, packed rows prefetched from L2
     {
+        unsigned char *stage = smem_raw + C::XCH_X;
         const int t = threadIdx.x % C::NTX, l = threadIdx.x / C::NTX;
         const int per = (Ny + XY_CLUSTER - 1) / XY_CLUSTER;
         const int y_lo = r * per, y_hi = min(Ny, y_lo + per);
-        for (int y0 = y_lo; y0 < y_hi; y0 += C::NL) {
-            const int y = y0 + l;
+        const int rounds = y_hi > y_lo ? (y_hi - y_lo + C::NL - 1) / C::NL : 0;
+        auto issue = [&](int j, int buf) {
+            const int y0 = y_lo + j * C::NL;
+            stage_rows<sizeof(Cx<T>)>(
+                stage + buf * C::ROWS_I, LX * C::CS, C::NL, LX * (int)C::CS,
+                [&](int rr) -> const unsigned char * {
+                    const int y = y0 + rr;
+                    return y < y_hi ? reinterpret_cast<const unsigned char *>(W + ((size_t)z * LY + y) * LX)
+                                    : nullptr;
+                },
+                true, W);
+        };
+        auto compute = [&](int j, int buf) {
+            const int y = y_lo + j * C::NL + l;
             const bool active = y < y_hi;
-            x_inverse_row<T, LX, true>(W, phi, twx, rtw, Nx, Ny, C::LY, (int64_t)z * Ny + (active ? y : y_lo),
-                                       active, sm + l * RowPad<LX>::LP, t);
-            __syncthreads();
-        }
+            const Cx<T> *in = reinterpret_cast<const Cx<T> *>(stage + buf * C::ROWS_I) + l * LX;
+            x_inverse_row_at<T, LX>(in, phi + ((size_t)z * Ny + (active ? y : y_lo)) * Nx, twx, rtw, Nx, active,
+                                    xch + l * RowPad<LX>::LP, t);
+        };
+        pipelined_rounds(rounds, issue, compute);
     }
 }
 
@@ -574,6 +719,9 @@ k_z_convolve(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, const T *__res
     };
 
     ColXch<T, L, E, COLS> xch{sm, col};
+    using Rad = typename ZShape<T, L>::Rad;
+    typename TwRegsOf<T, L, E, Rad>::type twr;  // this thread's twiddles, for every tile
+    twr.load(tw, t);
     int tile = blockIdx.x;
     if (tile < ntiles) {
         stage_input(tile);
@@ -595,7 +743,7 @@ k_z_convolve(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, const T *__res
         if (next < ntiles) stage_input(next);
         cp_async_commit();
 
-        run_stages<T, L, E, true>(v, t, tw, xch, typename ZShape<T, L>::Rad{});
+        run_stages_reg<T, L, E, true>(v, t, twr, xch, Rad{});
 
         cp_async_wait<1>();  // this tile's spectrum has landed
         const bool packed = xt == 0 && c == 0;  // the kx = 0 / Mx/2 column
@@ -630,7 +778,7 @@ k_z_convolve(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, const T *__res
 
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = cswap(v[m]);
-        run_stages<T, L, E, false>(v, t, tw, xch, typename ZShape<T, L>::Rad{});
+        run_stages_reg<T, L, E, false>(v, t, twr, xch, Rad{});
         if (active) {
             Cx<T> *base = W + (size_t)ky * Kx + kx;
 #pragma unroll

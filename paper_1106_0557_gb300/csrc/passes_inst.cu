@@ -164,10 +164,11 @@ static cudaError_t run_xy(const T *src, void *W, const void *twx, const void *rt
                           int Nz, cudaStream_t st)
 {
     using C = XYCfg<T, LX>;
+    if (!C::OK) return cudaErrorNotSupported;
     static std::atomic<uint64_t> done{0};
-    cudaError_t e = ensure_smem(k_xy_forward<T, LX>, C::SMEM, done);
+    cudaError_t e = ensure_smem(k_xy_forward<T, LX>, C::SMEM_F, done);
     if (e != cudaSuccess) return e;
-    e = launch_cluster(k_xy_forward<T, LX>, (unsigned)(XY_CLUSTER * Nz), C::THREADS, C::SMEM, st, src,
+    e = launch_cluster(k_xy_forward<T, LX>, (unsigned)(XY_CLUSTER * Nz), C::THREADS, C::SMEM_F, st, src,
                        (Cx<T> *)W, (const Cx<T> *)twx, (const Cx<T> *)rtw, (const Cx<T> *)twy, Nx, Ny);
     if (e == cudaSuccess) count_launch();
     return e;
@@ -177,10 +178,11 @@ static cudaError_t run_yx(void *W, T *phi, const void *twx, const void *rtw, con
                           cudaStream_t st)
 {
     using C = XYCfg<T, LX>;
+    if (!C::OK) return cudaErrorNotSupported;
     static std::atomic<uint64_t> done{0};
-    cudaError_t e = ensure_smem(k_yx_inverse<T, LX>, C::SMEM, done);
+    cudaError_t e = ensure_smem(k_yx_inverse<T, LX>, C::SMEM_I, done);
     if (e != cudaSuccess) return e;
-    e = launch_cluster(k_yx_inverse<T, LX>, (unsigned)(XY_CLUSTER * Nz), C::THREADS, C::SMEM, st, (Cx<T> *)W, phi,
+    e = launch_cluster(k_yx_inverse<T, LX>, (unsigned)(XY_CLUSTER * Nz), C::THREADS, C::SMEM_I, st, (Cx<T> *)W, phi,
                        (const Cx<T> *)twx, (const Cx<T> *)rtw, (const Cx<T> *)twy, Nx, Ny);
     if (e == cudaSuccess) count_launch();
     return e;
@@ -209,6 +211,18 @@ cudaError_t launch_yx_inverse(int LX, void *W, R_ *phi, const void *twx, const v
     default: return cudaErrorInvalidValue;
     }
 }
+template <typename R_>
+bool xy_fusable(int LX)
+{
+    switch (LX) {
+#define X_(n) \
+    case n: return XYCfg<R_, n>::OK;
+        ISOFFT_ROW_LENGTHS(X_)
+#undef X_
+    default: return false;
+    }
+}
+template bool xy_fusable<Real>(int);
 template cudaError_t launch_xy_forward<Real>(int, const Real *, void *, const void *, const void *, const void *,
                                              int, int, int, cudaStream_t);
 template cudaError_t launch_yx_inverse<Real>(int, void *, Real *, const void *, const void *, const void *, int,

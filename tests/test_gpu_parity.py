@@ -244,7 +244,7 @@ def test_batch_graph_replay_matches_single_solves():
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
-@pytest.mark.parametrize("N", [(64, 64, 64), (40, 37, 13), (256, 200, 31), (7, 5, 3)])
+@pytest.mark.parametrize("N", [(64, 64, 64), (60, 50, 13), (256, 200, 31), (500, 400, 7)])
 def test_fused_xy_passes_equal_separate_passes(N, dtype, monkeypatch):
     """Planes with My = Mx run the x and y passes fused in one cluster
     kernel per direction; the result is bitwise that of the separate
