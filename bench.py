@@ -385,7 +385,7 @@ def run_isofft(args, ws, rank, local):
     stream = torch.cuda.current_stream()
 
     def timed_solves(dtype, steps, warmup, pool=4):
-        tdt = torch.float32 if dtype == "f32" else torch.float64
+        tdt = torch.float32 if dtype == "f32" else torch.float64  # df64 reads and writes FP64 arrays
         plan = Plan(N, w.h, dtype, flags=native.IPF_FLAG_PASS_EVENTS)
         base = torch.from_numpy(src64).to(dev, tdt)
         srcs = [base.clone() for _ in range(pool)]
@@ -444,6 +444,15 @@ def run_isofft(args, ws, rank, local):
     gbs64 = sum(kernel_times(passes64, bytes64, fused)[k]["bytes"] for k in kernel_times(passes64, bytes64, fused)) / (
         ms64 / steps64 / 1e3) / 1e9
 
+    # FP64-class float pairs on the FP32 units (same FP64 buffers)
+    stepsdf = max(3, args.steps // 4)
+    msdf, _, passesdf, _, finitedf = timed_solves("df64", stepsdf, max(3, args.warmup // 4))
+    msdf = reduce_max(msdf, ws, dev)
+    valuedf = reduce_sum(stepsdf, ws, dev) / (msdf / 1e3)
+    bytesdf = pass_bytes(N, M, 8)
+    kdf = kernel_times(passesdf, bytesdf, fused)
+    gbsdf = sum(kdf[k]["bytes"] for k in kdf) / (msdf / stepsdf / 1e3) / 1e9
+
     # end to end through the public host-buffer entry point
     plan = Plan(N, w.h, "f32")
     hsrc = torch.from_numpy(src64.astype(np.float32)).pin_memory()
@@ -497,6 +506,10 @@ def run_isofft(args, ws, rank, local):
         "hbm_gbs": round(gbs32, 1),
         "fp64": {"value": value64, "unit": "solves/s", "ms_per_step": ms64 / steps64, "steps": steps64,
                  "hbm_gbs": round(gbs64, 1)},
+        "df64": {"value": valuedf, "unit": "solves/s", "ms_per_step": msdf / stepsdf, "steps": stepsdf,
+                 "hbm_gbs": round(gbsdf, 1), "what": "FP64-class float-pair arithmetic on the FP32 units, "
+                 "FP64 buffers, tolerance 1e-12",
+                 "kernels": {k: {"ms": round(v["ms"], 5), "gbs": round(v["gbs"], 1)} for k, v in kdf.items()}},
         "kernels": per_kernel,
         "roofline": {"bound": "hbm", "kernel": dname, "achieved": round(achieved, 1), "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
@@ -508,7 +521,7 @@ def run_isofft(args, ws, rank, local):
         "cpu_baseline": cpu,
         "gpu_launches": launches,
         "clocks": clocks,
-        "finite": finite32 and finite64,
+        "finite": finite32 and finite64 and finitedf,
     }
     print(json.dumps(line), flush=True)
 

@@ -17,7 +17,7 @@
  * Conventions shared by every entry point:
  *   - Arrays are C order [z][y][x], x contiguous (the paper's first Fortran
  *     index is x, Sec. 3.2), of `float` for IPF_F32 plans and `double` for
- *     IPF_F64 plans.  Device buffers must be 16-byte aligned.
+ *     IPF_F64 and IPF_DF64 plans.  Device buffers must be 16-byte aligned.
  *   - Device pointers are CUDA device (or managed) memory of the calling
  *     thread's current device; host pointers are ordinary host memory
  *     (pinned memory makes the copies faster but is not required).
@@ -42,8 +42,17 @@ extern "C" {
 
 typedef struct ipf_plan_s *ipf_plan_t;
 
-/* arithmetic type of a plan's buffers and butterflies */
-typedef enum { IPF_F32 = 0, IPF_F64 = 1 } ipf_dtype;
+/* Arithmetic type of a plan's butterflies (and of its buffers).
+ *   IPF_F32   float buffers, FP32 arithmetic.
+ *   IPF_F64   double buffers, FP64 arithmetic.
+ *   IPF_DF64  double buffers, FP64-class arithmetic on the FP32 units: each
+ *             value is a pair of floats (hi + lo, about 48 significant bits),
+ *             added with Knuth's two-sum and multiplied with a fused
+ *             multiply-add error term.  Not in the paper; it is a precision
+ *             variant of the same path for GPUs whose FP64 rate is a small
+ *             fraction of their FP32 rate.  The Green's spectrum is built in
+ *             FP64 and split into float pairs. */
+typedef enum { IPF_F32 = 0, IPF_F64 = 1, IPF_DF64 = 2 } ipf_dtype;
 
 typedef enum {
     IPF_OK = 0,
@@ -73,8 +82,8 @@ enum {
  *   n          {Nx, Ny, Nz}, each >= 1; the doubled mesh 2N must fit the
  *              largest supported length (1024), else IPF_UNSUPPORTED_SIZE.
  *   h          {hx, hy, hz}, each finite and > 0.
- *   dtype      IPF_F32 or IPF_F64.  The Green's spectrum is always built in
- *              FP64 and rounded to the plan's dtype.
+ *   dtype      IPF_F32, IPF_F64 or IPF_DF64.  The Green's spectrum is always
+ *              built in FP64 and rounded to the plan's dtype.
  *   flags      a bitwise OR of IPF_FLAG_*.
  *   verbosity  an IPF_CONSOLE_* level.
  *   stream     stream used for the one-off set-up work (Green's spectrum
@@ -121,7 +130,8 @@ int ipf_solve_host(ipf_plan_t plan, const void *h_src, void *h_phi, void *stream
  * time-step loop that must not take the device-wide synchronisation an
  * allocation or free may imply.  The paper has no counterpart; it is a
  * deployment variant of ipf_solve.
- *   n, h, dtype  as for ipf_plan_create (no plan is needed).
+ *   n, h, dtype  as for ipf_plan_create (no plan is needed; IPF_F32 or
+ *                IPF_F64 only).
  *   d_src, d_phi device arrays as for ipf_solve (d_phi may equal d_src).
  * Twiddle tables, the Green's spectrum and the workspace are all carved out
  * of one static device array of 64 MiB that the library holds on every

@@ -25,7 +25,7 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxe
 
 def _units():
     units = [("api", "api.cu", []), ("greens", "greens.cu", []), ("noalloc", "noalloc.cu", [])]
-    for real, tag in (("float", "f32"), ("double", "f64")):
+    for real, tag in (("float", "f32"), ("double", "f64"), ("isofft::df64", "df64")):
         for group, gname in ((1, "x"), (2, "y"), (3, "z"), (4, "xy")):
             units.append(("passes_%s_%s" % (gname, tag), "passes_inst.cu",
                           ["-DISOFFT_REAL=%s" % real, "-DISOFFT_GROUP=%d" % group]))

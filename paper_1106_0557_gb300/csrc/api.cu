@@ -86,7 +86,9 @@ static uint64_t g_clock = 0;
 
 static size_t spectrum_bytes(const int64_t M[3], int dtype)
 {
-    return dtype == IPF_F32 ? 4 * spectrum_elems<float>(M) : 8 * spectrum_elems<double>(M);
+    if (dtype == IPF_F32) return 4 * spectrum_elems<float>(M);
+    if (dtype == IPF_F64) return 8 * spectrum_elems<double>(M);
+    return 8 * spectrum_elems<df64>(M);
 }
 
 static void free_entry(SpecEntry &e)
@@ -137,12 +139,14 @@ int64_t choose_mesh(int64_t n)
     return -1;
 }
 
+// bytes of one real of the source / potential arrays (FP64 for df64 solves);
+// a workspace complex is twice that for every dtype
 size_t elem_size(int dtype) { return dtype == IPF_F32 ? 4 : 8; }
 
 int validate(const int64_t n[3], const double h[3], int dtype)
 {
     if (!n || !h) return IPF_INVALID_ARG;
-    if (dtype != IPF_F32 && dtype != IPF_F64) return IPF_INVALID_ARG;
+    if (dtype != IPF_F32 && dtype != IPF_F64 && dtype != IPF_DF64) return IPF_INVALID_ARG;
     for (int a = 0; a < 3; ++a) {
         if (n[a] < 1) return IPF_INVALID_ARG;
         if (!(h[a] > 0.0) || !isfinite(h[a])) return IPF_INVALID_ARG;
@@ -215,11 +219,14 @@ int acquire_spectrum(ipf_plan_s *p, cudaStream_t st)
         const size_t Y = p->M[1] / 2 + 1, Z = p->M[2] / 2 + 1;
         e.Gs = (char *)e.G + e.bytes - es * Y * Z;
         logf(IPF_CONSOLE_INFO_1, p->verbosity, "building Green's spectrum for mesh %lldx%lldx%lld (%s)",
-             (long long)p->M[0], (long long)p->M[1], (long long)p->M[2], p->dtype == IPF_F32 ? "f32" : "f64");
+             (long long)p->M[0], (long long)p->M[1], (long long)p->M[2],
+             p->dtype == IPF_F32 ? "f32" : (p->dtype == IPF_F64 ? "f64" : "df64"));
         if (p->dtype == IPF_F32)
             ce = build_green_spectrum<float>(p->M, p->key.hn, (float *)e.G, (float *)e.Gs, st);
-        else
+        else if (p->dtype == IPF_F64)
             ce = build_green_spectrum<double>(p->M, p->key.hn, (double *)e.G, (double *)e.Gs, st);
+        else
+            ce = build_green_spectrum<df64>(p->M, p->key.hn, (df64 *)e.G, (df64 *)e.Gs, st);
         if (ce != cudaSuccess) {
             free_entry(e);
             return cuda_status(ce);
@@ -261,6 +268,7 @@ cudaError_t fold_slot(ipf_plan_s *p, uint64_t i)
 template <typename T>
 cudaError_t enqueue_solve(ipf_plan_s *p, const void *src, void *phi, cudaStream_t st)
 {
+    using IoT = typename IoReal<T>::type;
     const int Nx = (int)p->N[0], Ny = (int)p->N[1], Nz = (int)p->N[2];
     const int Lx = (int)(p->M[0] / 2), My = (int)p->M[1], Mz = (int)p->M[2];
     const int64_t nrows = (int64_t)Ny * Nz;
@@ -279,7 +287,7 @@ cudaError_t enqueue_solve(ipf_plan_s *p, const void *src, void *phi, cudaStream_
     if (ev_on) cudaEventRecord(ev[0], st);
     bool fused = false;
     if (p->fuse_xy) {
-        e = launch_xy_forward<T>(Lx, (const T *)src, p->W, p->tw_x, p->rtw, p->tw_y, Nx, Ny, Nz, st);
+        e = launch_xy_forward<T>(Lx, (const IoT *)src, p->W, p->tw_x, p->rtw, p->tw_y, Nx, Ny, Nz, st);
         if (e == cudaSuccess) {
             fused = true;
         } else {
@@ -288,7 +296,7 @@ cudaError_t enqueue_solve(ipf_plan_s *p, const void *src, void *phi, cudaStream_
         }
     }
     if (!fused) {
-        e = launch_x_forward<T>(Lx, (const T *)src, p->W, p->tw_x, p->rtw, Nx, Ny, My, nrows, st);
+        e = launch_x_forward<T>(Lx, (const IoT *)src, p->W, p->tw_x, p->rtw, Nx, Ny, My, nrows, st);
         if (e != cudaSuccess) return e;
     }
     if (ev_on) cudaEventRecord(ev[1], st);
@@ -302,7 +310,7 @@ cudaError_t enqueue_solve(ipf_plan_s *p, const void *src, void *phi, cudaStream_
     if (e != cudaSuccess) return e;
     if (ev_on) cudaEventRecord(ev[3], st);
     if (fused) {
-        e = launch_yx_inverse<T>(Lx, p->W, (T *)phi, p->tw_x, p->rtw, p->tw_y, Nx, Ny, Nz, st);
+        e = launch_yx_inverse<T>(Lx, p->W, (IoT *)phi, p->tw_x, p->rtw, p->tw_y, Nx, Ny, Nz, st);
         if (e != cudaSuccess) {
             cudaGetLastError();  // refused: finish this solve, and later ones, with the separate passes
             p->fuse_xy = false;
@@ -315,7 +323,7 @@ cudaError_t enqueue_solve(ipf_plan_s *p, const void *src, void *phi, cudaStream_
     }
     if (ev_on) cudaEventRecord(ev[4], st);
     if (!fused) {
-        e = launch_x_inverse<T>(Lx, p->W, (T *)phi, p->tw_x, p->rtw, Nx, Ny, My, nrows, st);
+        e = launch_x_inverse<T>(Lx, p->W, (IoT *)phi, p->tw_x, p->rtw, Nx, Ny, My, nrows, st);
         if (e != cudaSuccess) return e;
     }
     if (ev_on) cudaEventRecord(ev[5], st);
@@ -324,8 +332,9 @@ cudaError_t enqueue_solve(ipf_plan_s *p, const void *src, void *phi, cudaStream_
 
 int solve_impl(ipf_plan_s *p, const void *src, void *phi, cudaStream_t st)
 {
-    cudaError_t e = p->dtype == IPF_F32 ? enqueue_solve<float>(p, src, phi, st)
-                                        : enqueue_solve<double>(p, src, phi, st);
+    cudaError_t e = p->dtype == IPF_F32   ? enqueue_solve<float>(p, src, phi, st)
+                    : p->dtype == IPF_F64 ? enqueue_solve<double>(p, src, phi, st)
+                                          : enqueue_solve<df64>(p, src, phi, st);
     return cuda_status(e);
 }
 
@@ -392,7 +401,9 @@ int ipf_plan_create(ipf_plan_t *out, const int64_t n[3], const double h[3], int 
     {
         const char *fz = getenv("ISOFFT_FUSE_XY");
         const int lx = (int)(p->M[0] / 2);
-        const bool fits = dtype == IPF_F32 ? xy_fusable<float>(lx) : xy_fusable<double>(lx);
+        const bool fits = dtype == IPF_F32   ? xy_fusable<float>(lx)
+                          : dtype == IPF_F64 ? xy_fusable<double>(lx)
+                                             : xy_fusable<df64>(lx);
         p->fuse_xy = p->M[0] == p->M[1] && fits && fz && fz[0] == '1';
     }
     p->verbosity = verbosity;
@@ -416,7 +427,9 @@ int ipf_plan_create(ipf_plan_t *out, const int64_t n[3], const double h[3], int 
         ipf_plan_destroy(p);
         return rc;
     }
-    rc = dtype == IPF_F32 ? upload_tables<float>(p, st) : upload_tables<double>(p, st);
+    rc = dtype == IPF_F32   ? upload_tables<float>(p, st)
+         : dtype == IPF_F64 ? upload_tables<double>(p, st)
+                            : upload_tables<df64>(p, st);
     if (!rc) rc = acquire_spectrum(p, st);
     if (!rc && (flags & IPF_FLAG_PASS_EVENTS)) {
         for (int s = 0; s < ipf_plan_s::kSlots && !rc; ++s)
@@ -554,7 +567,7 @@ int ipf_submit_batch(const ipf_plan_t *plans, int count, const void *const *d_sr
     for (int i = 0; i < count; ++i) {
         order[i] = i;
         const ipf_plan_s *p = plans[i];
-        cost[i] = (double)p->M[0] * p->M[1] * p->N[2] * (p->dtype == IPF_F64 ? 16.0 : 1.0);
+        cost[i] = (double)p->M[0] * p->M[1] * p->N[2] * (p->dtype == IPF_F64 ? 16.0 : (p->dtype == IPF_DF64 ? 6.0 : 1.0));
     }
     std::sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
     for (int i : order) {

@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "df64.cuh"
+
 namespace isofft {
 
 // Building blocks are host-callable too, so a host harness can run the
@@ -84,9 +86,10 @@ ISOFFT_HD Cx<T> mul_root(Cx<T> a)
     } else if constexpr (j == 6 || j == 18 || j == 30 || j == 42) {
         // |cos| = |sin| = 1/sqrt(2): a * (c - i s) with only the signs differing
         constexpr T r = (T)0.7071067811865476;
-        constexpr T sc = cos48(j) > 0 ? (T)1 : (T)-1;
-        constexpr T ss = sin48(j) > 0 ? (T)1 : (T)-1;
-        return {(sc * a.x + ss * a.y) * r, (sc * a.y - ss * a.x) * r};
+        constexpr bool cp = cos48(j) > 0, sp = sin48(j) > 0;
+        const T cx = cp ? a.x : -a.x, cy = cp ? a.y : -a.y;  // c a / |c|
+        const T sx = sp ? a.x : -a.x, sy = sp ? a.y : -a.y;  // s a / |s|
+        return {(cx + sy) * r, (cy - sx) * r};
     } else {
         constexpr T c = (T)cos48(j);
         constexpr T s = (T)sin48(j);
@@ -436,6 +439,8 @@ template <int L>
 struct Shape<float, L> : Shape32<L> {};
 template <int L>
 struct Shape<double, L> : Shape64<L> {};
+template <int L>
+struct Shape<df64, L> : Shape64<L> {};  // float pairs: register footprint of FP64
 
 // The z pass holds two lines groups per tile and stages its prefetches in
 // shared memory; for 512-point FP32 lines it runs 16 points per thread on

@@ -94,6 +94,7 @@ size_t spectrum_elems(const int64_t M[3])
 }
 template size_t spectrum_elems<float>(const int64_t *);
 template size_t spectrum_elems<double>(const int64_t *);
+template size_t spectrum_elems<df64>(const int64_t *);
 
 void host_roots(int64_t n, int64_t count, double *re, double *im)
 {
@@ -273,5 +274,6 @@ template cudaError_t build_green_spectrum<float>(const int64_t *, const double *
                                                  cudaStream_t);
 template cudaError_t build_green_spectrum<double>(const int64_t *, const double *, double *, double *,
                                                   cudaStream_t);
+template cudaError_t build_green_spectrum<df64>(const int64_t *, const double *, df64 *, df64 *, cudaStream_t);
 
 }  // namespace isofft

@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "df64.cuh"
+
 namespace isofft {
 
 // Doubled-mesh lengths the kernels are instantiated for (any M >= 2N - 1
@@ -16,13 +18,14 @@ constexpr int kMaxM = 1024;
 void count_launch();
 
 // All pointers are device pointers of the current device; complex buffers
-// are interleaved (re, im) of the real type.
+// are interleaved (re, im) of the arithmetic type T; source and potential
+// arrays hold IoReal<T>::type (double for df64).
 template <typename T>
-cudaError_t launch_x_forward(int L, const T *src, void *W, const void *tw, const void *rtw, int Nx,
-                             int Ny, int My, int64_t nrows, cudaStream_t st);
+cudaError_t launch_x_forward(int L, const typename IoReal<T>::type *src, void *W, const void *tw, const void *rtw,
+                             int Nx, int Ny, int My, int64_t nrows, cudaStream_t st);
 template <typename T>
-cudaError_t launch_x_inverse(int L, const void *W, T *phi, const void *tw, const void *rtw, int Nx,
-                             int Ny, int My, int64_t nrows, cudaStream_t st);
+cudaError_t launch_x_inverse(int L, const void *W, typename IoReal<T>::type *phi, const void *tw, const void *rtw,
+                             int Nx, int Ny, int My, int64_t nrows, cudaStream_t st);
 template <typename T>
 cudaError_t launch_y_forward(int L, void *W, const void *tw, int Ny, int Kx, int Nz, cudaStream_t st);
 template <typename T>
@@ -36,11 +39,11 @@ cudaError_t launch_z_convolve(int L, void *W, const void *tw, const T *G, const 
 template <typename T>
 bool xy_fusable(int LX);  // both fused kernels exist and fit for this LX
 template <typename T>
-cudaError_t launch_xy_forward(int LX, const T *src, void *W, const void *twx, const void *rtw, const void *twy,
-                              int Nx, int Ny, int Nz, cudaStream_t st);
+cudaError_t launch_xy_forward(int LX, const typename IoReal<T>::type *src, void *W, const void *twx,
+                              const void *rtw, const void *twy, int Nx, int Ny, int Nz, cudaStream_t st);
 template <typename T>
-cudaError_t launch_yx_inverse(int LX, void *W, T *phi, const void *twx, const void *rtw, const void *twy, int Nx,
-                              int Ny, int Nz, cudaStream_t st);
+cudaError_t launch_yx_inverse(int LX, void *W, typename IoReal<T>::type *phi, const void *twx, const void *rtw,
+                              const void *twy, int Nx, int Ny, int Nz, cudaStream_t st);
 
 // Width (kx columns per tile) of the z pass for line length L; the cached
 // Green's spectrum is stored in tiles of this width (0: unsupported L).

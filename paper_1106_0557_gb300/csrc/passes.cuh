@@ -83,13 +83,27 @@ struct ColXch {
     }
 };
 
-// Shared-memory exchange for row passes: one padded line per row; one pad
-// slot every 16 points spreads the strided first-stage writes over banks.
+// Shared-memory exchange for row passes: one line per row, positions
+// XOR-swizzled within blocks of 16 (p ^ ((p >> 4) & 15)).  With 8-byte
+// points and a row held by one warp, the swizzle sends the warp's 32
+// accesses of every exchange pattern (stride-8 first-stage writes, blocked
+// second-stage writes, consecutive reads) to each bank pair exactly twice.
 template <int L>
 struct RowPad {
-    static constexpr int LP = L + L / 16;
-    static __device__ __forceinline__ int at(int p) { return p + (p >> 4); }
+    static constexpr int LP = (L + 15) & ~15;
+    static __device__ __forceinline__ int at(int p) { return p ^ ((p >> 4) & 15); }
 };
+
+// A row held by at most one warp needs only a warp barrier between the
+// writes and reads of its line.
+template <int NT>
+__device__ __forceinline__ void row_sync()
+{
+    if constexpr (NT <= 32 && 32 % NT == 0)
+        __syncwarp();
+    else
+        __syncthreads();
+}
 
 template <typename T, int L, int E>
 struct RowXch {
@@ -102,10 +116,10 @@ struct RowXch {
         for (int q = 0; q < G::B; ++q)
 #pragma unroll
             for (int r = 0; r < R; ++r) s[RowPad<L>::at(G::out_pos(t, q, r))] = v[q + r * G::B];
-        __syncthreads();
+        row_sync<G::NT>();
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = s[RowPad<L>::at(t + m * G::NT)];
-        __syncthreads();
+        row_sync<G::NT>();
     }
 };
 
@@ -198,12 +212,16 @@ __device__ __forceinline__ Cx<T> ld_cx(const Cx<T> *p)
 
 // K1 body: row rr = z * Ny + y of the source, real -> packed half spectrum.
 // tw: W_L^k (k < L), rtw: W_{2L}^k (k < L), L = Mx / 2.
+template <typename T>
+using In = typename IoReal<T>::type;  // real type of the source / potential arrays
+
 template <typename T, int L>
-__device__ __forceinline__ void x_forward_row_at(const T *in, Cx<T> *__restrict__ out, const Cx<T> *__restrict__ tw,
-                                                 const Cx<T> *__restrict__ rtw, int Nx, bool active, Cx<T> *line,
-                                                 int t)
+__device__ __forceinline__ void x_forward_row_at(const In<T> *in, Cx<T> *__restrict__ out,
+                                                 const Cx<T> *__restrict__ tw, const Cx<T> *__restrict__ rtw, int Nx,
+                                                 bool active, Cx<T> *line, int t)
 {
     constexpr int E = Shape<T, L>::E, NT = L / E;
+    using IO = IoReal<T>;
 
     // pairs (x[2p], x[2p+1]) as one complex point; p >= L/2 is padding
     Cx<T> v[E];
@@ -214,10 +232,11 @@ __device__ __forceinline__ void x_forward_row_at(const T *in, Cx<T> *__restrict_
         if (m < E / 2 && active) {
             const int p = t + m * NT;
             if (vec && 2 * p + 1 < Nx) {
-                v[m] = reinterpret_cast<const Cx<T> *>(in)[p];
+                const Cx<In<T>> pr = reinterpret_cast<const Cx<In<T>> *>(in)[p];
+                v[m] = {IO::in(pr.x), IO::in(pr.y)};
             } else {
-                if (2 * p < Nx) v[m].x = in[2 * p];
-                if (2 * p + 1 < Nx) v[m].y = in[2 * p + 1];
+                if (2 * p < Nx) v[m].x = IO::in(in[2 * p]);
+                if (2 * p + 1 < Nx) v[m].y = IO::in(in[2 * p + 1]);
             }
         }
     }
@@ -229,7 +248,7 @@ __device__ __forceinline__ void x_forward_row_at(const T *in, Cx<T> *__restrict_
     //   2X[0] = 2(Re Z0 + Im Z0), 2X[L] = 2(Re Z0 - Im Z0).
 #pragma unroll
     for (int m = 0; m < E; ++m) line[RowPad<L>::at(t + m * NT)] = v[m];
-    __syncthreads();
+    row_sync<NT>();
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         const int k = t + m * NT;
@@ -244,7 +263,7 @@ __device__ __forceinline__ void x_forward_row_at(const T *in, Cx<T> *__restrict_
 }
 
 template <typename T, int L>
-__device__ __forceinline__ void x_forward_row(const T *__restrict__ src, Cx<T> *__restrict__ W,
+__device__ __forceinline__ void x_forward_row(const In<T> *__restrict__ src, Cx<T> *__restrict__ W,
                                               const Cx<T> *__restrict__ tw, const Cx<T> *__restrict__ rtw, int Nx,
                                               int Ny, int My, int64_t rr, bool active, Cx<T> *line, int t)
 {
@@ -255,7 +274,7 @@ __device__ __forceinline__ void x_forward_row(const T *__restrict__ src, Cx<T> *
 
 // K5 body: packed half spectrum of row rr -> real row, cropped to x < Nx.
 template <typename T, int L, bool CG = false>
-__device__ __forceinline__ void x_inverse_row_at(const Cx<T> *in, T *__restrict__ out, const Cx<T> *__restrict__ tw,
+__device__ __forceinline__ void x_inverse_row_at(const Cx<T> *in, In<T> *__restrict__ out, const Cx<T> *__restrict__ tw,
                                                  const Cx<T> *__restrict__ rtw, int Nx, bool active, Cx<T> *line,
                                                  int t)
 {
@@ -265,7 +284,7 @@ __device__ __forceinline__ void x_inverse_row_at(const Cx<T> *in, T *__restrict_
         const int k = t + m * NT;
         line[RowPad<L>::at(k)] = active ? ld_cx<CG>(in + k) : Cx<T>{(T)0, (T)0};
     }
-    __syncthreads();
+    row_sync<NT>();
     // rebuild the half-length spectrum of z[m] = y[2m] + i y[2m+1]:
     //   Z[k] = A + i B,  A = X[k] + conj X[L-k],  B = (X[k] - conj X[L-k]) W_2L^{-k}
     Cx<T> v[E];
@@ -284,7 +303,7 @@ __device__ __forceinline__ void x_inverse_row_at(const Cx<T> *in, T *__restrict_
         }
         v[m] = {a.x - b.y, a.y + b.x};
     }
-    __syncthreads();
+    row_sync<NT>();
     // inverse transform = swap o forward o swap
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = cswap(v[m]);
@@ -296,17 +315,18 @@ __device__ __forceinline__ void x_inverse_row_at(const Cx<T> *in, T *__restrict_
         const int p = t + m * NT;
         const Cx<T> o = cswap(v[m]);
         if (!active) continue;
+        using IO = IoReal<T>;
         if (vec && 2 * p + 1 < Nx) {
-            reinterpret_cast<Cx<T> *>(out)[p] = o;
+            reinterpret_cast<Cx<In<T>> *>(out)[p] = {IO::out(o.x), IO::out(o.y)};
         } else {
-            if (2 * p < Nx) out[2 * p] = o.x;
-            if (2 * p + 1 < Nx) out[2 * p + 1] = o.y;
+            if (2 * p < Nx) out[2 * p] = IO::out(o.x);
+            if (2 * p + 1 < Nx) out[2 * p + 1] = IO::out(o.y);
         }
     }
 }
 
 template <typename T, int L, bool CG = false>
-__device__ __forceinline__ void x_inverse_row(const Cx<T> *__restrict__ W, T *__restrict__ phi,
+__device__ __forceinline__ void x_inverse_row(const Cx<T> *__restrict__ W, In<T> *__restrict__ phi,
                                               const Cx<T> *__restrict__ tw, const Cx<T> *__restrict__ rtw, int Nx,
                                               int Ny, int My, int64_t rr, bool active, Cx<T> *line, int t)
 {
@@ -379,7 +399,7 @@ __device__ __forceinline__ void y_inverse_tile(Cx<T> *__restrict__ W, const Cx<T
 // ---------------------------------------------------------------------
 template <typename T, int L>
 __global__ void __launch_bounds__(RowCfg<T, L>::THREADS)
-k_x_forward(const T *__restrict__ src, Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw,
+k_x_forward(const In<T> *__restrict__ src, Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw,
             const Cx<T> *__restrict__ rtw, int Nx, int Ny, int My, int64_t nrows)
 {
     using C = RowCfg<T, L>;
@@ -393,7 +413,7 @@ k_x_forward(const T *__restrict__ src, Cx<T> *__restrict__ W, const Cx<T> *__res
 
 template <typename T, int L>
 __global__ void __launch_bounds__(RowCfg<T, L>::THREADS)
-k_x_inverse(const Cx<T> *__restrict__ W, T *__restrict__ phi, const Cx<T> *__restrict__ tw,
+k_x_inverse(const Cx<T> *__restrict__ W, In<T> *__restrict__ phi, const Cx<T> *__restrict__ tw,
             const Cx<T> *__restrict__ rtw, int Nx, int Ny, int My, int64_t nrows)
 {
     using C = RowCfg<T, L>;
@@ -455,7 +475,7 @@ struct XYCfg {
     static constexpr size_t XCH_X = (size_t)NL * RowPad<LX>::LP * CS;
     static constexpr size_t XCH_Y = (size_t)LY * TX * CS;
     // one stage of prefetched input (each phase double-buffers its stage)
-    static constexpr size_t ROWS_F = (size_t)NL * LX * sizeof(T);  // real source rows
+    static constexpr size_t ROWS_F = (size_t)NL * LX * sizeof(In<T>);  // real source rows
     static constexpr size_t ROWS_I = (size_t)NL * LX * CS;         // packed half-spectrum rows
     static constexpr size_t COLS_F = (size_t)LX * TX * CS;         // half columns (y < My/2)
     static constexpr size_t COLS_I = (size_t)LY * TX * CS;         // whole columns
@@ -522,7 +542,7 @@ __device__ __forceinline__ void stage_rows(unsigned char *dst, size_t stride, in
 
 template <typename T, int LX>
 __global__ void __launch_bounds__(XYCfg<T, LX>::THREADS, XYCfg<T, LX>::MIN_BLOCKS)
-k_xy_forward(const T *__restrict__ src, Cx<T> *__restrict__ W, const Cx<T> *__restrict__ twx,
+k_xy_forward(const In<T> *__restrict__ src, Cx<T> *__restrict__ W, const Cx<T> *__restrict__ twx,
              const Cx<T> *__restrict__ rtw, const Cx<T> *__restrict__ twy, int Nx, int Ny)
 {
     using C = XYCfg<T, LX>;
@@ -538,11 +558,11 @@ k_xy_forward(const T *__restrict__ src, Cx<T> *__restrict__ W, const Cx<T> *__re
         const int per = (Ny + XY_CLUSTER - 1) / XY_CLUSTER;
         const int y_lo = r * per, y_hi = min(Ny, y_lo + per);
         const int rounds = y_hi > y_lo ? (y_hi - y_lo + C::NL - 1) / C::NL : 0;
-        const bool vec16 = ((size_t)Nx * sizeof(T)) % 16 == 0;
+        const bool vec16 = ((size_t)Nx * sizeof(In<T>)) % 16 == 0;
         auto issue = [&](int j, int buf) {
             const int y0 = y_lo + j * C::NL;
-            stage_rows<sizeof(T)>(
-                stage + buf * C::ROWS_F, LX * sizeof(T), C::NL, Nx * (int)sizeof(T),
+            stage_rows<sizeof(In<T>)>(
+                stage + buf * C::ROWS_F, LX * sizeof(In<T>), C::NL, Nx * (int)sizeof(In<T>),
                 [&](int rr) -> const unsigned char * {
                     const int y = y0 + rr;
                     return y < y_hi ? reinterpret_cast<const unsigned char *>(src + ((size_t)z * Ny + y) * Nx)
@@ -553,7 +573,7 @@ k_xy_forward(const T *__restrict__ src, Cx<T> *__restrict__ W, const Cx<T> *__re
         auto compute = [&](int j, int buf) {
             const int y = y_lo + j * C::NL + l;
             const bool active = y < y_hi;
-            const T *in = reinterpret_cast<const T *>(stage + buf * C::ROWS_F) + l * LX;
+            const In<T> *in = reinterpret_cast<const In<T> *>(stage + buf * C::ROWS_F) + l * LX;
             x_forward_row_at<T, LX>(in, W + ((size_t)z * LY + (active ? y : y_lo)) * LX, twx, rtw, Nx, active,
                                     xch + l * RowPad<LX>::LP, t);
         };
@@ -589,7 +609,7 @@ k_xy_forward(const T *__restrict__ src, Cx<T> *__restrict__ W, const Cx<T> *__re
 
 template <typename T, int LX>
 __global__ void __launch_bounds__(XYCfg<T, LX>::THREADS, XYCfg<T, LX>::MIN_BLOCKS)
-k_yx_inverse(Cx<T> *__restrict__ W, T *__restrict__ phi, const Cx<T> *__restrict__ twx,
+k_yx_inverse(Cx<T> *__restrict__ W, In<T> *__restrict__ phi, const Cx<T> *__restrict__ twx,
              const Cx<T> *__restrict__ rtw, const Cx<T> *__restrict__ twy, int Nx, int Ny)
 {
     using C = XYCfg<T, LX>;

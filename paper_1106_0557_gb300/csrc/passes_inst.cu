@@ -1,6 +1,6 @@
 // passes_inst.cu -- instantiates and launches the pass kernels for one real
 // type and one group of passes.  The build compiles this file several times:
-//   -DISOFFT_REAL=float|double   the arithmetic type
+//   -DISOFFT_REAL=float|double|isofft::df64   the arithmetic type
 //   -DISOFFT_GROUP=1|2|3|4       1: x passes (K1, K5), 2: y passes (K2, K4),
 //                                3: z pass (K3), 4: fused x+y passes
 // so that the instantiations compile in parallel.
@@ -41,7 +41,7 @@ static cudaError_t ensure_smem(F *func, size_t bytes, std::atomic<uint64_t> &don
 
 #if ISOFFT_GROUP == 1
 template <typename T, int L>
-static cudaError_t run_x_forward(const T *src, void *W, const void *tw, const void *rtw, int Nx, int Ny,
+static cudaError_t run_x_forward(const In<T> *src, void *W, const void *tw, const void *rtw, int Nx, int Ny,
                                  int My, int64_t nrows, cudaStream_t st)
 {
     using C = RowCfg<T, L>;
@@ -55,7 +55,7 @@ static cudaError_t run_x_forward(const T *src, void *W, const void *tw, const vo
     return cudaGetLastError();
 }
 template <typename T, int L>
-static cudaError_t run_x_inverse(const void *W, T *phi, const void *tw, const void *rtw, int Nx, int Ny,
+static cudaError_t run_x_inverse(const void *W, In<T> *phi, const void *tw, const void *rtw, int Nx, int Ny,
                                  int My, int64_t nrows, cudaStream_t st)
 {
     using C = RowCfg<T, L>;
@@ -70,7 +70,7 @@ static cudaError_t run_x_inverse(const void *W, T *phi, const void *tw, const vo
 }
 
 template <typename R_>
-cudaError_t launch_x_forward(int L, const R_ *src, void *W, const void *tw, const void *rtw, int Nx,
+cudaError_t launch_x_forward(int L, const In<R_> *src, void *W, const void *tw, const void *rtw, int Nx,
                                  int Ny, int My, int64_t nrows, cudaStream_t st)
 {
     switch (L) {
@@ -82,7 +82,7 @@ cudaError_t launch_x_forward(int L, const R_ *src, void *W, const void *tw, cons
     }
 }
 template <typename R_>
-cudaError_t launch_x_inverse(int L, const void *W, R_ *phi, const void *tw, const void *rtw, int Nx,
+cudaError_t launch_x_inverse(int L, const void *W, In<R_> *phi, const void *tw, const void *rtw, int Nx,
                                  int Ny, int My, int64_t nrows, cudaStream_t st)
 {
     switch (L) {
@@ -93,9 +93,9 @@ cudaError_t launch_x_inverse(int L, const void *W, R_ *phi, const void *tw, cons
     default: return cudaErrorInvalidValue;
     }
 }
-template cudaError_t launch_x_forward<Real>(int, const Real *, void *, const void *, const void *, int, int,
+template cudaError_t launch_x_forward<Real>(int, const In<Real> *, void *, const void *, const void *, int, int,
                                             int, int64_t, cudaStream_t);
-template cudaError_t launch_x_inverse<Real>(int, const void *, Real *, const void *, const void *, int, int,
+template cudaError_t launch_x_inverse<Real>(int, const void *, In<Real> *, const void *, const void *, int, int,
                                             int, int64_t, cudaStream_t);
 #endif
 
@@ -160,7 +160,7 @@ static cudaError_t launch_cluster(K *kernel, unsigned grid, unsigned threads, si
 }
 
 template <typename T, int LX>
-static cudaError_t run_xy(const T *src, void *W, const void *twx, const void *rtw, const void *twy, int Nx, int Ny,
+static cudaError_t run_xy(const In<T> *src, void *W, const void *twx, const void *rtw, const void *twy, int Nx, int Ny,
                           int Nz, cudaStream_t st)
 {
     using C = XYCfg<T, LX>;
@@ -174,7 +174,7 @@ static cudaError_t run_xy(const T *src, void *W, const void *twx, const void *rt
     return e;
 }
 template <typename T, int LX>
-static cudaError_t run_yx(void *W, T *phi, const void *twx, const void *rtw, const void *twy, int Nx, int Ny, int Nz,
+static cudaError_t run_yx(void *W, In<T> *phi, const void *twx, const void *rtw, const void *twy, int Nx, int Ny, int Nz,
                           cudaStream_t st)
 {
     using C = XYCfg<T, LX>;
@@ -188,7 +188,7 @@ static cudaError_t run_yx(void *W, T *phi, const void *twx, const void *rtw, con
     return e;
 }
 template <typename R_>
-cudaError_t launch_xy_forward(int LX, const R_ *src, void *W, const void *twx, const void *rtw, const void *twy,
+cudaError_t launch_xy_forward(int LX, const In<R_> *src, void *W, const void *twx, const void *rtw, const void *twy,
                               int Nx, int Ny, int Nz, cudaStream_t st)
 {
     switch (LX) {
@@ -200,7 +200,7 @@ cudaError_t launch_xy_forward(int LX, const R_ *src, void *W, const void *twx, c
     }
 }
 template <typename R_>
-cudaError_t launch_yx_inverse(int LX, void *W, R_ *phi, const void *twx, const void *rtw, const void *twy, int Nx,
+cudaError_t launch_yx_inverse(int LX, void *W, In<R_> *phi, const void *twx, const void *rtw, const void *twy, int Nx,
                               int Ny, int Nz, cudaStream_t st)
 {
     switch (LX) {
@@ -223,9 +223,9 @@ bool xy_fusable(int LX)
     }
 }
 template bool xy_fusable<Real>(int);
-template cudaError_t launch_xy_forward<Real>(int, const Real *, void *, const void *, const void *, const void *,
-                                             int, int, int, cudaStream_t);
-template cudaError_t launch_yx_inverse<Real>(int, void *, Real *, const void *, const void *, const void *, int,
+template cudaError_t launch_xy_forward<Real>(int, const In<Real> *, void *, const void *, const void *,
+                                             const void *, int, int, int, cudaStream_t);
+template cudaError_t launch_yx_inverse<Real>(int, void *, In<Real> *, const void *, const void *, const void *, int,
                                              int, int, cudaStream_t);
 #endif
 

@@ -17,6 +17,7 @@ from . import build as _build
 
 IPF_F32 = 0
 IPF_F64 = 1
+IPF_DF64 = 2
 IPF_OK = 0
 IPF_INVALID_ARG = 1
 IPF_UNSUPPORTED_SIZE = 2
@@ -31,7 +32,8 @@ IPF_CONSOLE_INFO_1 = 2
 IPF_CONSOLE_INFO_2 = 3
 IPF_FLAG_PASS_EVENTS = 1
 
-DTYPES = {"f32": IPF_F32, "f64": IPF_F64, IPF_F32: IPF_F32, IPF_F64: IPF_F64}
+DTYPES = {"f32": IPF_F32, "f64": IPF_F64, "df64": IPF_DF64, IPF_F32: IPF_F32, IPF_F64: IPF_F64,
+          IPF_DF64: IPF_DF64}
 
 _lib = None
 

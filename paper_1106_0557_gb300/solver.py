@@ -9,8 +9,9 @@ import torch
 
 from . import native
 
-_TORCH = {"f32": torch.float32, "f64": torch.float64}
-_NUMPY = {"f32": np.float32, "f64": np.float64}
+# source / potential arrays: double for the FP64-class float-pair dtype too
+_TORCH = {"f32": torch.float32, "f64": torch.float64, "df64": torch.float64}
+_NUMPY = {"f32": np.float32, "f64": np.float64, "df64": np.float64}
 
 
 def _stream_handle(stream):
@@ -21,7 +22,8 @@ def _stream_handle(stream):
 
 class Plan:
     """A solver for one mesh shape N = (Nx, Ny, Nz), widths h and dtype
-    ('f32' or 'f64'); sources and potentials are [Nz][Ny][Nx] arrays."""
+    ('f32', 'f64', or 'df64' -- FP64-class float pairs on the FP32 units);
+    sources and potentials are [Nz][Ny][Nx] arrays."""
 
     def __init__(self, n, h, dtype="f32", flags=0, verbosity=native.IPF_CONSOLE_ERROR, stream=None):
         if not torch.cuda.is_available():

@@ -1,8 +1,9 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
 
 Tolerances (normwise max relative error, max|phi - ref| / max|ref|):
-FP64 path 1e-12, FP32 path 1e-5; the FP32 source is cast to FP64 before the
-oracle runs, so input quantisation is not counted.
+FP64 path and FP64-class float-pair path (df64) 1e-12, FP32 path 1e-5; the
+FP32 source is cast to FP64 before the oracle runs, so input quantisation is
+not counted.
 """
 import numpy as np
 import pytest
@@ -14,8 +15,8 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f32": 1e-5, "f64": 1e-12}
-NP = {"f32": np.float32, "f64": np.float64}
+TOL = {"f32": 1e-5, "f64": 1e-12, "df64": 1e-12}
+NP = {"f32": np.float32, "f64": np.float64, "df64": np.float64}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -57,7 +58,7 @@ SHAPES = [
 ]
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "df64"])
 @pytest.mark.parametrize("N,h", SHAPES)
 def test_random_sources_match_oracle(N, h, dtype):
     src = rand_src(N, seed=sum(N))
@@ -66,7 +67,7 @@ def test_random_sources_match_oracle(N, h, dtype):
     assert oracle.max_rel_error(phi, ref) <= TOL[dtype]
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "df64"])
 def test_sphere_32_matches_oracle_and_direct_sum(dtype):
     w = sources.single_sphere(32)
     phi, s64 = gpu_solve(w.source(), w.h, dtype)
@@ -77,7 +78,7 @@ def test_sphere_32_matches_oracle_and_direct_sum(dtype):
     assert oracle.max_rel_error(phi16, oracle.direct_sum(s16, w16.h)) <= TOL[dtype]
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "df64"])
 @pytest.mark.parametrize("N,h", [((256, 256, 256), (1.0, 1.0, 1.0)), ((100, 60, 130), (0.5, 0.25, 1.0))])
 def test_impulse_response_is_green_table(N, h, dtype):
     """A unit source at a corner gives the Green's function itself at every
@@ -96,7 +97,7 @@ def test_impulse_response_is_green_table(N, h, dtype):
         assert np.max(np.abs(phi - want)) / np.max(np.abs(want)) <= TOL[dtype]
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "df64"])
 def test_multisphere_256_sampled_direct_sum(dtype):
     """The 256^3 multi-sphere workload: sampled cells against route 1 (the
     definition, summed over all 16.7 M source cells per sample)."""
@@ -195,7 +196,7 @@ LONG_SHAPES = [
 ]
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "df64"])
 @pytest.mark.parametrize("N,h", LONG_SHAPES)
 def test_long_lines_match_oracle(N, h, dtype):
     src = rand_src(N, seed=7 + sum(N))
@@ -243,7 +244,7 @@ def test_batch_graph_replay_matches_single_solves():
         p.close()
 
 
-@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("dtype", ["f32", "f64", "df64"])
 @pytest.mark.parametrize("N", [(64, 64, 64), (60, 50, 13), (256, 200, 31), (500, 400, 7)])
 def test_fused_xy_passes_equal_separate_passes(N, dtype, monkeypatch):
     """Planes with My = Mx run the x and y passes fused in one cluster
@@ -265,3 +266,18 @@ def test_fused_xy_passes_equal_separate_passes(N, dtype, monkeypatch):
         torch.cuda.synchronize()
         assert native.ipf_launch_count() - before == 5
     assert torch.equal(fused, sep)
+
+
+def test_df64_is_fp64_class_and_beats_fp32():
+    """The float-pair path reaches the FP64 tolerance where FP32 cannot:
+    on the 128^3 multi-sphere source its error against the oracle is below
+    1e-12 and at least 1e5 times smaller than the FP32 path's."""
+    w = sources.multi_sphere(128, seed=2)
+    src = w.source()
+    ref = oracle.solve(src, w.h)
+    e_df, _ = gpu_solve(src, w.h, "df64")
+    e32, s32 = gpu_solve(src, w.h, "f32")
+    err_df = oracle.max_rel_error(e_df, ref)
+    err32 = oracle.max_rel_error(e32, oracle.solve(s32, w.h))
+    assert err_df <= 1e-12
+    assert err_df * 1e5 < err32
