@@ -316,16 +316,19 @@ def run_batch(steps=50, count=64):
     return res
 
 
-def run_serving(n_requests, slots):
-    """Config-5 style serving: cubic N log-uniform in [32, 384], 70 % FP32 /
-    30 % FP64, HBM budget 120 GB.  Saturated throughput (all requests at t=0),
-    then Poisson arrivals at 0.8 x that rate for p50/p99 latency; and the FP32
-    class served vs the same shapes solved one at a time in FP64."""
+def run_serving(n_requests, slots, fp64_class="df64"):
+    """Config-5 style serving: cubic N log-uniform in [32, 384], 70 % FP32
+    (tolerance 1e-5) / 30 % FP64-class (tolerance 1e-12, served with the
+    `fp64_class` dtype), HBM budget 120 GB.  Saturated throughput (all
+    requests at t=0), then Poisson arrivals at 0.8 x that rate for p50/p99
+    latency; and the FP32 class served vs the same shapes solved one at a
+    time in plain FP64."""
     import torch
 
     from paper_1106_0557_gb300 import native, serving, sources
     spec = sources.serving_requests(count=n_requests, seed=0)
-    mk = lambda arr: [serving.Request(r["id"], r["n"], r["dtype"], r["seed"], a) for r, a in zip(spec, arr)]
+    cls = lambda d: fp64_class if d == "f64" else d
+    mk = lambda arr: [serving.Request(r["id"], r["n"], cls(r["dtype"]), r["seed"], a) for r, a in zip(spec, arr)]
     be = serving.TorchBackend(slots=slots)
     reqs = mk(np.zeros(len(spec)))
     be.prepare(reqs)
@@ -356,7 +359,7 @@ def run_serving(n_requests, slots):
         native.ipf_plan_destroy(p)
     plain64 = len(shapes) / plain_s
     return {"requests": len(spec), "slots": slots, "budget_gb": 120,
-            "mix": "cubic N log-uniform [32,384], 70% f32 / 30% f64",
+            "mix": "cubic N log-uniform [32,384], 70%% f32 / 30%% FP64-class served as %s" % fp64_class,
             "saturated_solves_per_s": round(sat["solves_per_s"], 1),
             "poisson_rate": round(rate, 1), "p50_ms": round(lat["p50_ms"], 3), "p99_ms": round(lat["p99_ms"], 3),
             "solves_per_s": round(lat["solves_per_s"], 1),
