@@ -133,8 +133,8 @@ struct RowCfg {
 };
 
 // Column tiles of the y passes: up to 128 bytes of complex per row and at
-// most 512 threads, so two tiles are resident per SM and one tile's global
-// loads overlap the other's butterflies.
+// most 512 threads, so two or three tiles are resident per SM and one tile's
+// global loads overlap the others' butterflies.
 template <typename T, int L>
 struct ColCfg {
     static constexpr int E = Shape<T, L>::E;
@@ -143,7 +143,11 @@ struct ColCfg {
     static constexpr int TX = TX0 * NT <= 512 ? TX0 : (512 / NT >= 1 ? 512 / NT : 1);
     static constexpr int THREADS = TX * NT;
     static constexpr size_t SMEM = (size_t)L * TX * sizeof(Cx<T>);
+    // FP32 forward: registers low enough for 3 resident CTAs per SM (the
+    // inverse, which holds every point of its lines, would spill)
+    static constexpr int MIN_BLOCKS_FWD = sizeof(T) == 4 && THREADS <= 512 ? 3 : 1;
     static_assert(THREADS <= 1024, "column tile too large");
+    static_assert(SMEM <= 227 * 1024, "column tile exceeds shared memory");
 };
 
 // z pass tiles: TX columns of the two lines ky and My - ky (2 TX lines),
@@ -153,9 +157,9 @@ struct ColCfg {
 // are narrower: FP64 arithmetic, not memory, bounds that path.
 constexpr size_t z_smem(int tx, int nt, int L, int e, int rb)
 {
-    return (size_t)L * 2 * tx * 2 * rb       // exchange buffer
-           + (size_t)2 * tx * nt * (e / 2) * 2 * rb  // staged input
-           + (size_t)2 * tx * nt * e * rb;     // staged spectrum
+    return (size_t)L * 2 * tx * 2 * rb                // exchange buffer
+           + 2 * (size_t)2 * tx * nt * (e / 2) * 2 * rb  // staged input, two slot sets
+           + (size_t)2 * tx * nt * e * rb;              // staged spectrum
 }
 constexpr int z_tile_width(int rb, int nt, int L, int e)
 {
@@ -172,9 +176,11 @@ struct ZCfg {
     static constexpr int COLS = 2 * TX;
     static constexpr int THREADS = COLS * NT;
     static constexpr size_t XCH = (size_t)L * COLS * sizeof(Cx<T>);
-    static constexpr size_t STAGE_IN = (size_t)THREADS * (E / 2) * sizeof(Cx<T>);
+    static constexpr size_t STAGE_IN = (size_t)THREADS * (E / 2) * sizeof(Cx<T>);  // one slot set
+    static constexpr size_t STAGE_G = (size_t)THREADS * E * sizeof(T);             // one slot set
     static constexpr size_t SMEM = z_smem(TX, NT, L, E, (int)sizeof(T));
     static_assert(THREADS <= 1024, "z tile too large");
+    static_assert(SMEM <= 227 * 1024, "z tile exceeds shared memory");
 };
 
 // Layout of the Green's spectrum read by the z pass: [ky'][kx tile][kz'][TX]
@@ -429,7 +435,7 @@ k_x_inverse(const Cx<T> *__restrict__ W, In<T> *__restrict__ phi, const Cx<T> *_
 // K2 / K4: y passes on column tiles; grid (ceil(Kx / TX), Nz).
 // ---------------------------------------------------------------------
 template <typename T, int L>
-__global__ void __launch_bounds__(ColCfg<T, L>::THREADS)
+__global__ void __launch_bounds__(ColCfg<T, L>::THREADS, ColCfg<T, L>::MIN_BLOCKS_FWD)
 k_y_forward(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx)
 {
     using C = ColCfg<T, L>;
@@ -692,8 +698,15 @@ k_z_convolve(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, const T *__res
     constexpr int Lh = L / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<T> *sm = reinterpret_cast<Cx<T> *>(smem_raw);
-    Cx<T> *st_in = reinterpret_cast<Cx<T> *>(smem_raw + C::XCH);          // [E/2][TH]
-    T *st_g = reinterpret_cast<T *>(smem_raw + C::XCH + C::STAGE_IN);     // [E][TH]
+    // Per-thread staging slots.  The input slots come in two sets that
+    // alternate with the tile parity: the next tile's copies are issued right
+    // after this tile's slots are read, before anything consumes those reads,
+    // and cp.async is not ordered against them.  The spectrum slots are read
+    // by the multiply, which in-order issue completes before the next copies
+    // into them are issued, so one set suffices.
+    Cx<T> *st_in0 = reinterpret_cast<Cx<T> *>(smem_raw + C::XCH);  // 2 x [E/2][TH]
+    T *st_g = reinterpret_cast<T *>(smem_raw + C::XCH + 2 * C::STAGE_IN);  // [E][TH]
+    constexpr int IN_SET = (E / 2) * TH;
     // thread -> (column c, group g, position t): a warp holds both groups of
     // a few positions, so each position row of the exchange buffer is written
     // whole and the warp's shared-memory accesses are conflict-free
@@ -712,12 +725,13 @@ k_z_convolve(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, const T *__res
         ky = g == 0 ? pr : (pr == 0 ? My / 2 : My - pr);
         kx = xt * TX + c;
     };
-    // stage the non-zero half of this thread's line of `tile`
-    auto stage_input = [&](int tile) {
+    // stage the non-zero half of this thread's line of `tile` into slot set `set`
+    auto stage_input = [&](int tile, int set) {
         int ky, kx, pr, xt;
         line_of(tile, ky, kx, pr, xt);
         const bool active = kx < Kx;
         const Cx<T> *base = W + (size_t)ky * Kx + (active ? kx : 0);
+        Cx<T> *st_in = st_in0 + set * IN_SET;
 #pragma unroll
         for (int m = 0; m < E / 2; ++m) {
             const int z = t + m * NT;
@@ -744,13 +758,15 @@ k_z_convolve(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, const T *__res
     twr.load(tw, t);
     int tile = blockIdx.x;
     if (tile < ntiles) {
-        stage_input(tile);
+        stage_input(tile, 0);
         cp_async_commit();
         stage_spectrum(tile);
         cp_async_commit();
     }
-    for (; tile < ntiles; tile += gridDim.x) {
+    for (int it = 0; tile < ntiles; tile += gridDim.x, ++it) {
         const int next = tile + gridDim.x;
+        const int set = it & 1;
+        const Cx<T> *st_in = st_in0 + set * IN_SET;
         int ky, kx, pr, xt;
         line_of(tile, ky, kx, pr, xt);
         const bool active = kx < Kx;
@@ -760,7 +776,7 @@ k_z_convolve(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, const T *__res
         Cx<T> v[E];
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = m < E / 2 ? st_in[m * TH + tid] : Cx<T>{(T)0, (T)0};
-        if (next < ntiles) stage_input(next);
+        if (next < ntiles) stage_input(next, set ^ 1);
         cp_async_commit();
 
         run_stages_reg<T, L, E, true>(v, t, twr, xch, Rad{});
