@@ -79,8 +79,10 @@ enum {
 /* Create a solver for an Nx x Ny x Nz mesh of widths h (paper Sec. 3.2,
  * `Create(PoissonSolver, CellWidth, nTotalCells, ...)`).
  *   out        receives the plan handle (NULL on failure).
- *   n          {Nx, Ny, Nz}, each >= 1; the doubled mesh 2N must fit the
- *              largest supported length (1024), else IPF_UNSUPPORTED_SIZE.
+ *   n          {Nx, Ny, Nz}, each >= 1 and at most 768: the doubled mesh
+ *              (2N rounded up to one of 32, 48, 64, 96, 128, 192, 256, 384,
+ *              512, 768, 1024, 1536) must fit the largest supported length,
+ *              else IPF_UNSUPPORTED_SIZE.
  *   h          {hx, hy, hz}, each finite and > 0.
  *   dtype      IPF_F32, IPF_F64 or IPF_DF64.  The Green's spectrum is always
  *              built in FP64 and rounded to the plan's dtype.

@@ -35,9 +35,9 @@ static cudaError_t ensure_smem(F *func, size_t bytes, std::atomic<uint64_t> &don
     return e;
 }
 
-#define ISOFFT_ROW_LENGTHS(X) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512)
+#define ISOFFT_ROW_LENGTHS(X) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768)
 #define ISOFFT_COL_LENGTHS(X) \
-    X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768) X(1024)
+    X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768) X(1024) X(1536)
 
 #if ISOFFT_GROUP == 1
 template <typename T, int L>
