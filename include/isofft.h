@@ -123,7 +123,12 @@ int ipf_solve(ipf_plan_t plan, const void *d_src, void *d_phi, void *stream);
 
 /* One solve from and to HOST memory: copies h_src to a device staging
  * buffer owned by the plan, solves, copies the potential back to h_phi and
- * synchronises `stream` before returning. */
+ * synchronises `stream` before returning.  The copies run on a stream of the
+ * plan, in chunks of z planes, overlapped with the x and y passes of the
+ * chunks already on the device (and, on the way back, with the inverse
+ * passes of later chunks); with pinned host buffers most of the copy time
+ * hides behind those passes.  Pass events (IPF_FLAG_PASS_EVENTS) are not
+ * recorded by this call. */
 int ipf_solve_host(ipf_plan_t plan, const void *h_src, void *h_phi, void *stream);
 
 /* One solve that allocates no memory, for callers that cannot call

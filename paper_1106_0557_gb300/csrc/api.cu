@@ -117,6 +117,10 @@ struct ipf_plan_s {
     void *tables = nullptr;  // tw_x | rtw | tw_y | tw_z
     const void *tw_x = nullptr, *rtw = nullptr, *tw_y = nullptr, *tw_z = nullptr;
     void *stage = nullptr;  // device staging for ipf_solve_host
+    // ipf_solve_host pipeline: a copy stream and per-chunk events
+    static constexpr int kChunks = 8;
+    cudaStream_t copy_st = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_done = nullptr, ev_in[kChunks] = {}, ev_out[kChunks] = {};
     // IPF_FLAG_PASS_EVENTS: a ring of event sets, one per recent solve; a
     // slot is folded into the running sums before it is reused, so timing
     // many back-to-back solves never waits on the device.
@@ -338,6 +342,61 @@ int solve_impl(ipf_plan_s *p, const void *src, void *phi, cudaStream_t st)
     return cuda_status(e);
 }
 
+// Host-buffer solve, pipelined over chunks of z planes.  The x and y passes
+// (and their inverses) treat z planes independently, so chunk k's forward
+// x/y passes start as soon as its copy has landed while later chunks are
+// still in flight on the copy stream; only the z pass needs every plane.
+// On the way back, chunk k's potential is copied out while later chunks'
+// inverse passes run.
+template <typename T>
+cudaError_t enqueue_solve_host(ipf_plan_s *p, const void *h_src, void *h_phi, cudaStream_t st)
+{
+    using IoT = typename IoReal<T>::type;
+    const int Nx = (int)p->N[0], Ny = (int)p->N[1], Nz = (int)p->N[2];
+    const int Lx = (int)(p->M[0] / 2), My = (int)p->M[1], Mz = (int)p->M[2];
+    const size_t plane = (size_t)Nx * Ny, wplane = (size_t)My * Lx;
+    const int chunks = Nz < ipf_plan_s::kChunks ? Nz : ipf_plan_s::kChunks;
+    const int per = (Nz + chunks - 1) / chunks;
+    IoT *stage = (IoT *)p->stage;
+    const char *hs = (const char *)h_src;
+    char *hp = (char *)h_phi;
+    char *W = (char *)p->W;
+    const size_t cs = 2 * sizeof(T);  // bytes of one workspace complex
+    cudaError_t e = cudaEventRecord(p->ev_start, st);  // the copies start after prior work on `st`
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->copy_st, p->ev_start, 0);
+    for (int k = 0; k < chunks && e == cudaSuccess; ++k) {
+        const int z0 = k * per, nz = z0 + per <= Nz ? per : Nz - z0;
+        if (nz <= 0) break;
+        e = cudaMemcpyAsync(stage + z0 * plane, hs + z0 * plane * sizeof(IoT), nz * plane * sizeof(IoT),
+                            cudaMemcpyHostToDevice, p->copy_st);
+        if (e == cudaSuccess) e = cudaEventRecord(p->ev_in[k], p->copy_st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, p->ev_in[k], 0);
+        if (e == cudaSuccess)
+            e = launch_x_forward<T>(Lx, stage + z0 * plane, W + z0 * wplane * cs, p->tw_x, p->rtw, Nx, Ny, My,
+                                    (int64_t)nz * Ny, st);
+        if (e == cudaSuccess) e = launch_y_forward<T>(My, W + z0 * wplane * cs, p->tw_y, Ny, Lx, nz, st);
+    }
+    if (e == cudaSuccess)
+        e = launch_z_convolve<T>(Mz, p->W, p->tw_z, (const T *)p->spec->G, (const T *)p->spec->Gs, (T)p->gscale, Nz,
+                                 My, Lx, st);
+    for (int k = 0; k < chunks && e == cudaSuccess; ++k) {
+        const int z0 = k * per, nz = z0 + per <= Nz ? per : Nz - z0;
+        if (nz <= 0) break;
+        e = launch_y_inverse<T>(My, W + z0 * wplane * cs, p->tw_y, Ny, Lx, nz, st);
+        if (e == cudaSuccess)
+            e = launch_x_inverse<T>(Lx, W + z0 * wplane * cs, stage + z0 * plane, p->tw_x, p->rtw, Nx, Ny, My,
+                                    (int64_t)nz * Ny, st);
+        if (e == cudaSuccess) e = cudaEventRecord(p->ev_out[k], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(p->copy_st, p->ev_out[k], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(hp + z0 * plane * sizeof(IoT), stage + z0 * plane, nz * plane * sizeof(IoT),
+                                cudaMemcpyDeviceToHost, p->copy_st);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev_done, p->copy_st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, p->ev_done, 0);
+    return e;
+}
+
 bool aligned16(const void *ptr) { return ((uintptr_t)ptr & 15u) == 0; }
 
 // Internal streams a batch is spread over, created once per device on the
@@ -454,6 +513,13 @@ int ipf_plan_destroy(ipf_plan_t p)
     if (p->W) cudaFree(p->W);
     if (p->tables) cudaFree(p->tables);
     if (p->stage) cudaFree(p->stage);
+    if (p->copy_st) cudaStreamDestroy(p->copy_st);
+    if (p->ev_start) cudaEventDestroy(p->ev_start);
+    if (p->ev_done) cudaEventDestroy(p->ev_done);
+    for (int k = 0; k < ipf_plan_s::kChunks; ++k) {
+        if (p->ev_in[k]) cudaEventDestroy(p->ev_in[k]);
+        if (p->ev_out[k]) cudaEventDestroy(p->ev_out[k]);
+    }
     for (int s = 0; s < ipf_plan_s::kSlots; ++s)
         for (int i = 0; i < 6; ++i)
             if (p->ev[s][i]) cudaEventDestroy(p->ev[s][i]);
@@ -515,6 +581,7 @@ int ipf_solve(ipf_plan_t p, const void *d_src, void *d_phi, void *stream)
     return solve_impl(p, d_src, d_phi, (cudaStream_t)stream);
 }
 
+
 int ipf_solve_host(ipf_plan_t p, const void *h_src, void *h_phi, void *stream)
 {
     if (!p || !h_src || !h_phi) return IPF_INVALID_ARG;
@@ -527,11 +594,19 @@ int ipf_solve_host(ipf_plan_t p, const void *h_src, void *h_phi, void *stream)
             return cuda_status(e);
         }
     }
-    cudaError_t e = cudaMemcpyAsync(p->stage, h_src, bytes, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_status(e);
-    int rc = solve_impl(p, p->stage, p->stage, st);
-    if (rc) return rc;
-    e = cudaMemcpyAsync(h_phi, p->stage, bytes, cudaMemcpyDeviceToHost, st);
+    if (!p->copy_st) {
+        cudaError_t e = cudaStreamCreateWithFlags(&p->copy_st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_done, cudaEventDisableTiming);
+        for (int k = 0; k < ipf_plan_s::kChunks && e == cudaSuccess; ++k) {
+            e = cudaEventCreateWithFlags(&p->ev_in[k], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_out[k], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    cudaError_t e = p->dtype == IPF_F32   ? enqueue_solve_host<float>(p, h_src, h_phi, st)
+                    : p->dtype == IPF_F64 ? enqueue_solve_host<double>(p, h_src, h_phi, st)
+                                          : enqueue_solve_host<df64>(p, h_src, h_phi, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return cuda_status(e);
 }

@@ -322,3 +322,19 @@ def test_binary_spheroid_convergence_at_least_first_order():
     print("binary spheroid L1 errors", errs)
     assert errs[-1] <= errs[0] / 8.0, errs
     assert max(errs[1:]) < 2e-3, errs
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64", "df64"])
+@pytest.mark.parametrize("N", [(37, 20, 13), (64, 64, 64), (33, 17, 5), (9, 11, 1)])
+def test_host_buffer_solve_equals_device_solve(N, dtype):
+    """ipf_solve_host copies and solves in chunks of z planes (ragged last
+    chunk, odd row lengths, fewer planes than chunks); its potential is
+    bitwise the device solve's."""
+    from paper_1106_0557_gb300 import Plan
+    src = rand_src(N, 17).astype(NP[dtype])
+    with Plan(N, (1.0, 0.5, 2.0), dtype) as p:
+        dev = p.solve(torch.from_numpy(src).cuda()).cpu().numpy()
+        host = p.solve_host(src)
+        again = p.solve_host(src)
+    assert np.array_equal(host, dev)
+    assert np.array_equal(again, dev)
