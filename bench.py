@@ -372,6 +372,34 @@ def run_serving(n_requests, slots, fp64_class="df64"):
 # ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
+def host_copy_rates(hsrc, hphi, stream, reps=20):
+    """Plain pinned-host <-> device copy rates of one solve's buffers, the
+    floor under the end-to-end rate: each direction alone, and both at once
+    on two streams."""
+    import torch
+    d = torch.empty(hsrc.shape, dtype=hsrc.dtype, device="cuda")
+    d2 = torch.empty_like(d)
+    other = torch.cuda.Stream()
+    out = {}
+    for name in ("h2d", "d2h", "both"):
+        for rep in range(reps + 3):
+            if rep == 3:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+            if name in ("h2d", "both"):
+                with torch.cuda.stream(stream):
+                    d.copy_(hsrc, non_blocking=True)
+            if name in ("d2h", "both"):
+                with torch.cuda.stream(other):
+                    hphi.copy_(d2, non_blocking=True)
+        torch.cuda.synchronize()
+        secs = (time.perf_counter() - t0) / reps
+        out["ms_" + name] = round(secs * 1e3, 4)
+        out["gbs_" + name] = round(hsrc.numel() * hsrc.element_size() * (2 if name == "both" else 1)
+                                   / secs / 1e9, 1)
+    return out
+
+
 def run_isofft(args, ws, rank, local):
     import torch
 
@@ -407,6 +435,7 @@ def run_isofft(args, ws, rank, local):
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier(ws)
+        plan.check(stream)  # raises if a bounded device wait gave up
         ms = ev0.elapsed_time(ev1)
         launches = native.ipf_launch_count() - l0
         passes = plan.pass_times()
@@ -474,6 +503,7 @@ def run_isofft(args, ws, rank, local):
     t_e2e = reduce_max(t_e2e, ws, dev)
     e2e_value = reduce_sum(e2e_steps, ws, dev) / t_e2e
     io_bytes = hsrc.numel() * hsrc.element_size()
+    copy_rates = host_copy_rates(hsrc, hphi, stream)
 
     # roofline of the dominant kernel (the longest mean device time)
     k32 = kernel_times(passes32, bytes32, fused)
@@ -518,7 +548,7 @@ def run_isofft(args, ws, rank, local):
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": traffic, "algorithmic_bytes": k32[dname]["bytes"]},
         "e2e": {"value": e2e_value, "unit": "solves/s", "steps": e2e_steps, "h2d_bytes_per_step": io_bytes,
-                "d2h_bytes_per_step": io_bytes},
+                "d2h_bytes_per_step": io_bytes, "plain_copies": copy_rates},
         "batch": batch,
         "serving": serve,
         "cpu_baseline": cpu,

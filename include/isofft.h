@@ -128,8 +128,21 @@ int ipf_solve(ipf_plan_t plan, const void *d_src, void *d_phi, void *stream);
  * chunks already on the device (and, on the way back, with the inverse
  * passes of later chunks); with pinned host buffers most of the copy time
  * hides behind those passes.  Pass events (IPF_FLAG_PASS_EVENTS) are not
- * recorded by this call. */
+ * recorded by this call.  Returns what ipf_plan_check would return for the
+ * solve (IPF_TIMEOUT if a device wait of the z pass gave up). */
 int ipf_solve_host(ipf_plan_t plan, const void *h_src, void *h_phi, void *stream);
+
+/* Device-side status of the solves made on this plan since the previous
+ * check.  The z pass (forward z transform x spectrum x inverse) receives its
+ * tiles through the tensor memory accelerator and waits for each tile's
+ * copies on a shared-memory barrier; every such wait is bounded (2 s).  When
+ * one gives up, the pass lets its outstanding copies land (bounded again),
+ * stops early and sets a flag in a device word of the plan; the potential
+ * of that solve is then unspecified.  This call synchronises `stream`, reads
+ * and clears that word: IPF_OK, IPF_TIMEOUT (a wait gave up) or
+ * IPF_CUDA_ERROR (a pass refused to run because its shared memory was not
+ * aligned as the tensor copies require). */
+int ipf_plan_check(ipf_plan_t plan, void *stream);
 
 /* One solve that allocates no memory, for callers that cannot call
  * cudaMalloc: a code that has given all device memory to its own pool, a
@@ -153,6 +166,10 @@ int ipf_solve_host(ipf_plan_t plan, const void *h_src, void *h_phi, void *stream
  * call before any stream capture.  Asynchronous on `stream`. */
 int ipf_solve_noalloc(const int64_t n[3], const double h[3], int dtype, const void *d_src, void *d_phi,
                       void *stream);
+
+/* ipf_plan_check for the solves of ipf_solve_noalloc on the current device
+ * (their status word lives in the same static array). */
+int ipf_noalloc_check(void *stream);
 
 /* Submit `count` independent solves, possibly of different shapes and
  * dtypes; plans[i] solves d_src[i] into d_phi[i].  A plan may appear only

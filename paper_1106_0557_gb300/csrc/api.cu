@@ -116,6 +116,7 @@ struct ipf_plan_s {
     size_t W_bytes = 0;
     void *tables = nullptr;  // tw_x | rtw | tw_y | tw_z
     const void *tw_x = nullptr, *rtw = nullptr, *tw_y = nullptr, *tw_z = nullptr;
+    unsigned *status = nullptr;  // device word after the tables: bit 0 = a bounded wait gave up
     void *stage = nullptr;  // device staging for ipf_solve_host
     // ipf_solve_host pipeline: a copy stream and per-chunk events
     static constexpr int kChunks = 8;
@@ -197,9 +198,12 @@ int upload_tables(ipf_plan_s *p, cudaStream_t st)
     fill_roots<T>(h, orr, p->M[0], Lx);
     fill_roots<T>(h, oy, My, My);
     fill_roots<T>(h, oz, Mz, Mz);
-    cudaError_t e = cudaMalloc(&p->tables, tot * sizeof(T));
+    const size_t tbytes = (tot * sizeof(T) + 15) / 16 * 16;
+    cudaError_t e = cudaMalloc(&p->tables, tbytes + 16);
     if (e != cudaSuccess) return cuda_status(e);
+    p->status = (unsigned *)((char *)p->tables + tbytes);
     e = cudaMemcpyAsync(p->tables, h.data(), tot * sizeof(T), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->status, 0, 16, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(e);
     T *b = (T *)p->tables;
@@ -208,6 +212,22 @@ int upload_tables(ipf_plan_s *p, cudaStream_t st)
     p->tw_y = b + oy;
     p->tw_z = b + oz;
     return IPF_OK;
+}
+
+// Reads and clears the plan's device status word after the work queued on
+// `st` so far: IPF_TIMEOUT when a pass's bounded wait for its copies gave up,
+// IPF_CUDA_ERROR when a pass refused its shared-memory layout.
+int read_status(ipf_plan_s *p, cudaStream_t st)
+{
+    unsigned w = 0;
+    cudaError_t e = cudaMemcpyAsync(&w, p->status, sizeof(w), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (w == 0) return IPF_OK;
+    e = cudaMemsetAsync(p->status, 0, sizeof(w), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
+    return (w & 1u) ? IPF_TIMEOUT : IPF_CUDA_ERROR;
 }
 
 int acquire_spectrum(ipf_plan_s *p, cudaStream_t st)
@@ -310,7 +330,7 @@ cudaError_t enqueue_solve(ipf_plan_s *p, const void *src, void *phi, cudaStream_
     }
     if (ev_on) cudaEventRecord(ev[2], st);
     e = launch_z_convolve<T>(Mz, p->W, p->tw_z, (const T *)p->spec->G, (const T *)p->spec->Gs,
-                             (T)p->gscale, Nz, My, Lx, st);
+                             (T)p->gscale, Nz, My, Lx, p->status, st);
     if (e != cudaSuccess) return e;
     if (ev_on) cudaEventRecord(ev[3], st);
     if (fused) {
@@ -378,7 +398,7 @@ cudaError_t enqueue_solve_host(ipf_plan_s *p, const void *h_src, void *h_phi, cu
     }
     if (e == cudaSuccess)
         e = launch_z_convolve<T>(Mz, p->W, p->tw_z, (const T *)p->spec->G, (const T *)p->spec->Gs, (T)p->gscale, Nz,
-                                 My, Lx, st);
+                                 My, Lx, p->status, st);
     for (int k = 0; k < chunks && e == cudaSuccess; ++k) {
         const int z0 = k * per, nz = z0 + per <= Nz ? per : Nz - z0;
         if (nz <= 0) break;
@@ -608,7 +628,14 @@ int ipf_solve_host(ipf_plan_t p, const void *h_src, void *h_phi, void *stream)
                     : p->dtype == IPF_F64 ? enqueue_solve_host<double>(p, h_src, h_phi, st)
                                           : enqueue_solve_host<df64>(p, h_src, h_phi, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    return cuda_status(e);
+    if (e != cudaSuccess) return cuda_status(e);
+    return read_status(p, st);
+}
+
+int ipf_plan_check(ipf_plan_t p, void *stream)
+{
+    if (!p) return IPF_INVALID_ARG;
+    return read_status(p, (cudaStream_t)stream);
 }
 
 int ipf_submit_batch(const ipf_plan_t *plans, int count, const void *const *d_src, void *const *d_phi,

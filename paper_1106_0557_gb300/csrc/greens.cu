@@ -56,20 +56,26 @@ static __global__ void k_cos_axis(const double *__restrict__ in, double *__restr
 }
 
 // oct [Z][Y][X] (X = Mx/2 + 1) -> G in the z pass's tiled layout
-// [Y][ntx][Z][tx] (kx = xt * tx + c, zero past Kx = Mx/2) and Gs [Y][Z], of
-// type T; column kx = 0 packs the kx = 0 and kx = Mx/2 planes.
+// [Y][ntx][blk] with block element kz * tx + c (kx = xt * tx + c, zero past
+// Kx = Mx/2, zero in the padding past Z * tx) and Gs [Y][Z], of type T;
+// column kx = 0 packs the kx = 0 and kx = Mx/2 planes.
 template <typename T>
 static __global__ void k_pack(const double *__restrict__ oct, T *__restrict__ G, T *__restrict__ Gs, int X,
-                              int Y, int Z, int tx, int ntx, double scale)
+                              int Y, int Z, int tx, int ntx, int blk, double scale)
 {
     const int Kx = X - 1;
-    const int64_t tot = (int64_t)Y * ntx * Z * tx;
+    const int64_t tot = (int64_t)Y * ntx * blk;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i % tx);
-        const int64_t kz = (i / tx) % Z;
-        const int xt = (int)((i / ((int64_t)tx * Z)) % ntx);
-        const int64_t ky = i / ((int64_t)tx * Z * ntx);
+        const int j = (int)(i % blk);
+        if (j >= Z * tx) {
+            G[i] = (T)0;
+            continue;
+        }
+        const int c = j % tx;
+        const int64_t kz = j / tx;
+        const int xt = (int)((i / blk) % ntx);
+        const int64_t ky = i / ((int64_t)blk * ntx);
         const int kx = xt * tx + c;
         const double *o = oct + (kz * Y + ky) * X;
         if (kx >= Kx) {
@@ -90,7 +96,7 @@ size_t spectrum_elems(const int64_t M[3])
     const int tx = z_tile_for<T>((int)M[2]);
     const size_t Y = M[1] / 2 + 1, Z = M[2] / 2 + 1, Kx = M[0] / 2;
     const size_t ntx = (Kx + tx - 1) / tx;
-    return Y * ntx * Z * tx + Y * Z;
+    return Y * ntx * (size_t)z_spec_block(tx, (int)Z, (int)sizeof(T)) + Y * Z;
 }
 template size_t spectrum_elems<float>(const int64_t *);
 template size_t spectrum_elems<double>(const int64_t *);
@@ -193,7 +199,8 @@ cudaError_t build_green_spectrum(const int64_t M[3], const double hn[3], T *G, T
         const double scale = 1.0 / (2.0 * (double)M[0] * (double)M[1] * (double)M[2]);
         const int tx = z_tile_for<T>((int)M[2]);
         const int ntx = (int)((M[0] / 2 + tx - 1) / tx);
-        k_pack<T><<<grid_for((int64_t)Y * ntx * Z * tx), 256, 0, st>>>(o1, G, Gs, X, Y, Z, tx, ntx, scale);
+        const int blk = z_spec_block(tx, Z, (int)sizeof(T));
+        k_pack<T><<<grid_for((int64_t)Y * ntx * blk), 256, 0, st>>>(o1, G, Gs, X, Y, Z, tx, ntx, blk, scale);
         count_launch();
         e = cudaGetLastError();
     }
@@ -261,7 +268,8 @@ cudaError_t enqueue_green_spectrum(const int64_t M[3], const double hn[3], T *G,
     const double scale = 1.0 / (2.0 * (double)M[0] * (double)M[1] * (double)M[2]);
     const int tx = z_tile_for<T>((int)M[2]);
     const int ntx = (int)((M[0] / 2 + tx - 1) / tx);
-    k_pack<T><<<grid_for((int64_t)Y * ntx * Z * tx), 256, 0, st>>>(o1, G, Gs, X, Y, Z, tx, ntx, scale);
+    const int blk = z_spec_block(tx, Z, (int)sizeof(T));
+    k_pack<T><<<grid_for((int64_t)Y * ntx * blk), 256, 0, st>>>(o1, G, Gs, X, Y, Z, tx, ntx, blk, scale);
     count_launch();
     return cudaGetLastError();
 }

@@ -30,9 +30,11 @@ template <typename T>
 cudaError_t launch_y_forward(int L, void *W, const void *tw, int Ny, int Kx, int Nz, cudaStream_t st);
 template <typename T>
 cudaError_t launch_y_inverse(int L, void *W, const void *tw, int Ny, int Kx, int Nz, cudaStream_t st);
+// `status` (device word, may be null) gets bit 0 set when one of the pass's
+// bounded waits for its tile copies gave up (ipf_plan_check reads it).
 template <typename T>
 cudaError_t launch_z_convolve(int L, void *W, const void *tw, const T *G, const T *Gs, T gscale, int Nz,
-                              int My, int Kx, cudaStream_t st);
+                              int My, int Kx, unsigned *status, cudaStream_t st);
 
 // Fused x+y forward / y+x inverse for planes with My = Mx = 2 LX: one
 // cluster of 4 CTAs per z plane (see passes.cuh).
@@ -49,6 +51,14 @@ cudaError_t launch_yx_inverse(int LX, void *W, typename IoReal<T>::type *phi, co
 // Green's spectrum is stored in tiles of this width (0: unsupported L).
 template <typename T>
 int z_tile_for(int L);
+
+// Elements of one (k_y', kx tile) block of the cached spectrum: nkz x tx
+// values, padded so that every block starts on a 16-byte boundary (the z pass
+// copies a block with one bulk copy).
+constexpr int z_spec_block(int tx, int nkz, int elem_bytes)
+{
+    return (nkz * tx + 16 / elem_bytes - 1) / (16 / elem_bytes) * (16 / elem_bytes);
+}
 
 // Device bytes of the cached Green's spectrum of a doubled mesh M.
 template <typename T>

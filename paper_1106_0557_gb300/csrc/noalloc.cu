@@ -78,7 +78,7 @@ Carve carve(const int64_t N[3], const int64_t M[3])
     const size_t cs = 2 * sizeof(T);
     const int64_t Lx = M[0] / 2;
     Carve c;
-    size_t off = 0;
+    size_t off = align256(sizeof(unsigned));  // the status word comes first
     c.tw_x = off;
     off += align256(Lx * cs);
     c.rtw = off;
@@ -132,7 +132,7 @@ int solve_noalloc(const int64_t N[3], const int64_t M[3], const double hn[3], do
     if (e == cudaSuccess)
         e = launch_x_forward<T>(Lx, (const T *)src, W, tw_x, rtw, Nx, Ny, My, (int64_t)Ny * Nz, st);
     if (e == cudaSuccess) e = launch_y_forward<T>(My, W, tw_y, Ny, Lx, Nz, st);
-    if (e == cudaSuccess) e = launch_z_convolve<T>(Mz, W, tw_z, G, Gs, (T)gscale, Nz, My, Lx, st);
+    if (e == cudaSuccess) e = launch_z_convolve<T>(Mz, W, tw_z, G, Gs, (T)gscale, Nz, My, Lx, (unsigned *)b, st);
     if (e == cudaSuccess) e = launch_y_inverse<T>(My, W, tw_y, Ny, Lx, Nz, st);
     if (e == cudaSuccess) e = launch_x_inverse<T>(Lx, W, (T *)phi, tw_x, rtw, Nx, Ny, My, (int64_t)Ny * Nz, st);
     return e == cudaSuccess ? IPF_OK : IPF_CUDA_ERROR;
@@ -142,6 +142,22 @@ int solve_noalloc(const int64_t N[3], const int64_t M[3], const double hn[3], do
 }  // namespace isofft
 
 using namespace isofft;
+
+extern "C" int ipf_noalloc_check(void *stream)
+{
+    void *base = nullptr;
+    if (scratch_address(&base) != cudaSuccess) return IPF_CUDA_ERROR;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned w = 0;
+    cudaError_t e = cudaMemcpyAsync(&w, base, sizeof(w), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return IPF_CUDA_ERROR;
+    if (w == 0) return IPF_OK;
+    e = cudaMemsetAsync(base, 0, sizeof(w), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return IPF_CUDA_ERROR;
+    return (w & 1u) ? IPF_TIMEOUT : IPF_CUDA_ERROR;
+}
 
 extern "C" int ipf_solve_noalloc(const int64_t n[3], const double h[3], int dtype, const void *d_src, void *d_phi,
                                  void *stream)

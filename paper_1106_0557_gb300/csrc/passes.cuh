@@ -29,6 +29,8 @@
 //   K5 x inverse : W rows y < Ny -> real rows, x < Nx           (output pruned)
 #pragma once
 #include "fft_engine.cuh"
+#include "launch.h"
+#include "tma.cuh"
 
 namespace isofft {
 
@@ -151,20 +153,22 @@ struct ColCfg {
 };
 
 // z pass tiles: TX columns of the two lines ky and My - ky (2 TX lines),
-// processed by a persistent CTA.  While it transforms one tile, cp.async
-// copies the next tile's non-zero half (z < Mz/2) and the spectrum values
-// into shared staging slots, so loads never wait in registers.  FP64 tiles
-// are narrower: FP64 arithmetic, not memory, bounds that path.
-constexpr size_t z_smem(int tx, int nt, int L, int e, int rb)
+// processed by a persistent CTA.  While it transforms one tile, the tensor
+// memory accelerator copies the next tile's non-zero half (z < Mz/2, one box
+// per line group and 256 planes) and its Green's spectrum block into the
+// other of two shared-memory slot sets.  FP64 tiles are narrower: FP64
+// arithmetic, not memory, bounds that path.
+constexpr size_t z_smem(int tx, int L, int rb)
 {
-    return (size_t)L * 2 * tx * 2 * rb                // exchange buffer
-           + 2 * (size_t)2 * tx * nt * (e / 2) * 2 * rb  // staged input, two slot sets
-           + (size_t)2 * tx * nt * e * rb;              // staged spectrum
+    return (size_t)L * 2 * tx * 2 * rb                                  // exchange buffer
+           + 2 * (size_t)2 * (L / 2) * tx * 2 * rb                      // input, two slot sets
+           + 2 * 2 * (size_t)z_spec_block(tx, L / 2 + 1, rb) * rb  // spectrum blocks, two sets
+           + 16;                                                      // the sets' mbarriers
 }
 constexpr int z_tile_width(int rb, int nt, int L, int e)
 {
     int tx = rb == 4 ? 8 : 4;
-    while (tx > 1 && (2 * tx * nt > (e > 8 ? 512 : 1024) || z_smem(tx, nt, L, e, rb) > 200 * 1024)) tx /= 2;
+    while (tx > 1 && (2 * tx * nt > (e > 8 ? 512 : 1024) || z_smem(tx, L, rb) > 200 * 1024)) tx /= 2;
     return tx;
 }
 
@@ -172,25 +176,42 @@ template <typename T, int L>
 struct ZCfg {
     static constexpr int E = ZShape<T, L>::E;
     static constexpr int NT = L / E;
+    static constexpr int LH = L / 2;
     static constexpr int TX = z_tile_width((int)sizeof(T), NT, L, E);
     static constexpr int COLS = 2 * TX;
     static constexpr int THREADS = COLS * NT;
+    // tensor boxes: at most 256 planes each, NZB of them per line group
+    static constexpr int NZB = (LH + 255) / 256;
+    static constexpr int BOXZ = LH / NZB;
+    static constexpr int EPC = (int)sizeof(Cx<T>) / 8;  // 8-byte tensor elements per complex
+    static constexpr int GBLK = z_spec_block(TX, LH + 1, (int)sizeof(T));
     static constexpr size_t XCH = (size_t)L * COLS * sizeof(Cx<T>);
-    static constexpr size_t STAGE_IN = (size_t)THREADS * (E / 2) * sizeof(Cx<T>);  // one slot set
-    static constexpr size_t STAGE_G = (size_t)THREADS * E * sizeof(T);             // one slot set
-    static constexpr size_t SMEM = z_smem(TX, NT, L, E, (int)sizeof(T));
+    static constexpr size_t IN_GROUP = (size_t)LH * TX * sizeof(Cx<T>);  // one line group
+    static constexpr size_t IN_SET = 2 * IN_GROUP;
+    static constexpr size_t G_BLK = (size_t)GBLK * sizeof(T);
+    static constexpr size_t G_SET = 2 * G_BLK;  // the blocks of k_y' = pr and of My/2 (pr = 0 only)
+    static constexpr size_t SMEM = z_smem(TX, L, (int)sizeof(T));
+    static_assert(SMEM == XCH + 2 * IN_SET + 2 * G_SET + 16, "z pass shared-memory layout");
     static_assert(THREADS <= 1024, "z tile too large");
     static_assert(SMEM <= 227 * 1024, "z tile exceeds shared memory");
+    static_assert(BOXZ * NZB == LH && BOXZ <= 256, "tensor boxes must tile the half line");
+    static_assert(TX * sizeof(Cx<T>) % 16 == 0, "tensor box rows must be multiples of 16 bytes");
+    static_assert(XCH % 128 == 0 && IN_GROUP % 128 == 0 && ((size_t)BOXZ * TX * sizeof(Cx<T>)) % 128 == 0,
+                  "tensor copy destinations must stay 128-byte aligned");
+    static_assert(G_BLK % 16 == 0, "bulk copies move multiples of 16 bytes");
+    static_assert(E % 2 == 0, "the z pass splits a thread's points at L/2");
 };
 
 // Layout of the Green's spectrum read by the z pass: [ky'][kx tile][kz'][TX]
 // with ky' <= My/2, kz' <= Mz/2 and kx = tile * TX + c (padded with zeros
-// past Mx/2), so the TX x (Mz/2 + 1) block of one tile is contiguous.
+// past Mx/2); the (Mz/2 + 1) x TX block of one tile is contiguous and padded
+// to blk elements (a multiple of 16 bytes).
 struct ZSpecLayout {
-    int tx, ntx, nkz;  // tile width, kx tiles, Mz/2 + 1
+    int tx, ntx, nkz, blk;  // tile width, kx tiles, Mz/2 + 1, block stride
+    __host__ __device__ size_t block(int kyp, int xt) const { return ((size_t)kyp * ntx + xt) * blk; }
     __host__ __device__ size_t at(int kyp, int xt, int kzp, int c) const
     {
-        return (((size_t)kyp * ntx + xt) * nkz + kzp) * tx + c;
+        return block(kyp, xt) + (size_t)kzp * tx + c;
     }
 };
 
@@ -683,30 +704,34 @@ k_yx_inverse(Cx<T> *__restrict__ W, In<T> *__restrict__ phi, const Cx<T> *__rest
 // K3: z forward, multiply by the Green's spectrum, z inverse.
 // Tiles: (pair p, kx tile xt), tile = p * ntx + xt; pair p holds the lines
 // (ky, My - ky) = (p, My - p) for p > 0 and (0, My/2) for p = 0.  A
-// persistent grid walks the tiles; each CTA keeps the next tile's loads in
+// persistent grid walks the tiles; each CTA keeps the next tile's copies in
 // flight during the current tile's transforms.
 // gscale multiplies the cached spectrum (the cache stores it for widths
 // divided by min(h); G scales as h^2).
+//
+// Copies: thread 0 issues, per tile, one tensor-map box per line group and
+// 256 planes of W (tmW: 8-byte elements, dims {Kx EPC, My, Nz}; planes
+// z >= Nz and columns kx >= Kx read as zero) and a bulk copy of the tile's
+// spectrum block (a second one for the pair p = 0, whose line My/2 has its
+// own k_y').  Slot set s = tile parity; its mbarrier completes once per use.
+// A set is refilled at the top of the tile after the one that read it, and
+// that tile's reads are all behind the CTA barriers of the transform that
+// followed them.
 // ---------------------------------------------------------------------
 template <typename T, int L>
 __global__ void __launch_bounds__(ZCfg<T, L>::THREADS, 1)
-k_z_convolve(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, const T *__restrict__ G,
-             const T *__restrict__ Gs, T gscale, int Nz, int My, int Kx, int ntiles)
+k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw,
+             const T *__restrict__ G, const T *__restrict__ Gs, T gscale, int Nz, int My, int Kx, int ntiles,
+             unsigned *__restrict__ status)
 {
     using C = ZCfg<T, L>;
-    constexpr int E = C::E, NT = C::NT, TX = C::TX, COLS = C::COLS, TH = C::THREADS;
+    constexpr int E = C::E, NT = C::NT, TX = C::TX, COLS = C::COLS;
     constexpr int Lh = L / 2;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Cx<T> *sm = reinterpret_cast<Cx<T> *>(smem_raw);
-    // Per-thread staging slots.  The input slots come in two sets that
-    // alternate with the tile parity: the next tile's copies are issued right
-    // after this tile's slots are read, before anything consumes those reads,
-    // and cp.async is not ordered against them.  The spectrum slots are read
-    // by the multiply, which in-order issue completes before the next copies
-    // into them are issued, so one set suffices.
-    Cx<T> *st_in0 = reinterpret_cast<Cx<T> *>(smem_raw + C::XCH);  // 2 x [E/2][TH]
-    T *st_g = reinterpret_cast<T *>(smem_raw + C::XCH + 2 * C::STAGE_IN);  // [E][TH]
-    constexpr int IN_SET = (E / 2) * TH;
+    extern __shared__ __align__(128) unsigned char zsmem[];
+    Cx<T> *sm = reinterpret_cast<Cx<T> *>(zsmem);             // exchange buffer
+    unsigned char *s_in = zsmem + C::XCH;                      // [set][g][z < Lh][TX]
+    T *s_g = reinterpret_cast<T *>(zsmem + C::XCH + 2 * C::IN_SET);  // [set][2][GBLK]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(zsmem + C::XCH + 2 * C::IN_SET + 2 * C::G_SET);
     // thread -> (column c, group g, position t): a warp holds both groups of
     // a few positions, so each position row of the exchange buffer is written
     // whole and the warp's shared-memory accesses are conflict-free
@@ -717,71 +742,72 @@ k_z_convolve(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, const T *__res
     const int col = g * TX + c;
     const int ntx = (Kx + TX - 1) / TX;
     const size_t zstride = (size_t)My * Kx;
-    const ZSpecLayout lay{TX, ntx, Lh + 1};
+    const ZSpecLayout lay{TX, ntx, Lh + 1, C::GBLK};
 
-    auto line_of = [&](int tile, int &ky, int &kx, int &pr, int &xt) {
-        pr = tile / ntx;
-        xt = tile - pr * ntx;
-        ky = g == 0 ? pr : (pr == 0 ? My / 2 : My - pr);
-        kx = xt * TX + c;
-    };
-    // stage the non-zero half of this thread's line of `tile` into slot set `set`
-    auto stage_input = [&](int tile, int set) {
-        int ky, kx, pr, xt;
-        line_of(tile, ky, kx, pr, xt);
-        const bool active = kx < Kx;
-        const Cx<T> *base = W + (size_t)ky * Kx + (active ? kx : 0);
-        Cx<T> *st_in = st_in0 + set * IN_SET;
+    // tensor copies need 128-byte aligned destinations (uniform per CTA)
+    if (smem_addr(zsmem) & 127u) {
+        if (tid == 0 && status) atomicOr(status, 2u);
+        return;
+    }
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+
+    auto issue = [&](int tile, int set) {  // thread 0
+        const int pr = tile / ntx, xt = tile - pr * ntx;
+        const int ky1 = pr == 0 ? My / 2 : My - pr;
+        uint64_t *b = &bar[set];
+        mbar_arrive_expect_tx(b, (uint32_t)(C::IN_SET + (pr == 0 ? 2 : 1) * C::G_BLK));
+        unsigned char *dst = s_in + set * C::IN_SET;
 #pragma unroll
-        for (int m = 0; m < E / 2; ++m) {
-            const int z = t + m * NT;
-            const bool ok = active && z < Nz;
-            cp_async<sizeof(Cx<T>)>(&st_in[m * TH + tid], ok ? base + (size_t)z * zstride : W, ok);
+        for (int zb = 0; zb < C::NZB; ++zb) {
+            const size_t off = (size_t)zb * C::BOXZ * TX * sizeof(Cx<T>);
+            tma_load_3d(dst + off, &tmW, xt * TX * C::EPC, pr, zb * C::BOXZ, b);
+            tma_load_3d(dst + C::IN_GROUP + off, &tmW, xt * TX * C::EPC, ky1, zb * C::BOXZ, b);
         }
-    };
-    // stage the spectrum values at this thread's bins of `tile`
-    auto stage_spectrum = [&](int tile) {
-        int ky, kx, pr, xt;
-        line_of(tile, ky, kx, pr, xt);
-        const int kyp = ky <= My - ky ? ky : My - ky;
-#pragma unroll
-        for (int m = 0; m < E; ++m) {
-            const int kz = t + m * NT;
-            const int kzp = kz <= L - kz ? kz : L - kz;
-            cp_async<sizeof(T)>(&st_g[m * TH + tid], G + lay.at(kyp, xt, kzp, c), true);
-        }
+        T *gdst = s_g + (size_t)set * 2 * C::GBLK;
+        bulk_load(gdst, G + lay.block(pr, xt), (uint32_t)C::G_BLK, b);
+        if (pr == 0) bulk_load(gdst + C::GBLK, G + lay.block(My / 2, xt), (uint32_t)C::G_BLK, b);
     };
 
     ColXch<T, L, E, COLS> xch{sm, col};
     using Rad = typename ZShape<T, L>::Rad;
     typename TwRegsOf<T, L, E, Rad>::type twr;  // this thread's twiddles, for every tile
     twr.load(tw, t);
-    int tile = blockIdx.x;
-    if (tile < ntiles) {
-        stage_input(tile, 0);
-        cp_async_commit();
-        stage_spectrum(tile);
-        cp_async_commit();
-    }
-    for (int it = 0; tile < ntiles; tile += gridDim.x, ++it) {
+    int tile = blockIdx.x, it = 0;
+    bool ok = true;
+    if (tid == 0 && tile < ntiles) issue(tile, 0);
+    for (; tile < ntiles; tile += gridDim.x, ++it) {
         const int next = tile + gridDim.x;
         const int set = it & 1;
-        const Cx<T> *st_in = st_in0 + set * IN_SET;
-        int ky, kx, pr, xt;
-        line_of(tile, ky, kx, pr, xt);
+        if (tid == 0 && next < ntiles) issue(next, set ^ 1);
+        const bool landed = mbar_wait_bounded(&bar[set], (uint32_t)(it >> 1) & 1u, kCopyWaitNs);
+        if (!__syncthreads_and(landed)) {
+            ok = false;
+            break;
+        }
+        const int pr = tile / ntx, xt = tile - pr * ntx;
+        const int ky = g == 0 ? pr : (pr == 0 ? My / 2 : My - pr);
+        const int kx = xt * TX + c;
         const bool active = kx < Kx;
         const int kyp = ky <= My - ky ? ky : My - ky;
 
-        cp_async_wait<1>();  // this tile's input has landed (its spectrum may not have)
+        // z < Lh from the staged boxes (zeros past Nz), the upper half is zero
+        const Cx<T> *sin = reinterpret_cast<const Cx<T> *>(s_in + set * C::IN_SET + g * C::IN_GROUP) + t * TX + c;
         Cx<T> v[E];
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = m < E / 2 ? st_in[m * TH + tid] : Cx<T>{(T)0, (T)0};
-        if (next < ntiles) stage_input(next, set ^ 1);
-        cp_async_commit();
+        for (int m = 0; m < E; ++m) v[m] = m < E / 2 ? sin[m * NT * TX] : Cx<T>{(T)0, (T)0};
 
         run_stages_reg<T, L, E, true>(v, t, twr, xch, Rad{});
 
-        cp_async_wait<1>();  // this tile's spectrum has landed
+        // spectrum at kz = t + m NT: kz' = kz below Lh, L - kz from Lh on
+        const T *sg = s_g + ((size_t)set * 2 + (pr == 0 ? g : 0)) * C::GBLK;
+        const T *g_lo = sg + t * TX + c;
+        const T *g_hi = sg + (L - t) * TX + c;
+        auto gval = [&](int m) -> T { return m < E / 2 ? g_lo[m * NT * TX] : g_hi[-m * NT * TX]; };
         const bool packed = xt == 0 && c == 0;  // the kx = 0 / Mx/2 column
         if (xt == 0) {
             // the packed column needs the partner bin (-ky, -kz)
@@ -798,7 +824,7 @@ k_z_convolve(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, const T *__res
                     const int kz = t + m * NT;
                     const int kzp = kz <= L - kz ? kz : L - kz;
                     const Cx<T> partner = cconj(sm[(kz == 0 ? 0 : L - kz) * COLS + gp * TX]);
-                    const T gp_ = st_g[m * TH + tid] * gscale;
+                    const T gp_ = gval(m) * gscale;
                     const T gm_ = gsrow[kzp] * gscale;
                     v[m] = {v[m].x * gp_ + partner.x * gm_, v[m].y * gp_ + partner.y * gm_};
                 }
@@ -807,10 +833,8 @@ k_z_convolve(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, const T *__res
         }
         if (!packed) {
 #pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = cscale(v[m], st_g[m * TH + tid] * gscale);
+            for (int m = 0; m < E; ++m) v[m] = cscale(v[m], gval(m) * gscale);
         }
-        if (next < ntiles) stage_spectrum(next);
-        cp_async_commit();
 
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = cswap(v[m]);
@@ -824,7 +848,16 @@ k_z_convolve(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, const T *__res
             }
         }
     }
-    cp_async_wait<0>();
+    if (!ok) {
+        // a wait gave up: flag it, then let this tile's and the next tile's
+        // copies land (bounded again) before the CTA's shared memory is freed
+        if (tid == 0) {
+            if (status) atomicOr(status, 1u);
+            mbar_wait_bounded(&bar[it & 1], (uint32_t)(it >> 1) & 1u, kCopyWaitNs);
+            if (tile + (int)gridDim.x < ntiles)
+                mbar_wait_bounded(&bar[(it + 1) & 1], (uint32_t)((it + 1) >> 1) & 1u, kCopyWaitNs);
+        }
+    }
 }
 
 }  // namespace isofft

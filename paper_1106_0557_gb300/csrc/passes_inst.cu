@@ -245,13 +245,36 @@ static int resident_ctas(F *func, int threads, size_t smem, std::atomic<int> &ca
     return v;
 }
 
+// cuTensorMapEncodeTiled, resolved once through the runtime (no link
+// dependency on the driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                   CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                   CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled()
+{
+    static std::atomic<EncodeTiledFn> fn{nullptr};
+    EncodeTiledFn f = fn.load(std::memory_order_acquire);
+    if (f) return f;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p)
+        return nullptr;
+    f = reinterpret_cast<EncodeTiledFn>(p);
+    fn.store(f, std::memory_order_release);
+    return f;
+}
+
 template <typename T, int L>
 static cudaError_t run_z(void *W, const void *tw, const T *G, const T *Gs, T gscale, int Nz, int My, int Kx,
-                         cudaStream_t st)
+                         unsigned *status, cudaStream_t st)
 {
     using C = ZCfg<T, L>;
     static std::atomic<uint64_t> done{0};
     static std::atomic<int> slots{0};
+    if (((uintptr_t)W & 15) || ((uintptr_t)G & 15)) return cudaErrorMisalignedAddress;
     cudaError_t e = ensure_smem(k_z_convolve<T, L>, C::SMEM, done);
     if (e != cudaSuccess) return e;
     const int ntx = (Kx + C::TX - 1) / C::TX;
@@ -259,18 +282,31 @@ static cudaError_t run_z(void *W, const void *tw, const T *G, const T *Gs, T gsc
     int grid = resident_ctas(k_z_convolve<T, L>, C::THREADS, C::SMEM, slots);
     if (grid <= 0) return cudaErrorInvalidConfiguration;
     if (grid > ntiles) grid = ntiles;
-    k_z_convolve<T, L><<<grid, C::THREADS, C::SMEM, st>>>((Cx<T> *)W, (const Cx<T> *)tw, G, Gs, gscale, Nz, My,
-                                                         Kx, ntiles);
+    // W as 8-byte elements [Nz][My][Kx * EPC]; one box = TX columns of one
+    // line for BOXZ planes
+    EncodeTiledFn encode = encode_tiled();
+    if (!encode) return cudaErrorNotSupported;
+    CUtensorMap map;
+    const cuuint64_t dims[3] = {(cuuint64_t)Kx * C::EPC, (cuuint64_t)My, (cuuint64_t)Nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)Kx * sizeof(Cx<T>), (cuuint64_t)My * Kx * sizeof(Cx<T>)};
+    const cuuint32_t box[3] = {(cuuint32_t)(C::TX * C::EPC), 1u, (cuuint32_t)C::BOXZ};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, W, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    k_z_convolve<T, L><<<grid, C::THREADS, C::SMEM, st>>>(map, (Cx<T> *)W, (const Cx<T> *)tw, G, Gs, gscale, Nz,
+                                                         My, Kx, ntiles, status);
     count_launch();
     return cudaGetLastError();
 }
 template <typename R_>
 cudaError_t launch_z_convolve(int L, void *W, const void *tw, const R_ *G, const R_ *Gs, R_ gscale,
-                                  int Nz, int My, int Kx, cudaStream_t st)
+                                  int Nz, int My, int Kx, unsigned *status, cudaStream_t st)
 {
     switch (L) {
 #define X_(n) \
-    case n: return run_z<R_, n>(W, tw, G, Gs, gscale, Nz, My, Kx, st);
+    case n: return run_z<R_, n>(W, tw, G, Gs, gscale, Nz, My, Kx, status, st);
         ISOFFT_COL_LENGTHS(X_)
 #undef X_
     default: return cudaErrorInvalidValue;
@@ -288,7 +324,7 @@ int z_tile_for(int L)
     }
 }
 template cudaError_t launch_z_convolve<Real>(int, void *, const void *, const Real *, const Real *, Real, int,
-                                             int, int, cudaStream_t);
+                                             int, int, unsigned *, cudaStream_t);
 template int z_tile_for<Real>(int);
 #endif
 

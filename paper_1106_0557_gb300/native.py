@@ -57,6 +57,8 @@ def _declare(L):
         "ipf_solve": [vp, vp, vp, vp],
         "ipf_solve_host": [vp, vp, vp, vp],
         "ipf_solve_noalloc": [i64p, dp, ctypes.c_int, vp, vp, vp],
+        "ipf_plan_check": [vp, vp],
+        "ipf_noalloc_check": [vp],
         "ipf_submit_batch": [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), vp],
         "ipf_plan_pass_times": [vp, ctypes.POINTER(ctypes.c_float)],
         "ipf_greens_cache_bytes": [ctypes.POINTER(ctypes.c_size_t)],
@@ -153,6 +155,16 @@ def ipf_solve(plan, d_src, d_phi, stream=0):
 def ipf_solve_host(plan, h_src, h_phi, stream=0):
     _check(lib().ipf_solve_host(ctypes.c_void_p(plan), ctypes.c_void_p(int(h_src)), ctypes.c_void_p(int(h_phi)),
                                 ctypes.c_void_p(int(stream))), "ipf_solve_host")
+
+
+def ipf_plan_check(plan, stream=0):
+    """Synchronise `stream`; raise IsofftError if a bounded device wait of
+    the plan's solves gave up since the previous check."""
+    _check(lib().ipf_plan_check(ctypes.c_void_p(plan), ctypes.c_void_p(int(stream))), "ipf_plan_check")
+
+
+def ipf_noalloc_check(stream=0):
+    _check(lib().ipf_noalloc_check(ctypes.c_void_p(int(stream))), "ipf_noalloc_check")
 
 
 def ipf_solve_noalloc(n, h, dtype, d_src, d_phi, stream=0):

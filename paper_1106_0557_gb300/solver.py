@@ -77,6 +77,11 @@ class Plan:
     def pass_times(self):
         return native.ipf_plan_pass_times(self.handle)
 
+    def check(self, stream=None):
+        """Synchronise the stream and raise if a bounded device wait of this
+        plan's solves gave up since the previous check."""
+        native.ipf_plan_check(self.handle, _stream_handle(stream))
+
     def close(self):
         if getattr(self, "handle", None):
             native.ipf_plan_destroy(self.handle)

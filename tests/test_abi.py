@@ -77,5 +77,6 @@ def test_null_handles():
     assert native.lib().ipf_submit_batch(None, 0, None, None, None) == native.IPF_OK
     assert native.lib().ipf_submit_batch(None, 1, None, None, None) == native.IPF_INVALID_ARG
     assert native.lib().ipf_plan_pass_times(None, None) == native.IPF_INVALID_ARG
+    assert native.lib().ipf_plan_check(None, None) == native.IPF_INVALID_ARG
     assert native.ipf_greens_cache_bytes() >= 0
     assert native.ipf_launch_count() >= 0

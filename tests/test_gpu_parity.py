@@ -35,6 +35,7 @@ def gpu_solve(src, h, dtype, flags=0):
         d = torch.from_numpy(s).cuda()
         out = p.solve(d)
         torch.cuda.synchronize()
+        p.check()  # no bounded device wait gave up
         return out.cpu().numpy().astype(np.float64), s.astype(np.float64)
 
 
