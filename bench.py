@@ -320,8 +320,8 @@ def run_serving(n_requests, slots, fp64_class="df64"):
     """Config-5 style serving: cubic N log-uniform in [32, 384], 70 % FP32
     (tolerance 1e-5) / 30 % FP64-class (tolerance 1e-12, served with the
     `fp64_class` dtype), HBM budget 120 GB.  Saturated throughput (all
-    requests at t=0), then Poisson arrivals at 0.8 x that rate for p50/p99
-    latency; and the FP32 class served vs the same shapes solved one at a
+    requests at t=0), then Poisson arrivals at 0.5, 0.8 and 0.95 x that rate
+    for p50/p99 latency (0.8 headlined); and the FP32 class served vs the same shapes solved one at a
     time in plain FP64."""
     import torch
 
@@ -335,10 +335,18 @@ def run_serving(n_requests, slots, fp64_class="df64"):
     be.warm_spectra(reqs)
     srv = serving.Server(be, budget_bytes=120e9, slots=slots)
     sat = serving.saturated_throughput(srv, be, reqs)
-    rate = 0.8 * sat["solves_per_s"]
-    reqs2 = mk(serving.poisson_arrivals(len(spec), rate, seed=1))
-    srv.run(reqs2)
-    lat = serving.latency_stats(reqs2)
+    # Poisson arrivals at 0.5, 0.8 and 0.95 x the saturated rate; 0.8 is the
+    # headline
+    sweep = []
+    for load in (0.5, 0.8, 0.95):
+        r = load * sat["solves_per_s"]
+        rq = mk(serving.poisson_arrivals(len(spec), r, seed=1))
+        srv.run(rq)
+        st = serving.latency_stats(rq)
+        sweep.append({"load": load, "rate": round(r, 1), "p50_ms": round(st["p50_ms"], 3),
+                      "p99_ms": round(st["p99_ms"], 3), "solves_per_s": round(st["solves_per_s"], 1)})
+        if load == 0.8:
+            rate, lat = r, st
     # FP32 class served (saturated) vs plain unbatched FP64 on the same shapes
     sub = [r for r in reqs if r.dtype == "f32"][:300]
     served32 = serving.saturated_throughput(srv, be, sub)
@@ -362,7 +370,7 @@ def run_serving(n_requests, slots, fp64_class="df64"):
             "mix": "cubic N log-uniform [32,384], 70%% f32 / 30%% FP64-class served as %s" % fp64_class,
             "saturated_solves_per_s": round(sat["solves_per_s"], 1),
             "poisson_rate": round(rate, 1), "p50_ms": round(lat["p50_ms"], 3), "p99_ms": round(lat["p99_ms"], 3),
-            "solves_per_s": round(lat["solves_per_s"], 1),
+            "solves_per_s": round(lat["solves_per_s"], 1), "load_sweep": sweep,
             "f32_served_solves_per_s": round(served32["solves_per_s"], 1),
             "f64_plain_unbatched_solves_per_s": round(plain64, 1),
             "f32_served_over_f64_plain": round(served32["solves_per_s"] / plain64, 2),

@@ -79,10 +79,13 @@ enum {
 /* Create a solver for an Nx x Ny x Nz mesh of widths h (paper Sec. 3.2,
  * `Create(PoissonSolver, CellWidth, nTotalCells, ...)`).
  *   out        receives the plan handle (NULL on failure).
- *   n          {Nx, Ny, Nz}, each >= 1 and at most 768: the doubled mesh
+ *   n          {Nx, Ny, Nz}, each >= 1 and at most 1152: the doubled mesh
  *              (2N rounded up to one of 32, 48, 64, 96, 128, 192, 256, 384,
- *              512, 768, 1024, 1536) must fit the largest supported length,
- *              else IPF_UNSUPPORTED_SIZE.
+ *              512, 768, 1024, 1536, 2304) must fit the largest supported
+ *              length, else IPF_UNSUPPORTED_SIZE.  1152^3 cells in FP32 need
+ *              about 37 GB of device memory: a 24.5 GB workspace and a 6 GB
+ *              spectrum, plus 24.5 GB of FP64 scratch while the spectrum is
+ *              built.
  *   h          {hx, hy, hz}, each finite and > 0.
  *   dtype      IPF_F32, IPF_F64 or IPF_DF64.  The Green's spectrum is always
  *              built in FP64 and rounded to the plan's dtype.

@@ -38,6 +38,8 @@ def lib():
         L.oracle_green.argtypes = [ctypes.c_long, ctypes.c_long, ctypes.c_long, p]
         L.oracle_green_table.restype = None
         L.oracle_green_table.argtypes = [p, p, p]
+        L.oracle_green_block.restype = None
+        L.oracle_green_block.argtypes = [p, p, p, p]
         L.oracle_fft1d.restype = ctypes.c_int
         L.oracle_fft1d.argtypes = [p, i64, ctypes.c_int]
         L.oracle_fft3d.restype = ctypes.c_int
@@ -93,6 +95,16 @@ def green_table(M, h):
     MM, hh = _i64(M), _f64(h)
     out = np.empty((MM[2], MM[1], MM[0]), dtype=np.float64)
     lib().oracle_green_table(_ptr(MM), _ptr(hh), _ptr(out))
+    return out
+
+
+def green_block(lo, n, h):
+    """Eq. 6 (Eq. 9 at the origin) at the offsets lo + [0, n) per axis: real
+    array [n_z][n_y][n_x].  The corner-impulse response of a box, read in
+    slabs at sizes where the doubled table would not fit in memory."""
+    L0, NN, hh = _i64(lo), _i64(n), _f64(h)
+    out = np.empty((NN[2], NN[1], NN[0]), dtype=np.float64)
+    lib().oracle_green_block(_ptr(L0), _ptr(NN), _ptr(hh), _ptr(out))
     return out
 
 

@@ -92,6 +92,18 @@ void oracle_green_table(const int64_t M[3], const double h[3], double *G)
     }
 }
 
+/* Eq. 6 (Eq. 9 at the origin) on the block of offsets d = lo + [0, n) per
+ * axis: the potential of a unit source at a corner, read at the cells of a
+ * box, without the doubled table.  Output is a real [n2][n1][n0] array. */
+void oracle_green_block(const int64_t lo[3], const int64_t n[3], const double h[3], double *out)
+{
+    for (int64_t k = 0; k < n[2]; ++k)
+        for (int64_t j = 0; j < n[1]; ++j)
+            for (int64_t i = 0; i < n[0]; ++i)
+                out[(k * n[1] + j) * n[0] + i] =
+                    oracle_green((long)(lo[0] + i), (long)(lo[1] + j), (long)(lo[2] + k), h);
+}
+
 /* ------------------------------------------------------------------ */
 /* Recursive mixed-radix FFT                                            */
 /* ------------------------------------------------------------------ */

@@ -216,6 +216,10 @@ template <typename T>
 struct Dft<T, 16> {
     static ISOFFT_HD void run(Cx<T> (&a)[16]) { DftCT<T, 4, 4>::run(a); }
 };
+template <typename T>
+struct Dft<T, 24> {
+    static ISOFFT_HD void run(Cx<T> (&a)[24]) { DftCT<T, 8, 3>::run(a); }
+};
 
 // DFT of R inputs whose upper half a[R/2..R) is zero (first stage of a line
 // that is half zero padding): even bins are the length-R/2 DFT of a, odd bins
@@ -430,7 +434,9 @@ ISOFFT_SHAPE(Shape32, 384, 12, 12, 4, 4, 2)
 ISOFFT_SHAPE(Shape32, 512, 8, 8, 8, 8)
 ISOFFT_SHAPE(Shape32, 768, 12, 12, 4, 4, 4)
 ISOFFT_SHAPE(Shape32, 1024, 16, 16, 8, 8)
+ISOFFT_SHAPE(Shape32, 1152, 12, 12, 12, 4, 2)
 ISOFFT_SHAPE(Shape32, 1536, 12, 12, 4, 4, 4, 2)
+ISOFFT_SHAPE(Shape32, 2304, 12, 12, 12, 4, 4)
 ISOFFT_SHAPE(Shape64, 1024, 8, 8, 8, 8, 2)
 #undef ISOFFT_SHAPE
 
@@ -446,12 +452,32 @@ struct Shape<df64, L> : Shape64<L> {};  // float pairs: register footprint of FP
 // The z pass holds two lines groups per tile and stages its prefetches in
 // shared memory; for 512-point FP32 lines it runs 16 points per thread on
 // 512 threads so the transform never competes with a 64-register cap.
+// TW_REGS: the pass keeps its twiddles in registers across tiles (else it
+// reads them from the table, through L1).
 template <typename T, int L>
-struct ZShape : Shape<T, L> {};
+struct ZShape : Shape<T, L> {
+    static constexpr bool TW_REGS = sizeof(T) == 4 || Shape<T, L>::E <= 8;
+};
 template <>
 struct ZShape<float, 512> {
     static constexpr int E = 16;
     using Rad = Radices<8, 8, 8>;
+    static constexpr bool TW_REGS = true;
+};
+// 2304-point lines read their twiddles from the table (a thread's share
+// would not fit in registers next to its points).  FP32 takes 24 points per
+// thread and three stages, so that a tile of two columns (16 bytes, the
+// narrowest tensor-copy row) fits 384 threads; 16-byte FP64-class points
+// keep 12 per thread on one-column tiles.
+template <typename T>
+struct ZShape<T, 2304> : Shape<T, 2304> {
+    static constexpr bool TW_REGS = false;
+};
+template <>
+struct ZShape<float, 2304> {
+    static constexpr int E = 24;
+    using Rad = Radices<24, 24, 4>;
+    static constexpr bool TW_REGS = false;
 };
 
 }  // namespace isofft

@@ -11,8 +11,8 @@ namespace isofft {
 
 // Doubled-mesh lengths the kernels are instantiated for (any M >= 2N - 1
 // gives the same cropped result, so a plan rounds 2N up to the next one).
-constexpr int kSupportedM[] = {32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536};
-constexpr int kMaxM = 1536;
+constexpr int kSupportedM[] = {32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2304};
+constexpr int kMaxM = 2304;
 
 // Counts every kernel launch the library makes (ipf_launch_count).
 void count_launch();

@@ -145,9 +145,10 @@ struct ColCfg {
     static constexpr int TX = TX0 * NT <= 512 ? TX0 : (512 / NT >= 1 ? 512 / NT : 1);
     static constexpr int THREADS = TX * NT;
     static constexpr size_t SMEM = (size_t)L * TX * sizeof(Cx<T>);
-    // FP32 forward: registers low enough for 3 resident CTAs per SM (the
-    // inverse, which holds every point of its lines, would spill)
-    static constexpr int MIN_BLOCKS_FWD = sizeof(T) == 4 && THREADS <= 512 ? 3 : 1;
+    // FP32 forward: registers low enough for 3 resident CTAs per SM with 8
+    // points per thread, 2 with 12 (the inverse, which holds every point of
+    // its lines, and the 16-point shape would spill under such caps)
+    static constexpr int MIN_BLOCKS_FWD = sizeof(T) == 4 && THREADS <= 512 ? (E <= 8 ? 3 : (E <= 12 ? 2 : 1)) : 1;
     static_assert(THREADS <= 1024, "column tile too large");
     static_assert(SMEM <= 227 * 1024, "column tile exceeds shared memory");
 };
@@ -180,8 +181,14 @@ struct ZCfg {
     static constexpr int TX = z_tile_width((int)sizeof(T), NT, L, E);
     static constexpr int COLS = 2 * TX;
     static constexpr int THREADS = COLS * NT;
-    // tensor boxes: at most 256 planes each, NZB of them per line group
-    static constexpr int NZB = (LH + 255) / 256;
+    // tensor boxes: NZB equal boxes of at most 256 planes per line group
+    static constexpr int boxes()
+    {
+        int n = 1;
+        while (LH % n != 0 || LH / n > 256) ++n;
+        return n;
+    }
+    static constexpr int NZB = boxes();
     static constexpr int BOXZ = LH / NZB;
     static constexpr int EPC = (int)sizeof(Cx<T>) / 8;  // 8-byte tensor elements per complex
     static constexpr int GBLK = z_spec_block(TX, LH + 1, (int)sizeof(T));
@@ -700,6 +707,26 @@ k_yx_inverse(Cx<T> *__restrict__ W, In<T> *__restrict__ phi, const Cx<T> *__rest
     }
 }
 
+// Twiddles of the z pass: held in registers across tiles, or (TWR false)
+// read from the table by each stage.
+template <bool TWR, typename T, int L, int E, typename Rad>
+struct ZTwiddles {
+    using type = typename TwRegsOf<T, L, E, Rad>::type;
+};
+template <typename T, int L, int E, typename Rad>
+struct ZTwiddles<false, T, L, E, Rad> {
+    using type = TwRegs<T, L, E, 1>;  // holds nothing
+};
+template <bool TWR, bool HALF, typename T, int L, int E, typename TW, typename Xch, typename Rad>
+__device__ __forceinline__ void z_fft(Cx<T> (&v)[E], int t, const TW &twr, const Cx<T> *__restrict__ tw, Xch &xch,
+                                      Rad)
+{
+    if constexpr (TWR)
+        run_stages_reg<T, L, E, HALF>(v, t, twr, xch, Rad{});
+    else
+        run_stages<T, L, E, HALF>(v, t, tw, xch, Rad{});
+}
+
 // ---------------------------------------------------------------------
 // K3: z forward, multiply by the Green's spectrum, z inverse.
 // Tiles: (pair p, kx tile xt), tile = p * ntx + xt; pair p holds the lines
@@ -775,7 +802,8 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
 
     ColXch<T, L, E, COLS> xch{sm, col};
     using Rad = typename ZShape<T, L>::Rad;
-    typename TwRegsOf<T, L, E, Rad>::type twr;  // this thread's twiddles, for every tile
+    constexpr bool TWR = ZShape<T, L>::TW_REGS;
+    typename ZTwiddles<TWR, T, L, E, Rad>::type twr;  // this thread's twiddles, for every tile (when TW_REGS)
     twr.load(tw, t);
     int tile = blockIdx.x, it = 0;
     bool ok = true;
@@ -801,7 +829,7 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = m < E / 2 ? sin[m * NT * TX] : Cx<T>{(T)0, (T)0};
 
-        run_stages_reg<T, L, E, true>(v, t, twr, xch, Rad{});
+        z_fft<TWR, true, T, L, E>(v, t, twr, tw, xch, Rad{});
 
         // spectrum at kz = t + m NT: kz' = kz below Lh, L - kz from Lh on
         const T *sg = s_g + ((size_t)set * 2 + (pr == 0 ? g : 0)) * C::GBLK;
@@ -838,7 +866,7 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
 
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = cswap(v[m]);
-        run_stages_reg<T, L, E, false>(v, t, twr, xch, Rad{});
+        z_fft<TWR, false, T, L, E>(v, t, twr, tw, xch, Rad{});
         if (active) {
             Cx<T> *base = W + (size_t)ky * Kx + kx;
 #pragma unroll

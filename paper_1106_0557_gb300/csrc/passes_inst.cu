@@ -35,9 +35,13 @@ static cudaError_t ensure_smem(F *func, size_t bytes, std::atomic<uint64_t> &don
     return e;
 }
 
-#define ISOFFT_ROW_LENGTHS(X) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768)
+#define ISOFFT_ROW_LENGTHS(X) \
+    X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768) X(1152)
 #define ISOFFT_COL_LENGTHS(X) \
-    X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768) X(1024) X(1536)
+    X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768) X(1024) X(1536) X(2304)
+// row lengths with fused x+y kernels (their doubled length is a column length
+// up to 1536)
+#define ISOFFT_FUSED_LENGTHS(X) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768)
 
 #if ISOFFT_GROUP == 1
 template <typename T, int L>
@@ -194,7 +198,7 @@ cudaError_t launch_xy_forward(int LX, const In<R_> *src, void *W, const void *tw
     switch (LX) {
 #define X_(n) \
     case n: return run_xy<R_, n>(src, W, twx, rtw, twy, Nx, Ny, Nz, st);
-        ISOFFT_ROW_LENGTHS(X_)
+        ISOFFT_FUSED_LENGTHS(X_)
 #undef X_
     default: return cudaErrorInvalidValue;
     }
@@ -206,7 +210,7 @@ cudaError_t launch_yx_inverse(int LX, void *W, In<R_> *phi, const void *twx, con
     switch (LX) {
 #define X_(n) \
     case n: return run_yx<R_, n>(W, phi, twx, rtw, twy, Nx, Ny, Nz, st);
-        ISOFFT_ROW_LENGTHS(X_)
+        ISOFFT_FUSED_LENGTHS(X_)
 #undef X_
     default: return cudaErrorInvalidValue;
     }
@@ -217,7 +221,7 @@ bool xy_fusable(int LX)
     switch (LX) {
 #define X_(n) \
     case n: return XYCfg<R_, n>::OK;
-        ISOFFT_ROW_LENGTHS(X_)
+        ISOFFT_FUSED_LENGTHS(X_)
 #undef X_
     default: return false;
     }

@@ -169,6 +169,30 @@ def binary_spheroid(n=384, e=0.28, a=0.5, rho=1.0):
     return Workload("binary-spheroid-%d" % n, (2 * n, n, n), (h, h, h), bodies, lo=(-2.0, -1.0, -1.0))
 
 
+# The mesh resolutions of the convergence figures of Secs. 4.1 and 4.2.
+PAPER_LADDER = (48, 144, 288, 384, 576, 768, 1152)
+
+
+def paper_sphere(n, R=1.0, rho=1.0):
+    """The Sec. 4.1 test: a uniform sphere of radius 1 centred at the origin
+    of the box [-1.2, 1.2]^3, n^3 cells."""
+    h = 2.4 / n
+    return Workload("paper-sphere-%d" % n, (n, n, n), (h, h, h),
+                    [{"kind": "sphere", "center": (0.0, 0.0, 0.0), "radius": R, "rho": rho}],
+                    lo=(-1.2, -1.2, -1.2))
+
+
+def paper_spheroid(n, e=0.9, a=0.5, rho=1.0):
+    """The Sec. 4.2 test: a uniform oblate spheroid (axis z, eccentricity
+    0.9, semi-major axis 0.5) centred at the origin of a box of size two in
+    every dimension, [-1, 1]^3, n^3 cells."""
+    h = 2.0 / n
+    b = a * math.sqrt(1.0 - e * e)
+    return Workload("paper-spheroid-%d" % n, (n, n, n), (h, h, h),
+                    [{"kind": "spheroid", "center": (0.0, 0.0, 0.0), "a": a, "b": b, "rho": rho}],
+                    lo=(-1.0, -1.0, -1.0))
+
+
 BATCH_SIZES = (32, 48, 64, 96, 128)
 
 

@@ -49,7 +49,7 @@ def test_status_strings():
     ((4, 4, 4), (1.0, -1.0, 1.0), "f32", native.IPF_INVALID_ARG),
     ((4, 4, 4), (1.0, float("nan"), 1.0), "f64", native.IPF_INVALID_ARG),
     ((4, 4, 4), (1.0, 0.0, 1.0), "f64", native.IPF_INVALID_ARG),
-    ((4, 4, 800), (1.0, 1.0, 1.0), "f32", native.IPF_UNSUPPORTED_SIZE),
+    ((4, 4, 1200), (1.0, 1.0, 1.0), "f32", native.IPF_UNSUPPORTED_SIZE),
     ((2000, 4, 4), (1.0, 1.0, 1.0), "f64", native.IPF_UNSUPPORTED_SIZE),
 ])
 def test_validation_without_gpu(n, h, dtype, status):

@@ -196,6 +196,9 @@ LONG_SHAPES = [
     ((700, 9, 8), (1.0, 1.0, 1.0)),      # Mx = 1536
     ((9, 700, 8), (1.0, 2.0, 1.0)),      # My = 1536
     ((8, 9, 700), (1.0, 1.0, 1.0)),      # Mz = 1536
+    ((1000, 9, 8), (1.0, 1.0, 1.0)),     # Mx = 2304 (rows of 1152)
+    ((9, 1100, 8), (1.0, 2.0, 1.0)),     # My = 2304
+    ((8, 9, 1152), (1.0, 1.0, 0.5)),     # Mz = 2304, the largest N
     ((5, 3, 2), (1.0, 1.0, 1.0)),        # every axis padded up to 32
 ]
 

@@ -64,6 +64,22 @@ def test_table_replicates_green(oracle_mod, N, h):
     assert np.array_equal(T, np.roll(T[:, :, ::-1], 1, axis=2))
 
 
+@pytest.mark.parametrize("h", [(1.0, 1.0, 1.0), (0.5, 0.25, 1.0)])
+def test_green_block_is_the_table_read_in_a_box(oracle_mod, h):
+    """The block evaluator equals the doubled table on its non-negative
+    offsets (so a corner impulse's response can be read slab by slab), and a
+    block away from the origin equals the scalar function cell by cell."""
+    N = (5, 4, 6)
+    M = tuple(2 * n for n in N)
+    T = oracle_mod.green_table(M, h)
+    B = oracle_mod.green_block((0, 0, 0), N, h)
+    assert np.array_equal(B, T[:N[2], :N[1], :N[0]])
+    lo = (3, 7, 2)
+    B = oracle_mod.green_block(lo, (3, 2, 4), h)
+    for k, j, i in itertools.product(range(4), range(2), range(3)):
+        assert B[k, j, i] == oracle_mod.green((lo[0] + i, lo[1] + j, lo[2] + k), h)
+
+
 @pytest.mark.parametrize("M,h", [((8, 8, 8), (1.0, 1.0, 1.0)), ((12, 8, 10), (0.5, 0.25, 1.0))])
 def test_spectrum_real_even(oracle_mod, M, h):
     Gt = oracle_mod.green_spectrum(M, h)
