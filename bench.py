@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--no-paper-scale", action="store_true",
+                    help="skip the 1152^3 solve (the paper's largest ladder point)")
     return ap.parse_args()
 
 
@@ -267,6 +269,50 @@ def run_reference(args, ws, rank):
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the paper's largest mesh
+# ---------------------------------------------------------------------------
+def run_paper_scale(steps=20, warmup=3):
+    """The Sec. 4.2 spheroid at 1152^3 cells (doubled mesh 2304^3), FP32,
+    in place: the mesh of the paper's largest weak-scaling run (~1 s per
+    solve on 13 824 Opteron cores).  Set-up (the Green's spectrum) is
+    excluded, as the paper computes it once at initialisation."""
+    import torch
+
+    from paper_1106_0557_gb300 import Plan, native, sources
+    w = sources.paper_spheroid(1152)
+    t0 = time.perf_counter()
+    plan = Plan(w.N, w.h, "f32", flags=native.IPF_FLAG_PASS_EVENTS)
+    setup_s = time.perf_counter() - t0
+    src = sources.rasterize_torch(w.bodies, w.N, w.h, w.lo, dtype=torch.float32)
+    for _ in range(warmup):
+        plan.solve(src, src)
+    torch.cuda.synchronize()
+    plan.pass_times()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        plan.solve(src, src)
+    e1.record()
+    torch.cuda.synchronize()
+    plan.check()
+    ms = e0.elapsed_time(e1) / steps
+    passes = plan.pass_times()
+    pb = pass_bytes(w.N, plan.padded_shape, 4)
+    nbytes = sum(pb[k] for k in PASSES)
+    plan.close()
+    del src
+    torch.cuda.empty_cache()
+    native.ipf_greens_cache_trim(0)
+    return {"workload": "Sec. 4.2 spheroid (e=0.9, a=0.5) in [-1,1]^3, 1152^3 cells, doubled mesh 2304^3, FP32, "
+                        "in place", "ms_per_solve": round(ms, 3), "steps": steps,
+            "hbm_gbs_algorithmic": round(nbytes / (ms / 1e3) / 1e9, 1),
+            "kernels": {KERNELS[k]: {"ms": round(t, 3), "gbs": round(pb[k] / (t / 1e3) / 1e9, 1)}
+                        for k, t in zip(PASSES, passes)},
+            "setup_s": round(setup_s, 2),
+            "paper": "about 1 s per solve on ~13 000 Opteron cores (Cray XT-4), same mesh"}
 
 
 # ---------------------------------------------------------------------------
@@ -521,6 +567,7 @@ def run_isofft(args, ws, rank, local):
     traffic = profile_traffic(dname, "f32_%d" % n)
 
     batch = None if args.no_batch else run_batch()
+    paper_scale = None if args.no_paper_scale else run_paper_scale()
     serve = None if args.no_serve else run_serving(args.serve_requests, args.serve_slots)
 
     cpu = None
@@ -559,6 +606,7 @@ def run_isofft(args, ws, rank, local):
                 "d2h_bytes_per_step": io_bytes, "plain_copies": copy_rates},
         "batch": batch,
         "serving": serve,
+        "paper_scale": paper_scale,
         "cpu_baseline": cpu,
         "gpu_launches": launches,
         "clocks": clocks,

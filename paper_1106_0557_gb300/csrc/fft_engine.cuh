@@ -456,7 +456,7 @@ struct Shape<df64, L> : Shape64<L> {};  // float pairs: register footprint of FP
 // reads them from the table, through L1).
 template <typename T, int L>
 struct ZShape : Shape<T, L> {
-    static constexpr bool TW_REGS = sizeof(T) == 4 || Shape<T, L>::E <= 8;
+    static constexpr bool TW_REGS = true;
 };
 template <>
 struct ZShape<float, 512> {
@@ -478,6 +478,18 @@ struct ZShape<float, 2304> {
     static constexpr int E = 24;
     using Rad = Radices<24, 24, 4>;
     static constexpr bool TW_REGS = false;
+};
+
+// The x passes hold one row per (half) warp; a 256-point FP32 row runs 16
+// points per thread and two radix-16 stages, so it takes one exchange
+// instead of two and fewer twiddle loads (the x passes are bound by the
+// L1/shared pipe).
+template <typename T, int L>
+struct XShape : Shape<T, L> {};
+template <>
+struct XShape<float, 256> {
+    static constexpr int E = 16;
+    using Rad = Radices<16, 16>;
 };
 
 }  // namespace isofft

@@ -85,15 +85,31 @@ struct ColXch {
     }
 };
 
-// Shared-memory exchange for row passes: one line per row, positions
-// XOR-swizzled within blocks of 16 (p ^ ((p >> 4) & 15)).  With 8-byte
-// points and a row held by one warp, the swizzle sends the warp's 32
-// accesses of every exchange pattern (stride-8 first-stage writes, blocked
-// second-stage writes, consecutive reads) to each bank pair exactly twice.
-template <int L>
+// Shared-memory exchange for row passes: one line per row.  A warp's 8-byte
+// accesses are served per half-warp (16-byte ones per quarter-warp), which
+// is conflict-free when those lanes hit distinct bank pairs (quads).
+// * Positions are XOR-swizzled within blocks of 16: p ^ ((p >> 4) & 15), or
+//   for 8-byte points of 8- and 12-point shapes from 128 points up
+//   p ^ ((p >> 4) & 7) ^ (bit 6 of p moved to bit 3), which also separates
+//   the blocked writes of the second stage (positions 64 a + b + 8 r).
+// * Rows shorter than 128 points are several to a half-warp, so the row
+//   stride is padded (by 2, 4 or 8 points) to spread the rows over the
+//   banks.
+// The choice per length comes from counting wavefronts of every exchange
+// pattern of the row shapes.
+template <typename T, int L>
 struct RowPad {
-    static constexpr int LP = (L + 15) & ~15;
-    static __device__ __forceinline__ int at(int p) { return p ^ ((p >> 4) & 15); }
+    static constexpr bool WIDE = sizeof(Cx<T>) == 16;
+    static constexpr int PAD = L <= 24 ? 2 : (L <= 48 ? 4 : (L <= 96 && !WIDE ? 8 : 0));
+    static constexpr int LP = ((L + 15) & ~15) + PAD;
+    static constexpr bool ALT = !WIDE && L >= 128 && XShape<T, L>::E != 16;
+    static __device__ __forceinline__ int at(int p)
+    {
+        if constexpr (ALT)
+            return p ^ ((p >> 4) & 7) ^ (((p >> 6) & 1) << 3);
+        else
+            return p ^ ((p >> 4) & 15);
+    }
 };
 
 // A row held by at most one warp needs only a warp barrier between the
@@ -117,21 +133,21 @@ struct RowXch {
 #pragma unroll
         for (int q = 0; q < G::B; ++q)
 #pragma unroll
-            for (int r = 0; r < R; ++r) s[RowPad<L>::at(G::out_pos(t, q, r))] = v[q + r * G::B];
+            for (int r = 0; r < R; ++r) s[RowPad<T, L>::at(G::out_pos(t, q, r))] = v[q + r * G::B];
         row_sync<G::NT>();
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = s[RowPad<L>::at(t + m * G::NT)];
+        for (int m = 0; m < E; ++m) v[m] = s[RowPad<T, L>::at(t + m * G::NT)];
         row_sync<G::NT>();
     }
 };
 
 template <typename T, int L>
 struct RowCfg {
-    static constexpr int E = Shape<T, L>::E;
+    static constexpr int E = XShape<T, L>::E;
     static constexpr int NT = L / E;
     static constexpr int NL = NT >= 256 ? 1 : 256 / NT;  // rows per CTA
     static constexpr int THREADS = NL * NT;
-    static constexpr size_t SMEM = (size_t)NL * RowPad<L>::LP * sizeof(Cx<T>);
+    static constexpr size_t SMEM = (size_t)NL * RowPad<T, L>::LP * sizeof(Cx<T>);
 };
 
 // Column tiles of the y passes: up to 128 bytes of complex per row and at
@@ -254,7 +270,7 @@ __device__ __forceinline__ void x_forward_row_at(const In<T> *in, Cx<T> *__restr
                                                  const Cx<T> *__restrict__ tw, const Cx<T> *__restrict__ rtw, int Nx,
                                                  bool active, Cx<T> *line, int t)
 {
-    constexpr int E = Shape<T, L>::E, NT = L / E;
+    constexpr int E = XShape<T, L>::E, NT = L / E;
     using IO = IoReal<T>;
 
     // pairs (x[2p], x[2p+1]) as one complex point; p >= L/2 is padding
@@ -275,19 +291,19 @@ __device__ __forceinline__ void x_forward_row_at(const In<T> *in, Cx<T> *__restr
         }
     }
     RowXch<T, L, E> xch{line};
-    run_stages<T, L, E, true>(v, t, tw, xch, typename Shape<T, L>::Rad{});
+    run_stages<T, L, E, true>(v, t, tw, xch, typename XShape<T, L>::Rad{});
 
     // split the half-length transform Z into the real row's spectrum:
     //   2X[k] = (Z[k] + conj Z[L-k]) + W_2L^k (-i)(Z[k] - conj Z[L-k]),
     //   2X[0] = 2(Re Z0 + Im Z0), 2X[L] = 2(Re Z0 - Im Z0).
 #pragma unroll
-    for (int m = 0; m < E; ++m) line[RowPad<L>::at(t + m * NT)] = v[m];
+    for (int m = 0; m < E; ++m) line[RowPad<T, L>::at(t + m * NT)] = v[m];
     row_sync<NT>();
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         const int k = t + m * NT;
         const Cx<T> zk = v[m];
-        const Cx<T> zr = cconj(line[RowPad<L>::at(k == 0 ? 0 : L - k)]);
+        const Cx<T> zr = cconj(line[RowPad<T, L>::at(k == 0 ? 0 : L - k)]);
         const Cx<T> a = cadd(zk, zr);
         const Cx<T> b = cmul_mi(csub(zk, zr));
         Cx<T> p = cadd(a, cmul(b, rtw[k]));
@@ -312,11 +328,11 @@ __device__ __forceinline__ void x_inverse_row_at(const Cx<T> *in, In<T> *__restr
                                                  const Cx<T> *__restrict__ rtw, int Nx, bool active, Cx<T> *line,
                                                  int t)
 {
-    constexpr int E = Shape<T, L>::E, NT = L / E;
+    constexpr int E = XShape<T, L>::E, NT = L / E;
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         const int k = t + m * NT;
-        line[RowPad<L>::at(k)] = active ? ld_cx<CG>(in + k) : Cx<T>{(T)0, (T)0};
+        line[RowPad<T, L>::at(k)] = active ? ld_cx<CG>(in + k) : Cx<T>{(T)0, (T)0};
     }
     row_sync<NT>();
     // rebuild the half-length spectrum of z[m] = y[2m] + i y[2m+1]:
@@ -325,13 +341,13 @@ __device__ __forceinline__ void x_inverse_row_at(const Cx<T> *in, In<T> *__restr
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         const int k = t + m * NT;
-        const Cx<T> xk = line[RowPad<L>::at(k)];
+        const Cx<T> xk = line[RowPad<T, L>::at(k)];
         Cx<T> a, b;
         if (k == 0) {
             a = {xk.x + xk.y, (T)0};
             b = {xk.x - xk.y, (T)0};
         } else {
-            const Cx<T> xr = cconj(line[RowPad<L>::at(L - k)]);
+            const Cx<T> xr = cconj(line[RowPad<T, L>::at(L - k)]);
             a = cadd(xk, xr);
             b = cmul(csub(xk, xr), cconj(rtw[k]));
         }
@@ -342,7 +358,7 @@ __device__ __forceinline__ void x_inverse_row_at(const Cx<T> *in, In<T> *__restr
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = cswap(v[m]);
     RowXch<T, L, E> xch{line};
-    run_stages<T, L, E, false>(v, t, tw, xch, typename Shape<T, L>::Rad{});
+    run_stages<T, L, E, false>(v, t, tw, xch, typename XShape<T, L>::Rad{});
     const bool vec = (Nx & 1) == 0;
 #pragma unroll
     for (int m = 0; m < E / 2; ++m) {
@@ -439,7 +455,7 @@ k_x_forward(const In<T> *__restrict__ src, Cx<T> *__restrict__ W, const Cx<T> *_
     using C = RowCfg<T, L>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int t = threadIdx.x % C::NT, l = threadIdx.x / C::NT;
-    Cx<T> *line = reinterpret_cast<Cx<T> *>(smem_raw) + l * RowPad<L>::LP;
+    Cx<T> *line = reinterpret_cast<Cx<T> *>(smem_raw) + l * RowPad<T, L>::LP;
     const int64_t row = (int64_t)blockIdx.x * C::NL + l;  // row = z * Ny + y
     const bool active = row < nrows;
     x_forward_row<T, L>(src, W, tw, rtw, Nx, Ny, My, active ? row : 0, active, line, t);
@@ -453,7 +469,7 @@ k_x_inverse(const Cx<T> *__restrict__ W, In<T> *__restrict__ phi, const Cx<T> *_
     using C = RowCfg<T, L>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int t = threadIdx.x % C::NT, l = threadIdx.x / C::NT;
-    Cx<T> *line = reinterpret_cast<Cx<T> *>(smem_raw) + l * RowPad<L>::LP;
+    Cx<T> *line = reinterpret_cast<Cx<T> *>(smem_raw) + l * RowPad<T, L>::LP;
     const int64_t row = (int64_t)blockIdx.x * C::NL + l;
     const bool active = row < nrows;
     x_inverse_row<T, L>(W, phi, tw, rtw, Nx, Ny, My, active ? row : 0, active, line, t);
@@ -499,14 +515,14 @@ struct XYCfg {
     static constexpr int LY = 2 * LX;
     static constexpr int THREADS = 512;
     static constexpr int MIN_BLOCKS = sizeof(T) == 4 ? 2 : 1;  // FP32: two CTAs per SM
-    static constexpr int NTX = LX / Shape<T, LX>::E;
+    static constexpr int NTX = LX / XShape<T, LX>::E;
     static constexpr int NL = THREADS / NTX;  // rows per round
     static constexpr int NTY = LY / Shape<T, LY>::E;
     static constexpr int TX = THREADS / NTY;  // columns per round
     static_assert(NTX <= THREADS && NTY <= THREADS, "line too long for a fused tile");
     static constexpr size_t CS = sizeof(Cx<T>);
     // exchange buffers of the two phases
-    static constexpr size_t XCH_X = (size_t)NL * RowPad<LX>::LP * CS;
+    static constexpr size_t XCH_X = (size_t)NL * RowPad<T, LX>::LP * CS;
     static constexpr size_t XCH_Y = (size_t)LY * TX * CS;
     // one stage of prefetched input (each phase double-buffers its stage)
     static constexpr size_t ROWS_F = (size_t)NL * LX * sizeof(In<T>);  // real source rows
@@ -609,7 +625,7 @@ k_xy_forward(const In<T> *__restrict__ src, Cx<T> *__restrict__ W, const Cx<T> *
             const bool active = y < y_hi;
             const In<T> *in = reinterpret_cast<const In<T> *>(stage + buf * C::ROWS_F) + l * LX;
             x_forward_row_at<T, LX>(in, W + ((size_t)z * LY + (active ? y : y_lo)) * LX, twx, rtw, Nx, active,
-                                    xch + l * RowPad<LX>::LP, t);
+                                    xch + l * RowPad<T, LX>::LP, t);
         };
         pipelined_rounds(rounds, issue, compute);
     }
@@ -701,7 +717,7 @@ k_yx_inverse(Cx<T> *__restrict__ W, In<T> *__restrict__ phi, const Cx<T> *__rest
             const bool active = y < y_hi;
             const Cx<T> *in = reinterpret_cast<const Cx<T> *>(stage + buf * C::ROWS_I) + l * LX;
             x_inverse_row_at<T, LX>(in, phi + ((size_t)z * Ny + (active ? y : y_lo)) * Nx, twx, rtw, Nx, active,
-                                    xch + l * RowPad<LX>::LP, t);
+                                    xch + l * RowPad<T, LX>::LP, t);
         };
         pipelined_rounds(rounds, issue, compute);
     }
