@@ -469,9 +469,12 @@ def run_isofft(args, ws, rank, local):
     N = w.N
     stream = torch.cuda.current_stream()
 
+    forms = {}  # y-pass forms the plans picked
+
     def timed_solves(dtype, steps, warmup, pool=4):
         tdt = torch.float32 if dtype == "f32" else torch.float64  # df64 reads and writes FP64 arrays
         plan = Plan(N, w.h, dtype, flags=native.IPF_FLAG_PASS_EVENTS)
+        forms[dtype] = ["tiles" if v == 0 else "streamed" for v in plan.variants]
         base = torch.from_numpy(src64).to(dev, tdt)
         srcs = [base.clone() for _ in range(pool)]
         outs = [torch.empty_like(base) for _ in range(pool)]
@@ -589,6 +592,7 @@ def run_isofft(args, ws, rank, local):
         "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": list(N), "M": list(M), "h": w.h[0], "fused_xy": fused,
+                   "y_pass_forms": forms,
                    "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "4 rotating src/phi pairs (%d MB) > 129 MB L2" % (8 * 4 * n ** 3 // 2 ** 20)},
         "hbm_gbs": round(gbs32, 1),

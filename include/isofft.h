@@ -72,8 +72,13 @@ enum { IPF_CONSOLE_ERROR = 0, IPF_CONSOLE_WARNING = 1, IPF_CONSOLE_INFO_1 = 2, I
 
 /* Plan flags. */
 enum {
-    IPF_FLAG_PASS_EVENTS = 1u << 0 /* record CUDA events around each pass so
-                                      ipf_plan_pass_times can report them */
+    IPF_FLAG_PASS_EVENTS = 1u << 0, /* record CUDA events around each pass so
+                                       ipf_plan_pass_times can report them */
+    IPF_FLAG_Y_TILES = 1u << 1,     /* run the y passes in their tile form  */
+    IPF_FLAG_Y_STREAM = 1u << 2     /* run the y passes in their streamed form
+                                       (neither flag: the plan times both forms
+                                       and keeps the faster, see
+                                       ipf_plan_variants) */
 };
 
 /* Create a solver for an Nx x Ny x Nz mesh of widths h (paper Sec. 3.2,
@@ -198,6 +203,17 @@ int ipf_submit_batch(const ipf_plan_t *plans, int count, const void *const *d_sr
  * y-inverse entry covers y+x inverse, while the y-forward and x-inverse
  * entries are 0. */
 int ipf_plan_pass_times(ipf_plan_t plan, float ms[5]);
+
+/* The form each y pass of the plan runs in, v[0] for the forward and v[1]
+ * for the inverse pass: 0 tiles (one CTA per column tile, plain loads), 1
+ * streamed (persistent CTAs fed by tensor-map copies).  Both give bitwise
+ * the same potential.  Unless a flag forces one, ipf_plan_create times both
+ * forms on the plan's own workspace (a few launches of each) and keeps the
+ * faster; the choice is remembered per (dtype, mesh, shape, device) for the
+ * process, and in the file named by the environment variable
+ * ISOFFT_TUNE_FILE if set (read at the first plan, appended as choices are
+ * made).  ISOFFT_TUNE=0 skips the timing and takes the built-in rule. */
+int ipf_plan_variants(const ipf_plan_t plan, int v[2]);
 
 /* Bytes held by the library's cache of Green's spectra, and a trim of
  * unreferenced entries (least recently used first) until the cache holds

@@ -130,6 +130,7 @@ struct ipf_plan_s {
     bool have_events = false;
     // x and y passes fused per z plane (square xy mesh; opt-in with ISOFFT_FUSE_XY=1)
     bool fuse_xy = false;
+    int yvar[2] = {kYTile, kYTile};  // form of the y forward / inverse pass
     uint64_t solves = 0, folded = 0;
     double pass_sum[5] = {0, 0, 0, 0, 0};
     uint64_t pass_n = 0;
@@ -230,6 +231,136 @@ int read_status(ipf_plan_s *p, cudaStream_t st)
     return (w & 1u) ? IPF_TIMEOUT : IPF_CUDA_ERROR;
 }
 
+// ---------------------------------------------------------------------
+// y-pass form tuning: both forms run a few times on the plan's workspace and
+// the faster is kept, per (dtype, My, Kx, Ny, Nz, device capability); the
+// choices persist for the process and, with ISOFFT_TUNE_FILE, in a JSON
+// file of entries [dtype, My, Kx, Ny, Nz, sm, forward, inverse].
+// ---------------------------------------------------------------------
+struct TuneKey {
+    int v[6];
+    bool operator<(const TuneKey &o) const { return std::lexicographical_compare(v, v + 6, o.v, o.v + 6); }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune;
+bool g_tune_loaded = false;
+
+void tune_file_load()
+{
+    g_tune_loaded = true;
+    const char *path = getenv("ISOFFT_TUNE_FILE");
+    if (!path || !path[0]) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    // the integers of the file in order, eight per entry
+    std::vector<long> nums;
+    long cur = 0;
+    bool in = false, neg = false;
+    for (int ch; (ch = fgetc(f)) != EOF;) {
+        if (ch >= '0' && ch <= '9') {
+            cur = cur * 10 + (ch - '0');
+            in = true;
+        } else {
+            if (in) nums.push_back(neg ? -cur : cur);
+            neg = ch == '-';
+            cur = 0;
+            in = false;
+        }
+    }
+    if (in) nums.push_back(neg ? -cur : cur);
+    fclose(f);
+    for (size_t i = 0; i + 8 <= nums.size(); i += 8) {
+        TuneKey k;
+        for (int j = 0; j < 6; ++j) k.v[j] = (int)nums[i + j];
+        const int a = (int)nums[i + 6], b = (int)nums[i + 7];
+        if ((a == kYTile || a == kYStream) && (b == kYTile || b == kYStream)) g_tune[k] = {a, b};
+    }
+}
+
+void tune_file_save()
+{
+    const char *path = getenv("ISOFFT_TUNE_FILE");
+    if (!path || !path[0]) return;
+    FILE *f = fopen(path, "w");
+    if (!f) return;
+    fprintf(f, "{\"y_pass_forms\": [\n");
+    size_t i = 0;
+    for (const auto &kv : g_tune) {
+        const int *v = kv.first.v;
+        fprintf(f, "  [%d, %d, %d, %d, %d, %d, %d, %d]%s\n", v[0], v[1], v[2], v[3], v[4], v[5], kv.second.first,
+                kv.second.second, ++i < g_tune.size() ? "," : "");
+    }
+    fprintf(f, "]}\n");
+    fclose(f);
+}
+
+// Mean device milliseconds of three launches after one warm-up.
+template <typename Launch>
+float time_launches(Launch launch, cudaStream_t st, cudaEvent_t a, cudaEvent_t b, cudaError_t *err)
+{
+    cudaError_t e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(a, st);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(b, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    *err = e;
+    return ms;
+}
+
+template <typename T>
+int tune_y(ipf_plan_s *p, cudaStream_t st)
+{
+    const int Ny = (int)p->N[1], Nz = (int)p->N[2], My = (int)p->M[1], Lx = (int)(p->M[0] / 2);
+    if (p->flags & (IPF_FLAG_Y_TILES | IPF_FLAG_Y_STREAM)) {
+        p->yvar[0] = p->yvar[1] = (p->flags & IPF_FLAG_Y_STREAM) ? kYStream : kYTile;
+        return IPF_OK;
+    }
+    const char *env = getenv("ISOFFT_TUNE");
+    if (env && env[0] == '0') {
+        p->yvar[0] = p->yvar[1] = y_default_variant(My, sizeof(T));
+        return IPF_OK;
+    }
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, p->device);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, p->device);
+    const TuneKey key{{p->dtype, My, Lx, Ny, Nz, major * 10 + minor}};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        if (!g_tune_loaded) tune_file_load();
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            p->yvar[0] = it->second.first;
+            p->yvar[1] = it->second.second;
+            return IPF_OK;
+        }
+    }
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->W, 0, p->W_bytes, st);
+    float t[2][2] = {{0, 0}, {0, 0}};
+    for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+        t[0][v] = time_launches([&] { return launch_y_forward<T>(My, p->W, p->tw_y, Ny, Lx, Nz, p->status, v, st); },
+                                st, a, b, &e);
+        if (e == cudaSuccess)
+            t[1][v] = time_launches(
+                [&] { return launch_y_inverse<T>(My, p->W, p->tw_y, Ny, Lx, Nz, p->status, v, st); }, st, a, b, &e);
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (e != cudaSuccess) return cuda_status(e);
+    p->yvar[0] = t[0][kYStream] < t[0][kYTile] ? kYStream : kYTile;
+    p->yvar[1] = t[1][kYStream] < t[1][kYTile] ? kYStream : kYTile;
+    logf(IPF_CONSOLE_INFO_2, p->verbosity, "y forms for mesh %dx%d: forward %.4f/%.4f ms, inverse %.4f/%.4f ms",
+         My, Lx, t[0][0], t[0][1], t[1][0], t[1][1]);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = {p->yvar[0], p->yvar[1]};
+    tune_file_save();
+    return IPF_OK;
+}
+
 int acquire_spectrum(ipf_plan_s *p, cudaStream_t st)
 {
     std::lock_guard<std::mutex> lk(g_cache_mu);
@@ -325,7 +456,7 @@ cudaError_t enqueue_solve(ipf_plan_s *p, const void *src, void *phi, cudaStream_
     }
     if (ev_on) cudaEventRecord(ev[1], st);
     if (!fused) {
-        e = launch_y_forward<T>(My, p->W, p->tw_y, Ny, Lx, Nz, st);
+        e = launch_y_forward<T>(My, p->W, p->tw_y, Ny, Lx, Nz, p->status, p->yvar[0], st);
         if (e != cudaSuccess) return e;
     }
     if (ev_on) cudaEventRecord(ev[2], st);
@@ -342,7 +473,7 @@ cudaError_t enqueue_solve(ipf_plan_s *p, const void *src, void *phi, cudaStream_
         }
     }
     if (!fused) {
-        e = launch_y_inverse<T>(My, p->W, p->tw_y, Ny, Lx, Nz, st);
+        e = launch_y_inverse<T>(My, p->W, p->tw_y, Ny, Lx, Nz, p->status, p->yvar[1], st);
         if (e != cudaSuccess) return e;
     }
     if (ev_on) cudaEventRecord(ev[4], st);
@@ -394,7 +525,7 @@ cudaError_t enqueue_solve_host(ipf_plan_s *p, const void *h_src, void *h_phi, cu
         if (e == cudaSuccess)
             e = launch_x_forward<T>(Lx, stage + z0 * plane, W + z0 * wplane * cs, p->tw_x, p->rtw, Nx, Ny, My,
                                     (int64_t)nz * Ny, st);
-        if (e == cudaSuccess) e = launch_y_forward<T>(My, W + z0 * wplane * cs, p->tw_y, Ny, Lx, nz, st);
+        if (e == cudaSuccess) e = launch_y_forward<T>(My, W + z0 * wplane * cs, p->tw_y, Ny, Lx, nz, p->status, p->yvar[0], st);
     }
     if (e == cudaSuccess)
         e = launch_z_convolve<T>(Mz, p->W, p->tw_z, (const T *)p->spec->G, (const T *)p->spec->Gs, (T)p->gscale, Nz,
@@ -402,7 +533,7 @@ cudaError_t enqueue_solve_host(ipf_plan_s *p, const void *h_src, void *h_phi, cu
     for (int k = 0; k < chunks && e == cudaSuccess; ++k) {
         const int z0 = k * per, nz = z0 + per <= Nz ? per : Nz - z0;
         if (nz <= 0) break;
-        e = launch_y_inverse<T>(My, W + z0 * wplane * cs, p->tw_y, Ny, Lx, nz, st);
+        e = launch_y_inverse<T>(My, W + z0 * wplane * cs, p->tw_y, Ny, Lx, nz, p->status, p->yvar[1], st);
         if (e == cudaSuccess)
             e = launch_x_inverse<T>(Lx, W + z0 * wplane * cs, stage + z0 * plane, p->tw_x, p->rtw, Nx, Ny, My,
                                     (int64_t)nz * Ny, st);
@@ -463,7 +594,8 @@ int ipf_plan_create(ipf_plan_t *out, const int64_t n[3], const double h[3], int 
     *out = nullptr;
     int rc = validate(n, h, dtype);
     if (rc) return rc;
-    if (flags & ~(uint32_t)IPF_FLAG_PASS_EVENTS) return IPF_INVALID_ARG;
+    if (flags & ~(uint32_t)(IPF_FLAG_PASS_EVENTS | IPF_FLAG_Y_TILES | IPF_FLAG_Y_STREAM)) return IPF_INVALID_ARG;
+    if ((flags & IPF_FLAG_Y_TILES) && (flags & IPF_FLAG_Y_STREAM)) return IPF_INVALID_ARG;
     if (verbosity < IPF_CONSOLE_ERROR || verbosity > IPF_CONSOLE_INFO_2) return IPF_INVALID_ARG;
     const int ev = env_verbosity();
     if (ev >= 0) verbosity = ev;
@@ -510,6 +642,10 @@ int ipf_plan_create(ipf_plan_t *out, const int64_t n[3], const double h[3], int 
          : dtype == IPF_F64 ? upload_tables<double>(p, st)
                             : upload_tables<df64>(p, st);
     if (!rc) rc = acquire_spectrum(p, st);
+    if (!rc)
+        rc = dtype == IPF_F32   ? tune_y<float>(p, st)
+             : dtype == IPF_F64 ? tune_y<double>(p, st)
+                                : tune_y<df64>(p, st);
     if (!rc && (flags & IPF_FLAG_PASS_EVENTS)) {
         for (int s = 0; s < ipf_plan_s::kSlots && !rc; ++s)
             for (int i = 0; i < 6 && !rc; ++i) rc = cuda_status(cudaEventCreate(&p->ev[s][i]));
@@ -738,6 +874,14 @@ int ipf_launch_count(uint64_t *count)
 }
 
 int ipf_last_cuda_error(void) { return g_last_cuda; }
+
+int ipf_plan_variants(const ipf_plan_t p, int v[2])
+{
+    if (!p || !v) return IPF_INVALID_ARG;
+    v[0] = p->yvar[0];
+    v[1] = p->yvar[1];
+    return IPF_OK;
+}
 
 const char *ipf_status_string(int s)
 {

@@ -26,12 +26,26 @@ cudaError_t launch_x_forward(int L, const typename IoReal<T>::type *src, void *W
 template <typename T>
 cudaError_t launch_x_inverse(int L, const void *W, typename IoReal<T>::type *phi, const void *tw, const void *rtw,
                              int Nx, int Ny, int My, int64_t nrows, cudaStream_t st);
+// The y passes come in two forms with bitwise the same arithmetic:
+//   kYTile   one CTA per column tile (plain loads; many CTAs per SM),
+//   kYStream persistent CTAs fed by tensor-map copies (see passes.cuh).
+// Plans pick one per pass by timing both (y_default_variant without).
+enum { kYTile = 0, kYStream = 1 };
 template <typename T>
-cudaError_t launch_y_forward(int L, void *W, const void *tw, int Ny, int Kx, int Nz, cudaStream_t st);
+cudaError_t launch_y_forward(int L, void *W, const void *tw, int Ny, int Kx, int Nz, unsigned *status, int variant,
+                             cudaStream_t st);
 template <typename T>
-cudaError_t launch_y_inverse(int L, void *W, const void *tw, int Ny, int Kx, int Nz, cudaStream_t st);
+cudaError_t launch_y_inverse(int L, void *W, const void *tw, int Ny, int Kx, int Nz, unsigned *status, int variant,
+                             cudaStream_t st);
+// The form used without timing: streamed for 8-byte points on lines of 512
+// to 1024 points (where it measured faster), tiles elsewhere.
+inline int y_default_variant(int L, size_t real_bytes)
+{
+    return real_bytes == 4 && L >= 512 && L <= 1024 ? kYStream : kYTile;
+}
 // `status` (device word, may be null) gets bit 0 set when one of the pass's
-// bounded waits for its tile copies gave up (ipf_plan_check reads it).
+// bounded waits for its tile copies gave up (ipf_plan_check reads it); the
+// y passes and the z pass share it.
 template <typename T>
 cudaError_t launch_z_convolve(int L, void *W, const void *tw, const T *G, const T *Gs, T gscale, int Nz,
                               int My, int Kx, unsigned *status, cudaStream_t st);

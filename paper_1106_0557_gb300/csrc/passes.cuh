@@ -55,18 +55,30 @@ __device__ __forceinline__ void cp_async_wait()
 }
 
 // Shared-memory exchange for column passes: lines are the COLS columns of a
-// tile, stored [position][column].  A warp covers 32 / COLS' positions; when
-// a position row is only 64 bytes (SWZ), rows are swizzled by position bits
-// 3 and 4 so that the strided first-stage writes (position stride 8 or 16)
-// still alternate between the two halves of a 128-byte bank row.
-template <typename T, int L, int E, int COLS, bool SWZ = false>
+// tile, stored [position][column].  A warp's accesses cover 32 / COLS
+// positions; when a position row is narrower than a 128-byte bank row,
+// several positions share one, and the strided first-stage writes (position
+// stride 8, 12, 16 or 24) would land on the same banks.  Rows are therefore
+// swizzled by position bits:
+//   64-byte rows:        p ^ (bit 3 ^ bit 4 of p)
+//   32- and 16-byte rows: p ^ (bits 3-4 of p)
+// which makes every exchange pattern of the column shapes conflict-free or
+// nearly so (counted per pattern, per half- or quarter-warp).  The z pass
+// goes without (SWIZZLE false): it is bound by instruction issue, and the
+// per-access address arithmetic of the swizzle cost it more (measured at
+// 768 points) than the conflicts it removes.
+template <typename T, int L, int E, int COLS, bool SWIZZLE = true>
 struct ColXch {
+    static constexpr int ROW_BYTES = COLS * (int)sizeof(Cx<T>);
+    static constexpr int MODE = !SWIZZLE || ROW_BYTES >= 128 ? 0 : (ROW_BYTES == 64 ? 1 : 2);
     Cx<T> *s;
     int c;
     static __device__ __forceinline__ int row(int p)
     {
-        if constexpr (SWZ)
+        if constexpr (MODE == 1)
             return p ^ (((p >> 3) ^ (p >> 4)) & 1);
+        else if constexpr (MODE == 2)
+            return p ^ ((p >> 3) & 3);
         else
             return p;
     }
@@ -406,7 +418,7 @@ __device__ __forceinline__ void y_forward_tile(Cx<T> *__restrict__ W, const Cx<T
         else
             v[m] = ok ? ld_cx<CG>(base + (size_t)y * Kx) : Cx<T>{(T)0, (T)0};
     }
-    ColXch<T, L, E, TX, TX * sizeof(Cx<T>) == 64> xch{smem, c};
+    ColXch<T, L, E, TX> xch{smem, c};
     run_stages<T, L, E, true>(v, t, tw, xch, typename Shape<T, L>::Rad{});
     if (active) {
 #pragma unroll
@@ -433,7 +445,7 @@ __device__ __forceinline__ void y_inverse_tile(Cx<T> *__restrict__ W, const Cx<T
         else
             v[m] = active ? cswap(base[(size_t)y * Kx]) : Cx<T>{(T)0, (T)0};
     }
-    ColXch<T, L, E, TX, TX * sizeof(Cx<T>) == 64> xch{smem, c};
+    ColXch<T, L, E, TX> xch{smem, c};
     run_stages<T, L, E, false>(v, t, tw, xch, typename Shape<T, L>::Rad{});
     if (active) {
 #pragma unroll
@@ -476,7 +488,10 @@ k_x_inverse(const Cx<T> *__restrict__ W, In<T> *__restrict__ phi, const Cx<T> *_
 }
 
 // ---------------------------------------------------------------------
-// K2 / K4: y passes on column tiles; grid (ceil(Kx / TX), Nz).
+// K2 / K4, tile form: one CTA per column tile; grid (ceil(Kx / TX), Nz).
+// Each CTA loads its columns with plain coalesced loads, so many CTAs per SM
+// keep the loads in flight; best where the persistent form (below) would
+// hold fewer warps per SM (small lines, 16-byte points).
 // ---------------------------------------------------------------------
 template <typename T, int L>
 __global__ void __launch_bounds__(ColCfg<T, L>::THREADS, ColCfg<T, L>::MIN_BLOCKS_FWD)
@@ -496,6 +511,156 @@ k_y_inverse(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     y_inverse_tile<T, L, C::TX>(W, tw, Ny, Kx, blockIdx.y, blockIdx.x * C::TX, reinterpret_cast<Cx<T> *>(smem_raw),
                                 threadIdx.x % C::TX, threadIdx.x / C::TX);
+}
+
+// Twiddles of the persistent column passes: held in registers across
+// tiles, or (TWR false) read from the table by each stage.
+template <bool TWR, typename T, int L, int E, typename Rad>
+struct ZTwiddles {
+    using type = typename TwRegsOf<T, L, E, Rad>::type;
+};
+template <typename T, int L, int E, typename Rad>
+struct ZTwiddles<false, T, L, E, Rad> {
+    using type = TwRegs<T, L, E, 1>;  // holds nothing
+};
+template <bool TWR, bool HALF, typename T, int L, int E, typename TW, typename Xch, typename Rad>
+__device__ __forceinline__ void z_fft(Cx<T> (&v)[E], int t, const TW &twr, const Cx<T> *__restrict__ tw, Xch &xch,
+                                      Rad)
+{
+    if constexpr (TWR)
+        run_stages_reg<T, L, E, HALF>(v, t, twr, xch, Rad{});
+    else
+        run_stages<T, L, E, HALF>(v, t, tw, xch, Rad{});
+}
+
+// ---------------------------------------------------------------------
+// K2 / K4, streamed form: persistent over column tiles (z, kx tile).  Thread 0
+// issues the next tile's rows by tensor-map boxes (8-byte elements; K2:
+// dims {Kx EPC, Ny, Nz}, so rows y >= Ny arrive as zeros; K4: {Kx EPC, My,
+// Nz}) into the other of two staging sets while the CTA transforms the
+// current tile; completion and bounded waits as in the z pass.  Twiddles
+// stay in registers across tiles.
+// ---------------------------------------------------------------------
+template <typename T, int L>
+struct YCfg {
+    static constexpr int E = Shape<T, L>::E;
+    static constexpr int NT = L / E;
+    static constexpr int CB = (int)sizeof(Cx<T>);
+    static constexpr size_t smem_i(int tx) { return (size_t)3 * L * tx * CB + 16; }
+    static constexpr int width()
+    {
+        int tx = ColCfg<T, L>::TX;
+        while (tx > 1 && smem_i(tx) > 200 * 1024) tx /= 2;
+        return tx;
+    }
+    static constexpr int TX = width();
+    static constexpr int THREADS = TX * NT;
+    static constexpr int EPC = CB / 8;
+    static constexpr int boxes(int rows)
+    {
+        int n = 1;
+        while (rows % n != 0 || rows / n > 256) ++n;
+        return n;
+    }
+    static constexpr int NB_F = boxes(L / 2), BOX_F = L / 2 / NB_F;  // K2 reads y < L/2
+    static constexpr int NB_I = boxes(L), BOX_I = L / NB_I;          // K4 reads every row
+    static constexpr size_t XCH = (size_t)L * TX * CB;
+    static constexpr size_t IN_F = (size_t)(L / 2) * TX * CB, IN_I = (size_t)L * TX * CB;
+    static constexpr size_t SMEM_F = XCH + 2 * IN_F + 16, SMEM_I = XCH + 2 * IN_I + 16;
+    static constexpr int MIN_BLOCKS = THREADS <= 512 && SMEM_I <= 110 * 1024 ? 2 : 1;
+    // twiddles in registers across tiles, except for the long lines, whose
+    // per-thread share (29 points for 2304) would spill
+    static constexpr bool TW_REGS = L <= 1024;
+    static_assert(SMEM_I == smem_i(TX) && SMEM_I <= 227 * 1024, "y pass shared memory");
+    static_assert(TX * CB % 16 == 0, "tensor box rows must be multiples of 16 bytes");
+    static_assert(XCH % 128 == 0 && IN_F % 128 == 0 && ((size_t)BOX_F * TX * CB) % 128 == 0 &&
+                      ((size_t)BOX_I * TX * CB) % 128 == 0,
+                  "tensor copy destinations must stay 128-byte aligned");
+};
+
+template <typename T, int L, bool FWD>
+__global__ void __launch_bounds__(YCfg<T, L>::THREADS, YCfg<T, L>::MIN_BLOCKS)
+k_y_pass(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny,
+         int Kx, int ntiles, unsigned *__restrict__ status)
+{
+    using C = YCfg<T, L>;
+    constexpr int E = C::E, NT = C::NT, TX = C::TX;
+    constexpr int NB = FWD ? C::NB_F : C::NB_I, BOX = FWD ? C::BOX_F : C::BOX_I;
+    constexpr size_t IN = FWD ? C::IN_F : C::IN_I;
+    extern __shared__ __align__(128) unsigned char ysmem[];
+    Cx<T> *xs = reinterpret_cast<Cx<T> *>(ysmem);
+    unsigned char *s_in = ysmem + C::XCH;  // [set][row][TX]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(ysmem + C::XCH + 2 * IN);
+    const int tid = threadIdx.x;
+    const int c = tid % TX, t = tid / TX;
+    const int ntx = (Kx + TX - 1) / TX;
+    if (smem_addr(ysmem) & 127u) {
+        if (tid == 0 && status) atomicOr(status, 2u);
+        return;
+    }
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    auto issue = [&](int tile, int set) {  // thread 0
+        const int z = tile / ntx, xt = tile - z * ntx;
+        mbar_arrive_expect_tx(&bar[set], (uint32_t)IN);
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            tma_load_3d(s_in + set * IN + (size_t)b * BOX * TX * sizeof(Cx<T>), &tmW, xt * TX * C::EPC, b * BOX, z,
+                        &bar[set]);
+    };
+    ColXch<T, L, E, TX> xch{xs, c};
+    using Rad = typename Shape<T, L>::Rad;
+    typename ZTwiddles<C::TW_REGS, T, L, E, Rad>::type twr;
+    twr.load(tw, t);
+    int tile = blockIdx.x, it = 0;
+    bool ok = true;
+    if (tid == 0 && tile < ntiles) issue(tile, 0);
+    for (; tile < ntiles; tile += gridDim.x, ++it) {
+        const int next = tile + gridDim.x;
+        const int set = it & 1;
+        if (tid == 0 && next < ntiles) issue(next, set ^ 1);
+        const bool landed = mbar_wait_bounded(&bar[set], (uint32_t)(it >> 1) & 1u, kCopyWaitNs);
+        if (!__syncthreads_and(landed)) {
+            ok = false;
+            break;
+        }
+        const int z = tile / ntx, xt = tile - z * ntx;
+        const int kx = xt * TX + c;
+        const Cx<T> *sin = reinterpret_cast<const Cx<T> *>(s_in + set * IN) + t * TX + c;
+        Cx<T> v[E];
+        if constexpr (FWD) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = m < E / 2 ? sin[m * NT * TX] : Cx<T>{(T)0, (T)0};
+        } else {
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = cswap(sin[m * NT * TX]);
+        }
+        z_fft<C::TW_REGS, FWD, T, L, E>(v, t, twr, tw, xch, Rad{});
+        if (kx < Kx) {
+            Cx<T> *base = W + (size_t)z * L * Kx + kx;
+            if constexpr (FWD) {
+#pragma unroll
+                for (int m = 0; m < E; ++m) base[(size_t)(t + m * NT) * Kx] = v[m];
+            } else {
+#pragma unroll
+                for (int m = 0; m < E / 2; ++m) {
+                    const int y = t + m * NT;
+                    if (y < Ny) base[(size_t)y * Kx] = cswap(v[m]);
+                }
+            }
+        }
+    }
+    if (!ok && tid == 0) {
+        // a wait gave up: flag it and let the copies in flight land (bounded)
+        if (status) atomicOr(status, 1u);
+        mbar_wait_bounded(&bar[it & 1], (uint32_t)(it >> 1) & 1u, kCopyWaitNs);
+        if (tile + (int)gridDim.x < ntiles)
+            mbar_wait_bounded(&bar[(it + 1) & 1], (uint32_t)((it + 1) >> 1) & 1u, kCopyWaitNs);
+    }
 }
 
 // ---------------------------------------------------------------------
@@ -723,26 +888,6 @@ k_yx_inverse(Cx<T> *__restrict__ W, In<T> *__restrict__ phi, const Cx<T> *__rest
     }
 }
 
-// Twiddles of the z pass: held in registers across tiles, or (TWR false)
-// read from the table by each stage.
-template <bool TWR, typename T, int L, int E, typename Rad>
-struct ZTwiddles {
-    using type = typename TwRegsOf<T, L, E, Rad>::type;
-};
-template <typename T, int L, int E, typename Rad>
-struct ZTwiddles<false, T, L, E, Rad> {
-    using type = TwRegs<T, L, E, 1>;  // holds nothing
-};
-template <bool TWR, bool HALF, typename T, int L, int E, typename TW, typename Xch, typename Rad>
-__device__ __forceinline__ void z_fft(Cx<T> (&v)[E], int t, const TW &twr, const Cx<T> *__restrict__ tw, Xch &xch,
-                                      Rad)
-{
-    if constexpr (TWR)
-        run_stages_reg<T, L, E, HALF>(v, t, twr, xch, Rad{});
-    else
-        run_stages<T, L, E, HALF>(v, t, tw, xch, Rad{});
-}
-
 // ---------------------------------------------------------------------
 // K3: z forward, multiply by the Green's spectrum, z inverse.
 // Tiles: (pair p, kx tile xt), tile = p * ntx + xt; pair p holds the lines
@@ -816,7 +961,7 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
         if (pr == 0) bulk_load(gdst + C::GBLK, G + lay.block(My / 2, xt), (uint32_t)C::G_BLK, b);
     };
 
-    ColXch<T, L, E, COLS> xch{sm, col};
+    ColXch<T, L, E, COLS, false> xch{sm, col};
     using Rad = typename ZShape<T, L>::Rad;
     constexpr bool TWR = ZShape<T, L>::TW_REGS;
     typename ZTwiddles<TWR, T, L, E, Rad>::type twr;  // this thread's twiddles, for every tile (when TW_REGS)

@@ -43,6 +43,44 @@ static cudaError_t ensure_smem(F *func, size_t bytes, std::atomic<uint64_t> &don
 // up to 1536)
 #define ISOFFT_FUSED_LENGTHS(X) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768)
 
+// Resident CTAs per SM of a kernel on the current device (queried once).
+template <typename F>
+static int resident_ctas(F *func, int threads, size_t smem, std::atomic<int> &cache)
+{
+    int v = cache.load(std::memory_order_acquire);
+    if (v > 0) return v;
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, func, threads, smem) != cudaSuccess) return 0;
+    v = sms * (per > 0 ? per : 1);
+    cache.store(v, std::memory_order_release);
+    return v;
+}
+
+// cuTensorMapEncodeTiled, resolved once through the runtime (no link
+// dependency on the driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                   CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                   CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled()
+{
+    static std::atomic<EncodeTiledFn> fn{nullptr};
+    EncodeTiledFn f = fn.load(std::memory_order_acquire);
+    if (f) return f;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p)
+        return nullptr;
+    f = reinterpret_cast<EncodeTiledFn>(p);
+    fn.store(f, std::memory_order_release);
+    return f;
+}
+
+
 #if ISOFFT_GROUP == 1
 template <typename T, int L>
 static cudaError_t run_x_forward(const In<T> *src, void *W, const void *tw, const void *rtw, int Nx, int Ny,
@@ -105,7 +143,7 @@ template cudaError_t launch_x_inverse<Real>(int, const void *, In<Real> *, const
 
 #if ISOFFT_GROUP == 2
 template <typename T, int L, bool FWD>
-static cudaError_t run_y(void *W, const void *tw, int Ny, int Kx, int Nz, cudaStream_t st)
+static cudaError_t run_y_tile(void *W, const void *tw, int Ny, int Kx, int Nz, cudaStream_t st)
 {
     using C = ColCfg<T, L>;
     static std::atomic<uint64_t> done{0};
@@ -117,30 +155,71 @@ static cudaError_t run_y(void *W, const void *tw, int Ny, int Kx, int Nz, cudaSt
     count_launch();
     return cudaGetLastError();
 }
+template <typename T, int L, bool FWD>
+static cudaError_t run_y_stream(void *W, const void *tw, int Ny, int Kx, int Nz, unsigned *status, cudaStream_t st)
+{
+    using C = YCfg<T, L>;
+    constexpr size_t SMEM = FWD ? C::SMEM_F : C::SMEM_I;
+    static std::atomic<uint64_t> done{0};
+    static std::atomic<int> slots{0};
+    if ((uintptr_t)W & 15) return cudaErrorMisalignedAddress;
+    auto *k = k_y_pass<T, L, FWD>;
+    cudaError_t e = ensure_smem(k, SMEM, done);
+    if (e != cudaSuccess) return e;
+    const int ntx = (Kx + C::TX - 1) / C::TX;
+    const int ntiles = ntx * Nz;
+    int grid = resident_ctas(k, C::THREADS, SMEM, slots);
+    if (grid <= 0) return cudaErrorInvalidConfiguration;
+    if (grid > ntiles) grid = ntiles;
+    // W as 8-byte elements [Nz][My][Kx * EPC]; K2 sees only rows y < Ny
+    EncodeTiledFn encode = encode_tiled();
+    if (!encode) return cudaErrorNotSupported;
+    CUtensorMap map;
+    const cuuint64_t dims[3] = {(cuuint64_t)Kx * C::EPC, (cuuint64_t)(FWD ? Ny : L), (cuuint64_t)Nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)Kx * sizeof(Cx<T>), (cuuint64_t)L * Kx * sizeof(Cx<T>)};
+    const cuuint32_t box[3] = {(cuuint32_t)(C::TX * C::EPC), (cuuint32_t)(FWD ? C::BOX_F : C::BOX_I), 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, W, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    k<<<grid, C::THREADS, SMEM, st>>>(map, (Cx<T> *)W, (const Cx<T> *)tw, Ny, Kx, ntiles, status);
+    count_launch();
+    return cudaGetLastError();
+}
+template <typename T, int L, bool FWD>
+static cudaError_t run_y(void *W, const void *tw, int Ny, int Kx, int Nz, unsigned *status, int variant,
+                         cudaStream_t st)
+{
+    return variant == kYStream ? run_y_stream<T, L, FWD>(W, tw, Ny, Kx, Nz, status, st)
+                               : run_y_tile<T, L, FWD>(W, tw, Ny, Kx, Nz, st);
+}
 template <typename R_>
-cudaError_t launch_y_forward(int L, void *W, const void *tw, int Ny, int Kx, int Nz, cudaStream_t st)
+cudaError_t launch_y_forward(int L, void *W, const void *tw, int Ny, int Kx, int Nz, unsigned *status, int variant,
+                             cudaStream_t st)
 {
     switch (L) {
 #define X_(n) \
-    case n: return run_y<R_, n, true>(W, tw, Ny, Kx, Nz, st);
+    case n: return run_y<R_, n, true>(W, tw, Ny, Kx, Nz, status, variant, st);
         ISOFFT_COL_LENGTHS(X_)
 #undef X_
     default: return cudaErrorInvalidValue;
     }
 }
 template <typename R_>
-cudaError_t launch_y_inverse(int L, void *W, const void *tw, int Ny, int Kx, int Nz, cudaStream_t st)
+cudaError_t launch_y_inverse(int L, void *W, const void *tw, int Ny, int Kx, int Nz, unsigned *status, int variant,
+                             cudaStream_t st)
 {
     switch (L) {
 #define X_(n) \
-    case n: return run_y<R_, n, false>(W, tw, Ny, Kx, Nz, st);
+    case n: return run_y<R_, n, false>(W, tw, Ny, Kx, Nz, status, variant, st);
         ISOFFT_COL_LENGTHS(X_)
 #undef X_
     default: return cudaErrorInvalidValue;
     }
 }
-template cudaError_t launch_y_forward<Real>(int, void *, const void *, int, int, int, cudaStream_t);
-template cudaError_t launch_y_inverse<Real>(int, void *, const void *, int, int, int, cudaStream_t);
+template cudaError_t launch_y_forward<Real>(int, void *, const void *, int, int, int, unsigned *, int, cudaStream_t);
+template cudaError_t launch_y_inverse<Real>(int, void *, const void *, int, int, int, unsigned *, int, cudaStream_t);
 #endif
 
 #if ISOFFT_GROUP == 4
@@ -234,43 +313,6 @@ template cudaError_t launch_yx_inverse<Real>(int, void *, In<Real> *, const void
 #endif
 
 #if ISOFFT_GROUP == 3
-// Resident CTAs per SM of a kernel on the current device (queried once).
-template <typename F>
-static int resident_ctas(F *func, int threads, size_t smem, std::atomic<int> &cache)
-{
-    int v = cache.load(std::memory_order_acquire);
-    if (v > 0) return v;
-    int dev = 0, sms = 0, per = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, func, threads, smem) != cudaSuccess) return 0;
-    v = sms * (per > 0 ? per : 1);
-    cache.store(v, std::memory_order_release);
-    return v;
-}
-
-// cuTensorMapEncodeTiled, resolved once through the runtime (no link
-// dependency on the driver library).
-using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
-                                   CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
-                                   CUtensorMapFloatOOBfill);
-static EncodeTiledFn encode_tiled()
-{
-    static std::atomic<EncodeTiledFn> fn{nullptr};
-    EncodeTiledFn f = fn.load(std::memory_order_acquire);
-    if (f) return f;
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
-            cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !p)
-        return nullptr;
-    f = reinterpret_cast<EncodeTiledFn>(p);
-    fn.store(f, std::memory_order_release);
-    return f;
-}
-
 template <typename T, int L>
 static cudaError_t run_z(void *W, const void *tw, const T *G, const T *Gs, T gscale, int Nz, int My, int Kx,
                          unsigned *status, cudaStream_t st)

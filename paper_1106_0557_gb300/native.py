@@ -31,6 +31,8 @@ IPF_CONSOLE_WARNING = 1
 IPF_CONSOLE_INFO_1 = 2
 IPF_CONSOLE_INFO_2 = 3
 IPF_FLAG_PASS_EVENTS = 1
+IPF_FLAG_Y_TILES = 2
+IPF_FLAG_Y_STREAM = 4
 
 DTYPES = {"f32": IPF_F32, "f64": IPF_F64, "df64": IPF_DF64, IPF_F32: IPF_F32, IPF_F64: IPF_F64,
           IPF_DF64: IPF_DF64}
@@ -58,6 +60,7 @@ def _declare(L):
         "ipf_solve_host": [vp, vp, vp, vp],
         "ipf_solve_noalloc": [i64p, dp, ctypes.c_int, vp, vp, vp],
         "ipf_plan_check": [vp, vp],
+        "ipf_plan_variants": [vp, ctypes.POINTER(ctypes.c_int)],
         "ipf_noalloc_check": [vp],
         "ipf_submit_batch": [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), vp],
         "ipf_plan_pass_times": [vp, ctypes.POINTER(ctypes.c_float)],
@@ -161,6 +164,13 @@ def ipf_plan_check(plan, stream=0):
     """Synchronise `stream`; raise IsofftError if a bounded device wait of
     the plan's solves gave up since the previous check."""
     _check(lib().ipf_plan_check(ctypes.c_void_p(plan), ctypes.c_void_p(int(stream))), "ipf_plan_check")
+
+
+def ipf_plan_variants(plan):
+    """(forward, inverse) y-pass forms of a plan: 0 tiles, 1 streamed."""
+    v = (ctypes.c_int * 2)()
+    _check(lib().ipf_plan_variants(ctypes.c_void_p(plan), v), "ipf_plan_variants")
+    return int(v[0]), int(v[1])
 
 
 def ipf_noalloc_check(stream=0):

@@ -77,6 +77,11 @@ class Plan:
     def pass_times(self):
         return native.ipf_plan_pass_times(self.handle)
 
+    @property
+    def variants(self):
+        """(forward, inverse) y-pass forms: 0 tiles, 1 streamed."""
+        return native.ipf_plan_variants(self.handle)
+
     def check(self, stream=None):
         """Synchronise the stream and raise if a bounded device wait of this
         plan's solves gave up since the previous check."""

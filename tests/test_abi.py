@@ -68,6 +68,11 @@ def test_bad_dtype_and_flags():
     rc = native.lib().ipf_plan_create(ctypes.byref(ctypes.c_void_p()), (ctypes.c_int64 * 3)(4, 4, 4),
                                       (ctypes.c_double * 3)(1, 1, 1), 0, 1 << 9, 0, None)
     assert rc == native.IPF_INVALID_ARG
+    # the two y-pass forms cannot both be forced
+    rc = native.lib().ipf_plan_create(ctypes.byref(ctypes.c_void_p()), (ctypes.c_int64 * 3)(4, 4, 4),
+                                      (ctypes.c_double * 3)(1, 1, 1), 0,
+                                      native.IPF_FLAG_Y_TILES | native.IPF_FLAG_Y_STREAM, 0, None)
+    assert rc == native.IPF_INVALID_ARG
     assert native.lib().ipf_plan_create(None, None, None, 0, 0, 0, None) == native.IPF_INVALID_ARG
 
 
@@ -78,5 +83,6 @@ def test_null_handles():
     assert native.lib().ipf_submit_batch(None, 1, None, None, None) == native.IPF_INVALID_ARG
     assert native.lib().ipf_plan_pass_times(None, None) == native.IPF_INVALID_ARG
     assert native.lib().ipf_plan_check(None, None) == native.IPF_INVALID_ARG
+    assert native.lib().ipf_plan_variants(None, None) == native.IPF_INVALID_ARG
     assert native.ipf_greens_cache_bytes() >= 0
     assert native.ipf_launch_count() >= 0

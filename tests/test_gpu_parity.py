@@ -342,3 +342,40 @@ def test_host_buffer_solve_equals_device_solve(N, dtype):
         again = p.solve_host(src)
     assert np.array_equal(host, dev)
     assert np.array_equal(again, dev)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64", "df64"])
+@pytest.mark.parametrize("N", [(64, 64, 64), (37, 200, 13), (256, 256, 40), (20, 300, 17), (9, 700, 8)])
+def test_y_pass_forms_are_bitwise_equal(N, dtype):
+    """The tile and streamed forms of the y passes run the same arithmetic in
+    the same order: forcing either gives bitwise the same potential, and a
+    tuned plan picks one of the two for each pass."""
+    from paper_1106_0557_gb300 import Plan
+    src = torch.from_numpy(rand_src(N, 4).astype(NP[dtype])).cuda()
+    outs = []
+    for flag in (native.IPF_FLAG_Y_TILES, native.IPF_FLAG_Y_STREAM):
+        with Plan(N, (1.0, 0.5, 1.0), dtype, flags=flag) as p:
+            want = (1, 1) if flag == native.IPF_FLAG_Y_STREAM else (0, 0)
+            assert p.variants == want
+            outs.append(p.solve(src))
+            p.check()
+    assert torch.equal(outs[0], outs[1])
+    with Plan(N, (1.0, 0.5, 1.0), dtype) as p:
+        assert set(p.variants) <= {0, 1}
+        assert torch.equal(p.solve(src), outs[0])
+
+
+def test_tuned_forms_are_written_to_the_tune_file(tmp_path, monkeypatch):
+    """With ISOFFT_TUNE_FILE set, a plan of a shape not seen before records
+    its timed choice as an entry [dtype, My, Kx, Ny, Nz, sm, fwd, inv]."""
+    import json
+    from paper_1106_0557_gb300 import Plan
+    path = tmp_path / "tune.json"
+    monkeypatch.setenv("ISOFFT_TUNE_FILE", str(path))
+    N = (41, 83, 29)  # a shape no other test uses
+    with Plan(N, (1.0, 1.0, 1.0), "f32") as p:
+        fwd, inv = p.variants
+        M = p.padded_shape
+    entries = json.loads(path.read_text())["y_pass_forms"]
+    rows = [e for e in entries if e[:5] == [0, M[1], M[0] // 2, N[1], N[2]]]
+    assert len(rows) == 1 and rows[0][6:] == [fwd, inv]
