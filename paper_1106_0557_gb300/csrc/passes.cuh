@@ -272,6 +272,32 @@ __device__ __forceinline__ Cx<T> ld_cx(const Cx<T> *p)
     }
 }
 
+// Lane shuffle of one complex point within segments of `width` lanes.
+__device__ __forceinline__ float shfl_real(float v, int src, int width) { return __shfl_sync(0xffffffffu, v, src, width); }
+__device__ __forceinline__ double shfl_real(double v, int src, int width)
+{
+    return __shfl_sync(0xffffffffu, v, src, width);
+}
+__device__ __forceinline__ df64 shfl_real(df64 v, int src, int width)
+{
+    return {__shfl_sync(0xffffffffu, v.hi, src, width), __shfl_sync(0xffffffffu, v.lo, src, width)};
+}
+template <typename T>
+__device__ __forceinline__ Cx<T> shfl_cx(Cx<T> v, int src, int width)
+{
+    return {shfl_real(v.x, src, width), shfl_real(v.y, src, width)};
+}
+
+// For a row held by NT <= 32 lanes at positions k = t + m NT: the point at
+// L - k (L = E NT), which lane NT - t holds as its point E - 1 - m (lane 0
+// holds its own at (E - m) mod E).  Every lane of the warp must call it.
+template <typename T, int E, int NT>
+__device__ __forceinline__ Cx<T> mirror_partner(const Cx<T> (&v)[E], int m, int t)
+{
+    const Cx<T> other = shfl_cx(v[E - 1 - m], (NT - t) & (NT - 1), NT);
+    return t == 0 ? v[(E - m) % E] : other;
+}
+
 // K1 body: row rr = z * Ny + y of the source, real -> packed half spectrum.
 // tw: W_L^k (k < L), rtw: W_{2L}^k (k < L), L = Mx / 2.
 template <typename T>
@@ -308,14 +334,24 @@ __device__ __forceinline__ void x_forward_row_at(const In<T> *in, Cx<T> *__restr
     // split the half-length transform Z into the real row's spectrum:
     //   2X[k] = (Z[k] + conj Z[L-k]) + W_2L^k (-i)(Z[k] - conj Z[L-k]),
     //   2X[0] = 2(Re Z0 + Im Z0), 2X[L] = 2(Re Z0 - Im Z0).
+    // Z[L-k] comes from the mirror lane by a shuffle when the row lies within
+    // a warp, else through shared memory.
+    constexpr bool SHFL = NT <= 32 && 32 % NT == 0;
+    if constexpr (!SHFL) {
 #pragma unroll
-    for (int m = 0; m < E; ++m) line[RowPad<T, L>::at(t + m * NT)] = v[m];
-    row_sync<NT>();
+        for (int m = 0; m < E; ++m) line[RowPad<T, L>::at(t + m * NT)] = v[m];
+        row_sync<NT>();
+    }
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         const int k = t + m * NT;
         const Cx<T> zk = v[m];
-        const Cx<T> zr = cconj(line[RowPad<T, L>::at(k == 0 ? 0 : L - k)]);
+        Cx<T> zm;
+        if constexpr (SHFL)
+            zm = mirror_partner<T, E, NT>(v, m, t);
+        else
+            zm = line[RowPad<T, L>::at(k == 0 ? 0 : L - k)];
+        const Cx<T> zr = cconj(zm);
         const Cx<T> a = cadd(zk, zr);
         const Cx<T> b = cmul_mi(csub(zk, zr));
         Cx<T> p = cadd(a, cmul(b, rtw[k]));
@@ -341,6 +377,9 @@ __device__ __forceinline__ void x_inverse_row_at(const Cx<T> *in, In<T> *__restr
                                                  int t)
 {
     constexpr int E = XShape<T, L>::E, NT = L / E;
+    // (The mirror point X[L-k] goes through shared memory here: a shuffle
+    // from the loaded registers, as in K1, measured slower, since every
+    // shuffle then waits on the row's global loads.)
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         const int k = t + m * NT;
