@@ -64,9 +64,10 @@ __device__ __forceinline__ void cp_async_wait()
 //   32- and 16-byte rows: p ^ (bits 3-4 of p)
 // which makes every exchange pattern of the column shapes conflict-free or
 // nearly so (counted per pattern, per half- or quarter-warp).  The z pass
-// goes without (SWIZZLE false): it is bound by instruction issue, and the
-// per-access address arithmetic of the swizzle cost it more (measured at
-// 768 points) than the conflicts it removes.
+// swizzles only the 32-byte rows of its 2304-point lines, where 42 % of its
+// shared wavefronts were conflict replays: on 64-byte rows the per-access
+// address arithmetic cost it more (measured at 768 points) than the
+// conflicts it removes, and the register-twiddle shapes would spill.
 template <typename T, int L, int E, int COLS, bool SWIZZLE = true>
 struct ColXch {
     static constexpr int ROW_BYTES = COLS * (int)sizeof(Cx<T>);
@@ -229,9 +230,18 @@ struct ZCfg {
     static constexpr size_t IN_SET = 2 * IN_GROUP;
     static constexpr size_t G_BLK = (size_t)GBLK * sizeof(T);
     static constexpr size_t G_SET = 2 * G_BLK;  // the blocks of k_y' = pr and of My/2 (pr = 0 only)
-    static constexpr size_t SMEM = z_smem(TX, L, (int)sizeof(T));
+    // without register twiddles the CTA keeps the line's twiddle table in
+    // shared memory (read by every stage, loaded once per CTA)
+    static constexpr bool TWR = ZShape<T, L>::TW_REGS;
+    static constexpr size_t TWS = TWR ? 0 : (size_t)L * sizeof(Cx<T>);
+    static constexpr size_t SMEM = z_smem(TX, L, (int)sizeof(T)) + TWS;
     static constexpr int MIN_BLOCKS = sizeof(T) == 8 && E == 12 && NT >= 32 && NT <= 64 ? 3 : 1;
-    static_assert(SMEM == XCH + 2 * IN_SET + 2 * G_SET + 16, "z pass shared-memory layout");
+    // rows of 32 bytes or less put several positions on one bank row: the
+    // lines that keep their twiddles in shared memory swizzle them (the
+    // register-twiddle shapes would spill under the extra address registers;
+    // wider rows go without, see ColXch)
+    static constexpr bool SWZ = !TWR && COLS * sizeof(Cx<T>) <= 32;
+    static_assert(SMEM == XCH + 2 * IN_SET + 2 * G_SET + 16 + TWS, "z pass shared-memory layout");
     static_assert(MIN_BLOCKS * SMEM <= 227 * 1024, "z pass CTAs per SM exceed shared memory");
     static_assert(THREADS <= 1024, "z tile too large");
     static_assert(SMEM <= 227 * 1024, "z tile exceeds shared memory");
@@ -987,6 +997,12 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
         mbar_init(&bar[1], 1);
         mbar_init_fence();
     }
+    const Cx<T> *twz = tw;  // the twiddle table the stages read
+    if constexpr (!C::TWR) {
+        Cx<T> *s_tw = reinterpret_cast<Cx<T> *>(zsmem + C::XCH + 2 * C::IN_SET + 2 * C::G_SET + 16);
+        for (int i = tid; i < L; i += C::THREADS) s_tw[i] = tw[i];
+        twz = s_tw;
+    }
     __syncthreads();
 
     auto issue = [&](int tile, int set) {  // thread 0
@@ -1006,9 +1022,9 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
         if (pr == 0) bulk_load(gdst + C::GBLK, G + lay.block(My / 2, xt), (uint32_t)C::G_BLK, b);
     };
 
-    ColXch<T, L, E, COLS, false> xch{sm, col};
+    ColXch<T, L, E, COLS, C::SWZ> xch{sm, col};
     using Rad = typename ZShape<T, L>::Rad;
-    constexpr bool TWR = ZShape<T, L>::TW_REGS;
+    constexpr bool TWR = C::TWR;
     typename ZTwiddles<TWR, T, L, E, Rad>::type twr;  // this thread's twiddles, for every tile (when TW_REGS)
     twr.load(tw, t);
     int tile = blockIdx.x, it = 0;
@@ -1035,7 +1051,7 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = m < E / 2 ? sin[m * NT * TX] : Cx<T>{(T)0, (T)0};
 
-        z_fft<TWR, true, T, L, E>(v, t, twr, tw, xch, Rad{});
+        z_fft<TWR, true, T, L, E>(v, t, twr, twz, xch, Rad{});
 
         // spectrum at kz = t + m NT: kz' = kz below Lh, L - kz from Lh on
         const T *sg = s_g + ((size_t)set * 2 + (pr == 0 ? g : 0)) * C::GBLK;
@@ -1072,7 +1088,7 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
 
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = cswap(v[m]);
-        z_fft<TWR, false, T, L, E>(v, t, twr, tw, xch, Rad{});
+        z_fft<TWR, false, T, L, E>(v, t, twr, twz, xch, Rad{});
         if (active) {
             Cx<T> *base = W + (size_t)ky * Kx + kx;
 #pragma unroll
