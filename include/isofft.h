@@ -75,10 +75,17 @@ enum {
     IPF_FLAG_PASS_EVENTS = 1u << 0, /* record CUDA events around each pass so
                                        ipf_plan_pass_times can report them */
     IPF_FLAG_Y_TILES = 1u << 1,     /* run the y passes in their tile form  */
-    IPF_FLAG_Y_STREAM = 1u << 2     /* run the y passes in their streamed form
+    IPF_FLAG_Y_STREAM = 1u << 2,    /* run the y passes in their streamed form
                                        (neither flag: the plan times both forms
                                        and keeps the faster, see
                                        ipf_plan_variants) */
+    IPF_FLAG_TEST_WAIT_RUNOUT = 1u << 3 /* test hook: the z pass's first tile
+                                       on each CTA expects 16 bytes more than
+                                       its copies deliver, so its bounded wait
+                                       runs out (about 4 s) and the solve
+                                       reports IPF_TIMEOUT through
+                                       ipf_plan_check; its potential is then
+                                       unspecified */
 };
 
 /* Create a solver for an Nx x Ny x Nz mesh of widths h (paper Sec. 3.2,

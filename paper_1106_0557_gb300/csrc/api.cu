@@ -215,6 +215,10 @@ int upload_tables(ipf_plan_s *p, cudaStream_t st)
     return IPF_OK;
 }
 
+// IPF_FLAG_TEST_WAIT_RUNOUT: bytes the z pass's first tile on each CTA
+// expects beyond its copies, so that its bounded wait runs out.
+unsigned runout_bytes(const ipf_plan_s *p) { return (p->flags & IPF_FLAG_TEST_WAIT_RUNOUT) ? 16u : 0u; }
+
 // Reads and clears the plan's device status word after the work queued on
 // `st` so far: IPF_TIMEOUT when a pass's bounded wait for its copies gave up,
 // IPF_CUDA_ERROR when a pass refused its shared-memory layout.
@@ -461,7 +465,7 @@ cudaError_t enqueue_solve(ipf_plan_s *p, const void *src, void *phi, cudaStream_
     }
     if (ev_on) cudaEventRecord(ev[2], st);
     e = launch_z_convolve<T>(Mz, p->W, p->tw_z, (const T *)p->spec->G, (const T *)p->spec->Gs,
-                             (T)p->gscale, Nz, My, Lx, p->status, st);
+                             (T)p->gscale, Nz, My, Lx, p->status, runout_bytes(p), st);
     if (e != cudaSuccess) return e;
     if (ev_on) cudaEventRecord(ev[3], st);
     if (fused) {
@@ -529,7 +533,7 @@ cudaError_t enqueue_solve_host(ipf_plan_s *p, const void *h_src, void *h_phi, cu
     }
     if (e == cudaSuccess)
         e = launch_z_convolve<T>(Mz, p->W, p->tw_z, (const T *)p->spec->G, (const T *)p->spec->Gs, (T)p->gscale, Nz,
-                                 My, Lx, p->status, st);
+                                 My, Lx, p->status, runout_bytes(p), st);
     for (int k = 0; k < chunks && e == cudaSuccess; ++k) {
         const int z0 = k * per, nz = z0 + per <= Nz ? per : Nz - z0;
         if (nz <= 0) break;
@@ -594,7 +598,8 @@ int ipf_plan_create(ipf_plan_t *out, const int64_t n[3], const double h[3], int 
     *out = nullptr;
     int rc = validate(n, h, dtype);
     if (rc) return rc;
-    if (flags & ~(uint32_t)(IPF_FLAG_PASS_EVENTS | IPF_FLAG_Y_TILES | IPF_FLAG_Y_STREAM)) return IPF_INVALID_ARG;
+    if (flags & ~(uint32_t)(IPF_FLAG_PASS_EVENTS | IPF_FLAG_Y_TILES | IPF_FLAG_Y_STREAM | IPF_FLAG_TEST_WAIT_RUNOUT))
+        return IPF_INVALID_ARG;
     if ((flags & IPF_FLAG_Y_TILES) && (flags & IPF_FLAG_Y_STREAM)) return IPF_INVALID_ARG;
     if (verbosity < IPF_CONSOLE_ERROR || verbosity > IPF_CONSOLE_INFO_2) return IPF_INVALID_ARG;
     const int ev = env_verbosity();

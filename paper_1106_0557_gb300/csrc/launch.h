@@ -45,10 +45,11 @@ inline int y_default_variant(int L, size_t real_bytes)
 }
 // `status` (device word, may be null) gets bit 0 set when one of the pass's
 // bounded waits for its tile copies gave up (ipf_plan_check reads it); the
-// y passes and the z pass share it.
+// y passes and the z pass share it.  `test_extra_tx` (normally 0) is the
+// run-out test hook: bytes each CTA's first tile expects beyond its copies.
 template <typename T>
 cudaError_t launch_z_convolve(int L, void *W, const void *tw, const T *G, const T *Gs, T gscale, int Nz,
-                              int My, int Kx, unsigned *status, cudaStream_t st);
+                              int My, int Kx, unsigned *status, unsigned test_extra_tx, cudaStream_t st);
 
 // Fused x+y forward / y+x inverse for planes with My = Mx = 2 LX: one
 // cluster of 4 CTAs per z plane (see passes.cuh).

@@ -965,7 +965,7 @@ template <typename T, int L>
 __global__ void __launch_bounds__(ZCfg<T, L>::THREADS, ZCfg<T, L>::MIN_BLOCKS)
 k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw,
              const T *__restrict__ G, const T *__restrict__ Gs, T gscale, int Nz, int My, int Kx, int ntiles,
-             unsigned *__restrict__ status)
+             unsigned *__restrict__ status, unsigned test_extra_tx)
 {
     using C = ZCfg<T, L>;
     constexpr int E = C::E, NT = C::NT, TX = C::TX, COLS = C::COLS;
@@ -1005,11 +1005,11 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
     }
     __syncthreads();
 
-    auto issue = [&](int tile, int set) {  // thread 0
+    auto issue = [&](int tile, int set, uint32_t extra) {  // thread 0
         const int pr = tile / ntx, xt = tile - pr * ntx;
         const int ky1 = pr == 0 ? My / 2 : My - pr;
         uint64_t *b = &bar[set];
-        mbar_arrive_expect_tx(b, (uint32_t)(C::IN_SET + (pr == 0 ? 2 : 1) * C::G_BLK));
+        mbar_arrive_expect_tx(b, (uint32_t)(C::IN_SET + (pr == 0 ? 2 : 1) * C::G_BLK) + extra);
         unsigned char *dst = s_in + set * C::IN_SET;
 #pragma unroll
         for (int zb = 0; zb < C::NZB; ++zb) {
@@ -1029,11 +1029,13 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
     twr.load(tw, t);
     int tile = blockIdx.x, it = 0;
     bool ok = true;
-    if (tid == 0 && tile < ntiles) issue(tile, 0);
+    // test_extra_tx is a test hook: bytes the first tile's barrier expects
+    // beyond what its copies deliver, so that its wait runs out (normally 0)
+    if (tid == 0 && tile < ntiles) issue(tile, 0, test_extra_tx);
     for (; tile < ntiles; tile += gridDim.x, ++it) {
         const int next = tile + gridDim.x;
         const int set = it & 1;
-        if (tid == 0 && next < ntiles) issue(next, set ^ 1);
+        if (tid == 0 && next < ntiles) issue(next, set ^ 1, 0u);
         const bool landed = mbar_wait_bounded(&bar[set], (uint32_t)(it >> 1) & 1u, kCopyWaitNs);
         if (!__syncthreads_and(landed)) {
             ok = false;

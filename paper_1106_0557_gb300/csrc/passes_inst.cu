@@ -315,7 +315,7 @@ template cudaError_t launch_yx_inverse<Real>(int, void *, In<Real> *, const void
 #if ISOFFT_GROUP == 3
 template <typename T, int L>
 static cudaError_t run_z(void *W, const void *tw, const T *G, const T *Gs, T gscale, int Nz, int My, int Kx,
-                         unsigned *status, cudaStream_t st)
+                         unsigned *status, unsigned test_extra_tx, cudaStream_t st)
 {
     using C = ZCfg<T, L>;
     static std::atomic<uint64_t> done{0};
@@ -342,17 +342,17 @@ static cudaError_t run_z(void *W, const void *tw, const T *G, const T *Gs, T gsc
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
     k_z_convolve<T, L><<<grid, C::THREADS, C::SMEM, st>>>(map, (Cx<T> *)W, (const Cx<T> *)tw, G, Gs, gscale, Nz,
-                                                         My, Kx, ntiles, status);
+                                                         My, Kx, ntiles, status, test_extra_tx);
     count_launch();
     return cudaGetLastError();
 }
 template <typename R_>
 cudaError_t launch_z_convolve(int L, void *W, const void *tw, const R_ *G, const R_ *Gs, R_ gscale,
-                                  int Nz, int My, int Kx, unsigned *status, cudaStream_t st)
+                                  int Nz, int My, int Kx, unsigned *status, unsigned test_extra_tx, cudaStream_t st)
 {
     switch (L) {
 #define X_(n) \
-    case n: return run_z<R_, n>(W, tw, G, Gs, gscale, Nz, My, Kx, status, st);
+    case n: return run_z<R_, n>(W, tw, G, Gs, gscale, Nz, My, Kx, status, test_extra_tx, st);
         ISOFFT_COL_LENGTHS(X_)
 #undef X_
     default: return cudaErrorInvalidValue;
@@ -370,7 +370,7 @@ int z_tile_for(int L)
     }
 }
 template cudaError_t launch_z_convolve<Real>(int, void *, const void *, const Real *, const Real *, Real, int,
-                                             int, int, unsigned *, cudaStream_t);
+                                             int, int, unsigned *, unsigned, cudaStream_t);
 template int z_tile_for<Real>(int);
 #endif
 

@@ -379,3 +379,23 @@ def test_tuned_forms_are_written_to_the_tune_file(tmp_path, monkeypatch):
     entries = json.loads(path.read_text())["y_pass_forms"]
     rows = [e for e in entries if e[:5] == [0, M[1], M[0] // 2, N[1], N[2]]]
     assert len(rows) == 1 and rows[0][6:] == [fwd, inv]
+
+
+def test_bounded_wait_runout_reports_timeout_and_the_gpu_stays_usable():
+    """The z pass's copy waits are bounded: with the run-out test hook the
+    first tile of every CTA expects more bytes than its copies deliver, the
+    wait gives up after its time limit, the pass lets its copies land and
+    returns, and ipf_plan_check reports IPF_TIMEOUT once.  Solves afterwards,
+    on another plan, match the oracle."""
+    from paper_1106_0557_gb300 import Plan
+    N, h = (64, 64, 64), (1.0, 1.0, 1.0)
+    src = rand_src(N, 9)
+    d = torch.from_numpy(src.astype(np.float32)).cuda()
+    with Plan(N, h, "f32", flags=native.IPF_FLAG_TEST_WAIT_RUNOUT) as p:
+        p.solve(d)
+        with pytest.raises(native.IsofftError) as ei:
+            p.check()
+        assert ei.value.status == native.IPF_TIMEOUT
+        p.check()  # the status word was cleared
+    phi, s64 = gpu_solve(src, h, "f32")
+    assert oracle.max_rel_error(phi, oracle.solve(s64, h)) <= TOL["f32"]
