@@ -136,16 +136,31 @@ int ipf_estimate_bytes(const int64_t n[3], const double h[3], int dtype, size_t 
  * waiting. */
 int ipf_solve(ipf_plan_t plan, const void *d_src, void *d_phi, void *stream);
 
-/* One solve from and to HOST memory: copies h_src to a device staging
- * buffer owned by the plan, solves, copies the potential back to h_phi and
- * synchronises `stream` before returning.  The copies run on a stream of the
- * plan, in chunks of z planes, overlapped with the x and y passes of the
- * chunks already on the device (and, on the way back, with the inverse
- * passes of later chunks); with pinned host buffers most of the copy time
- * hides behind those passes.  Pass events (IPF_FLAG_PASS_EVENTS) are not
- * recorded by this call.  Returns what ipf_plan_check would return for the
- * solve (IPF_TIMEOUT if a device wait of the z pass gave up). */
+/* One solve from and to HOST memory: ipf_solve_host_async followed by
+ * ipf_plan_host_wait.  Returns what ipf_plan_check would return for the
+ * solve (IPF_TIMEOUT if a device wait of a pass gave up). */
 int ipf_solve_host(ipf_plan_t plan, const void *h_src, void *h_phi, void *stream);
+
+/* Enqueue one solve from and to host memory and return without waiting.
+ *   h_src, h_phi  host arrays of Nz*Ny*Nx elements of the plan's dtype (FP64
+ *                 for IPF_DF64); pinned memory lets the copies run
+ *                 asynchronously.  h_src is read, and h_phi written, after the
+ *                 call returns: keep both valid, h_src unchanged and h_phi
+ *                 unread until ipf_plan_host_wait.
+ *   stream        the passes run on it, after the work already enqueued there;
+ *                 the copies run on two streams of the plan.
+ * The source is copied in z-plane chunks into one of three device staging
+ * buffers of the plan (allocated on the first host solve), the x and y passes
+ * of each chunk start as it lands, and each chunk's potential is copied back
+ * as soon as its inverse passes finish.  Consecutive host solves on a plan
+ * take the buffers in turn, so one solve's copies overlap the passes of the
+ * solves before and after it.  The copy of h_src does not wait for earlier
+ * work on `stream`. */
+int ipf_solve_host_async(ipf_plan_t plan, const void *h_src, void *h_phi, void *stream);
+
+/* Wait until every host solve enqueued on the plan has written its potential
+ * back; returns what ipf_plan_check returns for them. */
+int ipf_plan_host_wait(ipf_plan_t plan);
 
 /* Device-side status of the solves made on this plan since the previous
  * check.  The z pass (forward z transform x spectrum x inverse) receives its

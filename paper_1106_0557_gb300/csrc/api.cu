@@ -117,11 +117,16 @@ struct ipf_plan_s {
     void *tables = nullptr;  // tw_x | rtw | tw_y | tw_z
     const void *tw_x = nullptr, *rtw = nullptr, *tw_y = nullptr, *tw_z = nullptr;
     unsigned *status = nullptr;  // device word after the tables: bit 0 = a bounded wait gave up
-    void *stage = nullptr;  // device staging for ipf_solve_host
-    // ipf_solve_host pipeline: a copy stream and per-chunk events
-    static constexpr int kChunks = 8;
-    cudaStream_t copy_st = nullptr;
-    cudaEvent_t ev_start = nullptr, ev_done = nullptr, ev_in[kChunks] = {}, ev_out[kChunks] = {};
+    // host-buffer solves: three device staging sets used in turn, copies on
+    // two streams of the plan (host to device, device to host) so that one
+    // solve's copies overlap its neighbours' passes (with three sets a
+    // solve's upload waits only on the download of the solve two before it);
+    // per-chunk events
+    static constexpr int kChunks = 8, kAsyncChunks = 2, kSets = 3;
+    void *stage[kSets] = {};
+    int stage_set = 0;
+    cudaStream_t h2d_st = nullptr, d2h_st = nullptr;
+    cudaEvent_t ev_free[kSets] = {}, ev_in[kSets][kChunks] = {}, ev_out[kSets][kChunks] = {};
     // IPF_FLAG_PASS_EVENTS: a ring of event sets, one per recent solve; a
     // slot is folded into the running sums before it is reused, so timing
     // many back-to-back solves never waits on the device.
@@ -504,32 +509,35 @@ int solve_impl(ipf_plan_s *p, const void *src, void *phi, cudaStream_t st)
 // On the way back, chunk k's potential is copied out while later chunks'
 // inverse passes run.
 template <typename T>
-cudaError_t enqueue_solve_host(ipf_plan_s *p, const void *h_src, void *h_phi, cudaStream_t st)
+cudaError_t enqueue_solve_host(ipf_plan_s *p, const void *h_src, void *h_phi, int max_chunks, cudaStream_t st)
 {
     using IoT = typename IoReal<T>::type;
     const int Nx = (int)p->N[0], Ny = (int)p->N[1], Nz = (int)p->N[2];
     const int Lx = (int)(p->M[0] / 2), My = (int)p->M[1], Mz = (int)p->M[2];
     const size_t plane = (size_t)Nx * Ny, wplane = (size_t)My * Lx;
-    const int chunks = Nz < ipf_plan_s::kChunks ? Nz : ipf_plan_s::kChunks;
+    const int chunks = Nz < max_chunks ? Nz : max_chunks;
     const int per = (Nz + chunks - 1) / chunks;
-    IoT *stage = (IoT *)p->stage;
+    const int s = p->stage_set;
+    p->stage_set = (s + 1) % ipf_plan_s::kSets;
+    IoT *stage = (IoT *)p->stage[s];
     const char *hs = (const char *)h_src;
     char *hp = (char *)h_phi;
     char *W = (char *)p->W;
     const size_t cs = 2 * sizeof(T);  // bytes of one workspace complex
-    cudaError_t e = cudaEventRecord(p->ev_start, st);  // the copies start after prior work on `st`
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->copy_st, p->ev_start, 0);
+    // the set's previous potential has left before its staging is refilled
+    cudaError_t e = cudaStreamWaitEvent(p->h2d_st, p->ev_free[s], 0);
     for (int k = 0; k < chunks && e == cudaSuccess; ++k) {
         const int z0 = k * per, nz = z0 + per <= Nz ? per : Nz - z0;
         if (nz <= 0) break;
         e = cudaMemcpyAsync(stage + z0 * plane, hs + z0 * plane * sizeof(IoT), nz * plane * sizeof(IoT),
-                            cudaMemcpyHostToDevice, p->copy_st);
-        if (e == cudaSuccess) e = cudaEventRecord(p->ev_in[k], p->copy_st);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, p->ev_in[k], 0);
+                            cudaMemcpyHostToDevice, p->h2d_st);
+        if (e == cudaSuccess) e = cudaEventRecord(p->ev_in[s][k], p->h2d_st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, p->ev_in[s][k], 0);
         if (e == cudaSuccess)
             e = launch_x_forward<T>(Lx, stage + z0 * plane, W + z0 * wplane * cs, p->tw_x, p->rtw, Nx, Ny, My,
                                     (int64_t)nz * Ny, st);
-        if (e == cudaSuccess) e = launch_y_forward<T>(My, W + z0 * wplane * cs, p->tw_y, Ny, Lx, nz, p->status, p->yvar[0], st);
+        if (e == cudaSuccess)
+            e = launch_y_forward<T>(My, W + z0 * wplane * cs, p->tw_y, Ny, Lx, nz, p->status, p->yvar[0], st);
     }
     if (e == cudaSuccess)
         e = launch_z_convolve<T>(Mz, p->W, p->tw_z, (const T *)p->spec->G, (const T *)p->spec->Gs, (T)p->gscale, Nz,
@@ -541,15 +549,52 @@ cudaError_t enqueue_solve_host(ipf_plan_s *p, const void *h_src, void *h_phi, cu
         if (e == cudaSuccess)
             e = launch_x_inverse<T>(Lx, W + z0 * wplane * cs, stage + z0 * plane, p->tw_x, p->rtw, Nx, Ny, My,
                                     (int64_t)nz * Ny, st);
-        if (e == cudaSuccess) e = cudaEventRecord(p->ev_out[k], st);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(p->copy_st, p->ev_out[k], 0);
+        if (e == cudaSuccess) e = cudaEventRecord(p->ev_out[s][k], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(p->d2h_st, p->ev_out[s][k], 0);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(hp + z0 * plane * sizeof(IoT), stage + z0 * plane, nz * plane * sizeof(IoT),
-                                cudaMemcpyDeviceToHost, p->copy_st);
+                                cudaMemcpyDeviceToHost, p->d2h_st);
     }
-    if (e == cudaSuccess) e = cudaEventRecord(p->ev_done, p->copy_st);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, p->ev_done, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev_free[s], p->d2h_st);
     return e;
+}
+
+// Staging buffers, copy streams and events of the host-buffer solves,
+// created on the plan's first such solve.
+int host_solve_setup(ipf_plan_s *p)
+{
+    const size_t bytes = elem_size(p->dtype) * (size_t)p->N[0] * (size_t)p->N[1] * (size_t)p->N[2];
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < ipf_plan_s::kSets && e == cudaSuccess; ++s)
+        if (!p->stage[s]) {
+            e = cudaMalloc(&p->stage[s], bytes);
+            if (e != cudaSuccess) p->stage[s] = nullptr;
+        }
+    if (e == cudaSuccess && !p->h2d_st) {
+        e = cudaStreamCreateWithFlags(&p->h2d_st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->d2h_st, cudaStreamNonBlocking);
+        for (int s = 0; s < ipf_plan_s::kSets && e == cudaSuccess; ++s) {
+            e = cudaEventCreateWithFlags(&p->ev_free[s], cudaEventDisableTiming);
+            for (int k = 0; k < ipf_plan_s::kChunks && e == cudaSuccess; ++k) {
+                e = cudaEventCreateWithFlags(&p->ev_in[s][k], cudaEventDisableTiming);
+                if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_out[s][k], cudaEventDisableTiming);
+            }
+        }
+    }
+    return cuda_status(e);
+}
+
+// chunks: z-plane chunks of the copies (more chunks overlap a lone solve's
+// copies with its own passes better; fewer keep the host's enqueue work per
+// solve small when solves overlap one another)
+int enqueue_host(ipf_plan_s *p, const void *h_src, void *h_phi, int chunks, cudaStream_t st)
+{
+    int rc = host_solve_setup(p);
+    if (rc) return rc;
+    const cudaError_t e = p->dtype == IPF_F32   ? enqueue_solve_host<float>(p, h_src, h_phi, chunks, st)
+                          : p->dtype == IPF_F64 ? enqueue_solve_host<double>(p, h_src, h_phi, chunks, st)
+                                                : enqueue_solve_host<df64>(p, h_src, h_phi, chunks, st);
+    return cuda_status(e);
 }
 
 bool aligned16(const void *ptr) { return ((uintptr_t)ptr & 15u) == 0; }
@@ -673,14 +718,16 @@ int ipf_plan_destroy(ipf_plan_t p)
     release_spectrum(p);
     if (p->W) cudaFree(p->W);
     if (p->tables) cudaFree(p->tables);
-    if (p->stage) cudaFree(p->stage);
-    if (p->copy_st) cudaStreamDestroy(p->copy_st);
-    if (p->ev_start) cudaEventDestroy(p->ev_start);
-    if (p->ev_done) cudaEventDestroy(p->ev_done);
-    for (int k = 0; k < ipf_plan_s::kChunks; ++k) {
-        if (p->ev_in[k]) cudaEventDestroy(p->ev_in[k]);
-        if (p->ev_out[k]) cudaEventDestroy(p->ev_out[k]);
+    for (int s = 0; s < ipf_plan_s::kSets; ++s) {
+        if (p->stage[s]) cudaFree(p->stage[s]);
+        if (p->ev_free[s]) cudaEventDestroy(p->ev_free[s]);
+        for (int k = 0; k < ipf_plan_s::kChunks; ++k) {
+            if (p->ev_in[s][k]) cudaEventDestroy(p->ev_in[s][k]);
+            if (p->ev_out[s][k]) cudaEventDestroy(p->ev_out[s][k]);
+        }
     }
+    if (p->h2d_st) cudaStreamDestroy(p->h2d_st);
+    if (p->d2h_st) cudaStreamDestroy(p->d2h_st);
     for (int s = 0; s < ipf_plan_s::kSlots; ++s)
         for (int i = 0; i < 6; ++i)
             if (p->ev[s][i]) cudaEventDestroy(p->ev[s][i]);
@@ -746,31 +793,24 @@ int ipf_solve(ipf_plan_t p, const void *d_src, void *d_phi, void *stream)
 int ipf_solve_host(ipf_plan_t p, const void *h_src, void *h_phi, void *stream)
 {
     if (!p || !h_src || !h_phi) return IPF_INVALID_ARG;
-    cudaStream_t st = (cudaStream_t)stream;
-    const size_t bytes = elem_size(p->dtype) * (size_t)p->N[0] * (size_t)p->N[1] * (size_t)p->N[2];
-    if (!p->stage) {
-        cudaError_t e = cudaMalloc(&p->stage, bytes);
-        if (e != cudaSuccess) {
-            p->stage = nullptr;
-            return cuda_status(e);
-        }
-    }
-    if (!p->copy_st) {
-        cudaError_t e = cudaStreamCreateWithFlags(&p->copy_st, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_done, cudaEventDisableTiming);
-        for (int k = 0; k < ipf_plan_s::kChunks && e == cudaSuccess; ++k) {
-            e = cudaEventCreateWithFlags(&p->ev_in[k], cudaEventDisableTiming);
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_out[k], cudaEventDisableTiming);
-        }
-        if (e != cudaSuccess) return cuda_status(e);
-    }
-    cudaError_t e = p->dtype == IPF_F32   ? enqueue_solve_host<float>(p, h_src, h_phi, st)
-                    : p->dtype == IPF_F64 ? enqueue_solve_host<double>(p, h_src, h_phi, st)
-                                          : enqueue_solve_host<df64>(p, h_src, h_phi, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    const int rc = enqueue_host(p, h_src, h_phi, ipf_plan_s::kChunks, (cudaStream_t)stream);
+    if (rc) return rc;
+    return ipf_plan_host_wait(p);
+}
+
+int ipf_solve_host_async(ipf_plan_t p, const void *h_src, void *h_phi, void *stream)
+{
+    if (!p || !h_src || !h_phi) return IPF_INVALID_ARG;
+    return enqueue_host(p, h_src, h_phi, ipf_plan_s::kAsyncChunks, (cudaStream_t)stream);
+}
+
+int ipf_plan_host_wait(ipf_plan_t p)
+{
+    if (!p) return IPF_INVALID_ARG;
+    if (!p->d2h_st) return IPF_OK;  // no host-buffer solve yet
+    const cudaError_t e = cudaStreamSynchronize(p->d2h_st);
     if (e != cudaSuccess) return cuda_status(e);
-    return read_status(p, st);
+    return read_status(p, p->d2h_st);
 }
 
 int ipf_plan_check(ipf_plan_t p, void *stream)

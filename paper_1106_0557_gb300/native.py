@@ -59,6 +59,8 @@ def _declare(L):
         "ipf_estimate_bytes": [i64p, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
         "ipf_solve": [vp, vp, vp, vp],
         "ipf_solve_host": [vp, vp, vp, vp],
+        "ipf_solve_host_async": [vp, vp, vp, vp],
+        "ipf_plan_host_wait": [vp],
         "ipf_solve_noalloc": [i64p, dp, ctypes.c_int, vp, vp, vp],
         "ipf_plan_check": [vp, vp],
         "ipf_plan_variants": [vp, ctypes.POINTER(ctypes.c_int)],
@@ -176,6 +178,16 @@ def ipf_plan_variants(plan):
 
 def ipf_noalloc_check(stream=0):
     _check(lib().ipf_noalloc_check(ctypes.c_void_p(int(stream))), "ipf_noalloc_check")
+
+
+def ipf_solve_host_async(plan, h_src, h_phi, stream=0):
+    _check(lib().ipf_solve_host_async(ctypes.c_void_p(plan), ctypes.c_void_p(int(h_src)),
+                                      ctypes.c_void_p(int(h_phi)), ctypes.c_void_p(int(stream))),
+           "ipf_solve_host_async")
+
+
+def ipf_plan_host_wait(plan):
+    _check(lib().ipf_plan_host_wait(ctypes.c_void_p(plan)), "ipf_plan_host_wait")
 
 
 def ipf_solve_noalloc(n, h, dtype, d_src, d_phi, stream=0):

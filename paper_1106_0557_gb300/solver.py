@@ -74,6 +74,22 @@ class Plan:
         native.ipf_solve_host(self.handle, src.ctypes.data, out.ctypes.data, _stream_handle(stream))
         return out
 
+    def solve_host_async(self, src, out, stream=None):
+        """Enqueue a solve from host array `src` into host array `out`
+        (numpy arrays or CPU torch tensors, pinned for asynchronous copies)
+        and return at once; both must stay alive and untouched until
+        host_wait()."""
+        def ptr(a):
+            return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+        for a in (src, out):
+            if tuple(a.shape) != self.shape:
+                raise ValueError("array shape %s != %s" % (tuple(a.shape), self.shape))
+        native.ipf_solve_host_async(self.handle, ptr(src), ptr(out), _stream_handle(stream))
+
+    def host_wait(self):
+        """Wait for every host solve enqueued on this plan."""
+        native.ipf_plan_host_wait(self.handle)
+
     def pass_times(self):
         return native.ipf_plan_pass_times(self.handle)
 

@@ -25,7 +25,7 @@ def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ["ipf_plan_create", "ipf_plan_destroy", "ipf_solve", "ipf_submit_batch",
                      "ipf_greens_cache_bytes", "ipf_greens_cache_trim", "ipf_status_string",
-                     "ipf_plan_workspace_bytes", "ipf_solve_host"]:
+                     "ipf_plan_workspace_bytes", "ipf_solve_host", "ipf_solve_host_async", "ipf_plan_host_wait"]:
         assert required in names
 
 
@@ -84,5 +84,7 @@ def test_null_handles():
     assert native.lib().ipf_plan_pass_times(None, None) == native.IPF_INVALID_ARG
     assert native.lib().ipf_plan_check(None, None) == native.IPF_INVALID_ARG
     assert native.lib().ipf_plan_variants(None, None) == native.IPF_INVALID_ARG
+    assert native.lib().ipf_solve_host_async(None, None, None, None) == native.IPF_INVALID_ARG
+    assert native.lib().ipf_plan_host_wait(None) == native.IPF_INVALID_ARG
     assert native.ipf_greens_cache_bytes() >= 0
     assert native.ipf_launch_count() >= 0

@@ -344,6 +344,25 @@ def test_host_buffer_solve_equals_device_solve(N, dtype):
     assert np.array_equal(again, dev)
 
 
+@pytest.mark.parametrize("dtype", ["f32", "df64"])
+def test_async_host_solves_in_flight_together(dtype):
+    """Several host solves enqueued back to back on one plan (they alternate
+    between its two staging buffers, and each one's copies overlap its
+    neighbours' passes) each return the potential of their own source,
+    bitwise the device solve's."""
+    from paper_1106_0557_gb300 import Plan
+    N = (48, 40, 33)
+    srcs = [torch.from_numpy(rand_src(N, 30 + i).astype(NP[dtype])).pin_memory() for i in range(5)]
+    outs = [torch.empty_like(s).pin_memory() for s in srcs]
+    with Plan(N, (1.0, 1.0, 1.0), dtype) as p:
+        want = [p.solve(s.cuda()).cpu() for s in srcs]
+        for s, o in zip(srcs, outs):
+            p.solve_host_async(s, o)
+        p.host_wait()
+    for o, w in zip(outs, want):
+        assert torch.equal(o, w)
+
+
 @pytest.mark.parametrize("dtype", ["f32", "f64", "df64"])
 @pytest.mark.parametrize("N", [(64, 64, 64), (37, 200, 13), (256, 256, 40), (20, 300, 17), (9, 700, 8)])
 def test_y_pass_forms_are_bitwise_equal(N, dtype):
