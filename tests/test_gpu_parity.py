@@ -418,3 +418,15 @@ def test_bounded_wait_runout_reports_timeout_and_the_gpu_stays_usable():
         p.check()  # the status word was cleared
     phi, s64 = gpu_solve(src, h, "f32")
     assert oracle.max_rel_error(phi, oracle.solve(s64, h)) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "df64", "f32"])
+def test_gpu_matches_the_stored_direct_sums(dtype):
+    """The GPU path at the cells of tests/golden/ (values of the direct sum
+    of the definition, written by tests/golden/make_golden.py from the
+    oracle only)."""
+    import test_golden
+    for name, src, h in test_golden.golden_sources():
+        cells, want = test_golden.golden(name)
+        phi, _ = gpu_solve(src, h, dtype)
+        assert np.max(np.abs(phi.ravel()[cells] - want)) / np.max(np.abs(phi)) <= TOL[dtype]
