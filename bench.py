@@ -340,12 +340,13 @@ def run_batch(steps=50, count=64):
     srcs = [torch.from_numpy(w.source(np.float32)).cuda() for w in wl]
     outs = [torch.empty_like(x) for x in srcs]
     nbytes = 0
+    fused = os.environ.get("ISOFFT_FUSE_XY") == "1"  # the fused x+y passes are opt-in
     for p, w in zip(plans, wl):
         b = pass_bytes(w.N, p.padded_shape, 4)
-        if p.padded_shape[0] == p.padded_shape[1]:
+        if fused and p.padded_shape[0] == p.padded_shape[1]:
             nbytes += 2 * b["_xy"] + b["z_convolve"]
         else:
-            nbytes += sum(v for k, v in b.items() if not k.startswith("_"))
+            nbytes += sum(b[k] for k in PASSES)
     res = {"grids": count, "workload": "ragged batch, each axis from {32,48,64,96,128}, seed = grid index"}
     for mode in ("graph", "submit"):
         if mode == "graph":
