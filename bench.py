@@ -130,10 +130,16 @@ KERNEL_SOURCES = ("df64.cuh", "fft_engine.cuh", "launch.h", "passes.cuh", "passe
 
 
 def sources_digest():
+    """Digest of the kernel sources' code (comments and blank lines left
+    out, so that a comment edit does not make a capture stale)."""
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1106_0557_gb300", "csrc")
     for fn in KERNEL_SOURCES:
-        h.update(open(os.path.join(csrc, fn), "rb").read())
+        t = open(os.path.join(csrc, fn)).read()
+        t = re.sub(r"/\*.*?\*/", "", t, flags=re.S)
+        t = re.sub(r"//[^\n]*", "", t)
+        h.update("\n".join(line.rstrip() for line in t.splitlines() if line.strip()).encode())
     return h.hexdigest()[:16]
 
 

@@ -9,9 +9,10 @@
 //              rest of its line as zero, and writes back only z < Nz.
 //   G        : real, the transform of the Eq. 9 table on the even octant (it
 //              is real and even in every axis) in the tiled order of
-//              ZSpecLayout, [My/2 + 1][kx tiles][Mz/2 + 1][tile width],
-//              pre-divided by 2 Mx My Mz (the factor 2 undoes the packed x
-//              spectra, which carry 2X); column kx = 0 holds (G0 + GN) / 2,
+//              ZSpecLayout, [My/2 + 1][kx tiles][Mz/2 + 1][tile width] (each
+//              tile block padded to 16 bytes), pre-divided by 2 Mx My Mz (the
+//              factor 2 undoes the packed x spectra, which carry 2X); column
+//              kx = 0 holds (G0 + GN) / 2,
 //   Gs       : real [My/2 + 1][Mz/2 + 1], (G0 - GN) / 2, where G0 and GN are
 //              the spectrum at kx = 0 and kx = Mx/2.
 //
@@ -27,6 +28,10 @@
 //   K3 z         : W z < Nz -> FFT_z, x spectrum, inverse FFT_z -> W z < Nz
 //   K4 y inverse : W all rows -> W rows y < Ny                  (output pruned)
 //   K5 x inverse : W rows y < Ny -> real rows, x < Nx           (output pruned)
+//
+// K3 and the streamed form of K2/K4 are persistent and receive their tiles
+// through the tensor memory accelerator (tma.cuh); K1, K5 and the tile form
+// of K2/K4 load with plain coalesced accesses, many CTAs per SM.
 #pragma once
 #include "fft_engine.cuh"
 #include "launch.h"
