@@ -239,14 +239,25 @@ struct ZCfg {
     // shared memory (read by every stage, loaded once per CTA)
     static constexpr bool TWR = ZShape<T, L>::TW_REGS;
     static constexpr size_t TWS = TWR ? 0 : (size_t)L * sizeof(Cx<T>);
-    static constexpr size_t SMEM = z_smem(TX, L, (int)sizeof(T)) + TWS;
     static constexpr int MIN_BLOCKS = sizeof(T) == 8 && E == 12 && NT >= 32 && NT <= 64 ? 3 : 1;
+    // Two exchange buffers used in turn need one CTA barrier per exchange
+    // instead of two; the input is then staged once per tile (the next
+    // tile's copies start after the first exchange's barrier, when every
+    // thread has read its input).  Taken wherever the extra buffer fits the
+    // CTAs per SM (every length but 2304); otherwise two input sets.
+    static constexpr size_t SMEM_DBX = 2 * XCH + IN_SET + 2 * G_SET + 16 + TWS;
+    static constexpr bool DBX = SMEM_DBX <= 227 * 1024 && MIN_BLOCKS * (SMEM_DBX + 1024) <= 228 * 1024;
+    static constexpr int NXB = DBX ? 2 : 1;  // exchange buffers
+    static constexpr int NIN = DBX ? 1 : 2;  // input sets
+    static constexpr size_t OFF_IN = NXB * XCH, OFF_G = OFF_IN + NIN * IN_SET, OFF_BAR = OFF_G + 2 * G_SET,
+                            OFF_TW = OFF_BAR + 16;
+    static constexpr size_t SMEM = OFF_TW + TWS;
     // rows of 32 bytes or less put several positions on one bank row: the
     // lines that keep their twiddles in shared memory swizzle them (the
     // register-twiddle shapes would spill under the extra address registers;
     // wider rows go without, see ColXch)
     static constexpr bool SWZ = !TWR && COLS * sizeof(Cx<T>) <= 32;
-    static_assert(SMEM == XCH + 2 * IN_SET + 2 * G_SET + 16 + TWS, "z pass shared-memory layout");
+    static_assert(DBX || SMEM == z_smem(TX, L, (int)sizeof(T)) + TWS, "z pass shared-memory layout");
     static_assert(MIN_BLOCKS * SMEM <= 227 * 1024, "z pass CTAs per SM exceed shared memory");
     static_assert(THREADS <= 1024, "z tile too large");
     static_assert(SMEM <= 227 * 1024, "z tile exceeds shared memory");
@@ -583,6 +594,40 @@ template <typename T, int L, int E, typename Rad>
 struct ZTwiddles<false, T, L, E, Rad> {
     using type = TwRegs<T, L, E, 1>;  // holds nothing
 };
+// z-pass exchanger.  With DB (two buffers, used in turn) an exchange needs a
+// single CTA barrier: a buffer is next written two exchanges later, after
+// the barrier of the exchange in between, which follows every read of its
+// previous use.  `hook` runs after the barrier of the tile's first exchange
+// (DB only); `free_buf()` is a buffer that no thread still reads.
+template <typename T, int L, int E, int COLS, bool SWZ, bool DB, typename Hook>
+struct ZXch {
+    using Rows = ColXch<T, L, E, COLS, SWZ>;
+    Cx<T> *a;  // DB: the second buffer follows at a + L COLS
+    int c;
+    Hook &hook;
+    int k = 0;  // exchanges done in this tile
+    __device__ __forceinline__ Cx<T> *buf(int i) const { return DB && (i & 1) ? a + (size_t)L * COLS : a; }
+    __device__ __forceinline__ Cx<T> *free_buf() const { return buf(k); }
+    template <int NS, int R>
+    __device__ __forceinline__ void exchange(Cx<T> (&v)[E], int t)
+    {
+        using G = StageGeom<L, E, NS, R>;
+        Cx<T> *s = buf(k);
+#pragma unroll
+        for (int q = 0; q < G::B; ++q)
+#pragma unroll
+            for (int r = 0; r < R; ++r) s[Rows::row(G::out_pos(t, q, r)) * COLS + c] = v[q + r * G::B];
+        __syncthreads();
+        if constexpr (DB) {
+            if (k == 0) hook();
+        }
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = s[Rows::row(t + m * G::NT) * COLS + c];
+        if constexpr (!DB) __syncthreads();
+        ++k;
+    }
+};
+
 template <bool TWR, bool HALF, typename T, int L, int E, typename TW, typename Xch, typename Rad>
 __device__ __forceinline__ void z_fft(Cx<T> (&v)[E], int t, const TW &twr, const Cx<T> *__restrict__ tw, Xch &xch,
                                       Rad)
@@ -961,10 +1006,12 @@ k_yx_inverse(Cx<T> *__restrict__ W, In<T> *__restrict__ phi, const Cx<T> *__rest
 // 256 planes of W (tmW: 8-byte elements, dims {Kx EPC, My, Nz}; planes
 // z >= Nz and columns kx >= Kx read as zero) and a bulk copy of the tile's
 // spectrum block (a second one for the pair p = 0, whose line My/2 has its
-// own k_y').  Slot set s = tile parity; its mbarrier completes once per use.
-// A set is refilled at the top of the tile after the one that read it, and
-// that tile's reads are all behind the CTA barriers of the transform that
-// followed them.
+// own k_y').  The spectrum set is the tile's parity.  With two input sets
+// (one mbarrier each) the next tile's copies are issued at the top of the
+// tile, into the set the previous tile read; with one (and two exchange
+// buffers) they are issued after the barrier of the tile's first exchange,
+// which every thread reaches after reading its input.  Either way the reads
+// of a set precede a CTA barrier that precedes its refill.
 // ---------------------------------------------------------------------
 template <typename T, int L>
 __global__ void __launch_bounds__(ZCfg<T, L>::THREADS, ZCfg<T, L>::MIN_BLOCKS)
@@ -976,10 +1023,10 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
     constexpr int E = C::E, NT = C::NT, TX = C::TX, COLS = C::COLS;
     constexpr int Lh = L / 2;
     extern __shared__ __align__(128) unsigned char zsmem[];
-    Cx<T> *sm = reinterpret_cast<Cx<T> *>(zsmem);             // exchange buffer
-    unsigned char *s_in = zsmem + C::XCH;                      // [set][g][z < Lh][TX]
-    T *s_g = reinterpret_cast<T *>(zsmem + C::XCH + 2 * C::IN_SET);  // [set][2][GBLK]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(zsmem + C::XCH + 2 * C::IN_SET + 2 * C::G_SET);
+    Cx<T> *sm = reinterpret_cast<Cx<T> *>(zsmem);             // exchange buffer(s)
+    unsigned char *s_in = zsmem + C::OFF_IN;                   // [set][g][z < Lh][TX]
+    T *s_g = reinterpret_cast<T *>(zsmem + C::OFF_G);          // [set][2][GBLK]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(zsmem + C::OFF_BAR);  // one per input set
     // thread -> (column c, group g, position t): a warp holds both groups of
     // a few positions, so each position row of the exchange buffer is written
     // whole and the warp's shared-memory accesses are conflict-free
@@ -998,24 +1045,26 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
         return;
     }
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int i = 0; i < C::NIN; ++i) mbar_init(&bar[i], 1);
         mbar_init_fence();
     }
     const Cx<T> *twz = tw;  // the twiddle table the stages read
     if constexpr (!C::TWR) {
-        Cx<T> *s_tw = reinterpret_cast<Cx<T> *>(zsmem + C::XCH + 2 * C::IN_SET + 2 * C::G_SET + 16);
+        Cx<T> *s_tw = reinterpret_cast<Cx<T> *>(zsmem + C::OFF_TW);
         for (int i = tid; i < L; i += C::THREADS) s_tw[i] = tw[i];
         twz = s_tw;
     }
     __syncthreads();
 
-    auto issue = [&](int tile, int set, uint32_t extra) {  // thread 0
+    // copies of a tile into spectrum set `set` (and input set `set` when
+    // there are two), issued by thread 0
+    auto issue = [&](int tile, int set, uint32_t extra) {
         const int pr = tile / ntx, xt = tile - pr * ntx;
         const int ky1 = pr == 0 ? My / 2 : My - pr;
-        uint64_t *b = &bar[set];
+        const int is = C::DBX ? 0 : set;
+        uint64_t *b = &bar[is];
         mbar_arrive_expect_tx(b, (uint32_t)(C::IN_SET + (pr == 0 ? 2 : 1) * C::G_BLK) + extra);
-        unsigned char *dst = s_in + set * C::IN_SET;
+        unsigned char *dst = s_in + is * C::IN_SET;
 #pragma unroll
         for (int zb = 0; zb < C::NZB; ++zb) {
             const size_t off = (size_t)zb * C::BOXZ * TX * sizeof(Cx<T>);
@@ -1027,7 +1076,6 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
         if (pr == 0) bulk_load(gdst + C::GBLK, G + lay.block(My / 2, xt), (uint32_t)C::G_BLK, b);
     };
 
-    ColXch<T, L, E, COLS, C::SWZ> xch{sm, col};
     using Rad = typename ZShape<T, L>::Rad;
     constexpr bool TWR = C::TWR;
     typename ZTwiddles<TWR, T, L, E, Rad>::type twr;  // this thread's twiddles, for every tile (when TW_REGS)
@@ -1040,8 +1088,16 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
     for (; tile < ntiles; tile += gridDim.x, ++it) {
         const int next = tile + gridDim.x;
         const int set = it & 1;
-        if (tid == 0 && next < ntiles) issue(next, set ^ 1, 0u);
-        const bool landed = mbar_wait_bounded(&bar[set], (uint32_t)(it >> 1) & 1u, kCopyWaitNs);
+        auto next_copies = [&]() {
+            if (tid == 0 && next < ntiles) issue(next, set ^ 1, 0u);
+        };
+        ZXch<T, L, E, COLS, C::SWZ, C::DBX, decltype(next_copies)> xch{sm, col, next_copies};
+        // two input sets: the next tile's copies go out now, and each set's
+        // barrier completes every other tile; one set: they go out after the
+        // first exchange, and its barrier completes once per tile
+        if constexpr (!C::DBX) next_copies();
+        const bool landed = C::DBX ? mbar_wait_bounded(&bar[0], (uint32_t)it & 1u, kCopyWaitNs)
+                                   : mbar_wait_bounded(&bar[set], (uint32_t)(it >> 1) & 1u, kCopyWaitNs);
         if (!__syncthreads_and(landed)) {
             ok = false;
             break;
@@ -1053,7 +1109,8 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
         const int kyp = ky <= My - ky ? ky : My - ky;
 
         // z < Lh from the staged boxes (zeros past Nz), the upper half is zero
-        const Cx<T> *sin = reinterpret_cast<const Cx<T> *>(s_in + set * C::IN_SET + g * C::IN_GROUP) + t * TX + c;
+        const Cx<T> *sin = reinterpret_cast<const Cx<T> *>(s_in + (C::DBX ? 0 : set) * C::IN_SET + g * C::IN_GROUP) +
+                           t * TX + c;
         Cx<T> v[E];
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = m < E / 2 ? sin[m * NT * TX] : Cx<T>{(T)0, (T)0};
@@ -1068,9 +1125,10 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
         const bool packed = xt == 0 && c == 0;  // the kx = 0 / Mx/2 column
         if (xt == 0) {
             // the packed column needs the partner bin (-ky, -kz)
+            Cx<T> *sp = xch.free_buf();
             if (c == 0) {
 #pragma unroll
-                for (int m = 0; m < E; ++m) sm[(t + m * NT) * COLS + col] = v[m];
+                for (int m = 0; m < E; ++m) sp[(t + m * NT) * COLS + col] = v[m];
             }
             __syncthreads();
             if (c == 0) {
@@ -1080,7 +1138,7 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
                 for (int m = 0; m < E; ++m) {
                     const int kz = t + m * NT;
                     const int kzp = kz <= L - kz ? kz : L - kz;
-                    const Cx<T> partner = cconj(sm[(kz == 0 ? 0 : L - kz) * COLS + gp * TX]);
+                    const Cx<T> partner = cconj(sp[(kz == 0 ? 0 : L - kz) * COLS + gp * TX]);
                     const T gp_ = gval(m) * gscale;
                     const T gm_ = gsrow[kzp] * gscale;
                     v[m] = {v[m].x * gp_ + partner.x * gm_, v[m].y * gp_ + partner.y * gm_};
@@ -1105,11 +1163,14 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
             }
         }
     }
-    if (!ok) {
-        // a wait gave up: flag it, then let this tile's and the next tile's
-        // copies land (bounded again) before the CTA's shared memory is freed
-        if (tid == 0) {
-            if (status) atomicOr(status, 1u);
+    if (!ok && tid == 0) {
+        // a wait gave up: flag it, then let the copies in flight land
+        // (bounded again) before the CTA's shared memory is freed: this
+        // tile's, and with two input sets the next tile's
+        if (status) atomicOr(status, 1u);
+        if constexpr (C::DBX) {
+            mbar_wait_bounded(&bar[0], (uint32_t)it & 1u, kCopyWaitNs);
+        } else {
             mbar_wait_bounded(&bar[it & 1], (uint32_t)(it >> 1) & 1u, kCopyWaitNs);
             if (tile + (int)gridDim.x < ntiles)
                 mbar_wait_bounded(&bar[(it + 1) & 1], (uint32_t)((it + 1) >> 1) & 1u, kCopyWaitNs);
