@@ -190,9 +190,10 @@ struct ColCfg {
 // z pass tiles: TX columns of the two lines ky and My - ky (2 TX lines),
 // processed by a persistent CTA.  While it transforms one tile, the tensor
 // memory accelerator copies the next tile's non-zero half (z < Mz/2, one box
-// per line group and 256 planes) and its Green's spectrum block into the
-// other of two shared-memory slot sets.  FP64 tiles are narrower: FP64
-// arithmetic, not memory, bounds that path.
+// per line group and 256 planes) and its Green's spectrum block into shared
+// memory (k_z_convolve describes the two staging schemes).  FP64 tiles are
+// narrower: FP64 arithmetic, not memory, bounds that path.  The tile width
+// is chosen on the layout with one exchange buffer and two input sets:
 constexpr size_t z_smem(int tx, int L, int rb)
 {
     return (size_t)L * 2 * tx * 2 * rb                                  // exchange buffer
@@ -671,12 +672,18 @@ struct YCfg {
     static constexpr int NB_I = boxes(L), BOX_I = L / NB_I;          // K4 reads every row
     static constexpr size_t XCH = (size_t)L * TX * CB;
     static constexpr size_t IN_F = (size_t)(L / 2) * TX * CB, IN_I = (size_t)L * TX * CB;
-    static constexpr size_t SMEM_F = XCH + 2 * IN_F + 16, SMEM_I = XCH + 2 * IN_I + 16;
-    static constexpr int MIN_BLOCKS = THREADS <= 512 && SMEM_I <= 110 * 1024 ? 2 : 1;
+    static constexpr int MIN_BLOCKS = THREADS <= 512 && smem_i(TX) <= 110 * 1024 ? 2 : 1;
+    // a second exchange buffer (one CTA barrier per exchange, see ZXch)
+    // where it still fits the resident CTAs
+    static constexpr bool fits(size_t bytes) { return bytes <= 227 * 1024 && MIN_BLOCKS * (bytes + 1024) <= 228 * 1024; }
+    static constexpr bool DBX_F = fits(2 * XCH + 2 * IN_F + 16), DBX_I = fits(2 * XCH + 2 * IN_I + 16);
+    static constexpr size_t SMEM_F = (DBX_F ? 2 : 1) * XCH + 2 * IN_F + 16,
+                            SMEM_I = (DBX_I ? 2 : 1) * XCH + 2 * IN_I + 16;
     // twiddles in registers across tiles, except for the long lines, whose
     // per-thread share (29 points for 2304) would spill
     static constexpr bool TW_REGS = L <= 1024;
-    static_assert(SMEM_I == smem_i(TX) && SMEM_I <= 227 * 1024, "y pass shared memory");
+    static_assert(smem_i(TX) == XCH + 2 * IN_I + 16 && SMEM_I <= 227 * 1024 && SMEM_F <= 227 * 1024,
+                  "y pass shared memory");
     static_assert(TX * CB % 16 == 0, "tensor box rows must be multiples of 16 bytes");
     static_assert(XCH % 128 == 0 && IN_F % 128 == 0 && ((size_t)BOX_F * TX * CB) % 128 == 0 &&
                       ((size_t)BOX_I * TX * CB) % 128 == 0,
@@ -692,10 +699,11 @@ k_y_pass(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, const C
     constexpr int E = C::E, NT = C::NT, TX = C::TX;
     constexpr int NB = FWD ? C::NB_F : C::NB_I, BOX = FWD ? C::BOX_F : C::BOX_I;
     constexpr size_t IN = FWD ? C::IN_F : C::IN_I;
+    constexpr bool DBX = FWD ? C::DBX_F : C::DBX_I;
     extern __shared__ __align__(128) unsigned char ysmem[];
-    Cx<T> *xs = reinterpret_cast<Cx<T> *>(ysmem);
-    unsigned char *s_in = ysmem + C::XCH;  // [set][row][TX]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(ysmem + C::XCH + 2 * IN);
+    Cx<T> *xs = reinterpret_cast<Cx<T> *>(ysmem);            // exchange buffer(s)
+    unsigned char *s_in = ysmem + (DBX ? 2 : 1) * C::XCH;  // [set][row][TX]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(s_in + 2 * IN);
     const int tid = threadIdx.x;
     const int c = tid % TX, t = tid / TX;
     const int ntx = (Kx + TX - 1) / TX;
@@ -717,7 +725,7 @@ k_y_pass(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, const C
             tma_load_3d(s_in + set * IN + (size_t)b * BOX * TX * sizeof(Cx<T>), &tmW, xt * TX * C::EPC, b * BOX, z,
                         &bar[set]);
     };
-    ColXch<T, L, E, TX> xch{xs, c};
+    auto no_hook = [] {};
     using Rad = typename Shape<T, L>::Rad;
     typename ZTwiddles<C::TW_REGS, T, L, E, Rad>::type twr;
     twr.load(tw, t);
@@ -736,6 +744,7 @@ k_y_pass(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, const C
         const int z = tile / ntx, xt = tile - z * ntx;
         const int kx = xt * TX + c;
         const Cx<T> *sin = reinterpret_cast<const Cx<T> *>(s_in + set * IN) + t * TX + c;
+        ZXch<T, L, E, TX, true, DBX, decltype(no_hook)> xch{xs, c, no_hook};
         Cx<T> v[E];
         if constexpr (FWD) {
 #pragma unroll
