@@ -166,6 +166,13 @@ struct RowCfg {
     static constexpr int NL = NT >= 256 ? 1 : 256 / NT;  // rows per CTA
     static constexpr int THREADS = NL * NT;
     static constexpr size_t SMEM = (size_t)NL * RowPad<T, L>::LP * sizeof(Cx<T>);
+    // Stage twiddles held in registers across the rows of a persistent CTA
+    // (K1: TWR_F, K5: TWR_I) where that measured faster than reading the
+    // table in every stage: FP32 forward rows of 192 and 384 points, inverse
+    // rows of 128 and 384.  Elsewhere the extra registers cost more
+    // occupancy than the table reads do.
+    static constexpr bool TWR_F = sizeof(T) == 4 && (L == 192 || L == 384);
+    static constexpr bool TWR_I = sizeof(T) == 4 && (L == 128 || L == 384);
 };
 
 // Column tiles of the y passes: up to 128 bytes of complex per row and at
@@ -336,10 +343,33 @@ __device__ __forceinline__ Cx<T> mirror_partner(const Cx<T> (&v)[E], int m, int 
 template <typename T>
 using In = typename IoReal<T>::type;  // real type of the source / potential arrays
 
-template <typename T, int L>
+// Twiddles of the persistent passes: held in registers across lines, or
+// (TWR false) read from the table by each stage.
+template <bool TWR, typename T, int L, int E, typename Rad>
+struct ZTwiddles {
+    using type = typename TwRegsOf<T, L, E, Rad>::type;
+};
+template <typename T, int L, int E, typename Rad>
+struct ZTwiddles<false, T, L, E, Rad> {
+    using type = TwRegs<T, L, E, 1>;  // holds nothing
+};
+template <bool TWR, bool HALF, typename T, int L, int E, typename TW, typename Xch, typename Rad>
+__device__ __forceinline__ void z_fft(Cx<T> (&v)[E], int t, const TW &twr, const Cx<T> *__restrict__ tw, Xch &xch,
+                                      Rad)
+{
+    if constexpr (TWR)
+        run_stages_reg<T, L, E, HALF>(v, t, twr, xch, Rad{});
+    else
+        run_stages<T, L, E, HALF>(v, t, tw, xch, Rad{});
+}
+template <bool TWR, typename T, int L>
+using RowTwiddles = typename ZTwiddles<TWR, T, L, XShape<T, L>::E, typename XShape<T, L>::Rad>::type;
+
+template <typename T, int L, bool TWR = false>
 __device__ __forceinline__ void x_forward_row_at(const In<T> *in, Cx<T> *__restrict__ out,
                                                  const Cx<T> *__restrict__ tw, const Cx<T> *__restrict__ rtw, int Nx,
-                                                 bool active, Cx<T> *line, int t)
+                                                 bool active, Cx<T> *line, int t,
+                                                 const RowTwiddles<TWR, T, L> &twr = {})
 {
     constexpr int E = XShape<T, L>::E, NT = L / E;
     using IO = IoReal<T>;
@@ -362,7 +392,7 @@ __device__ __forceinline__ void x_forward_row_at(const In<T> *in, Cx<T> *__restr
         }
     }
     RowXch<T, L, E> xch{line};
-    run_stages<T, L, E, true>(v, t, tw, xch, typename XShape<T, L>::Rad{});
+    z_fft<TWR, true, T, L, E>(v, t, twr, tw, xch, typename XShape<T, L>::Rad{});
 
     // split the half-length transform Z into the real row's spectrum:
     //   2X[k] = (Z[k] + conj Z[L-k]) + W_2L^k (-i)(Z[k] - conj Z[L-k]),
@@ -393,21 +423,22 @@ __device__ __forceinline__ void x_forward_row_at(const In<T> *in, Cx<T> *__restr
     }
 }
 
-template <typename T, int L>
+template <typename T, int L, bool TWR = false>
 __device__ __forceinline__ void x_forward_row(const In<T> *__restrict__ src, Cx<T> *__restrict__ W,
                                               const Cx<T> *__restrict__ tw, const Cx<T> *__restrict__ rtw, int Nx,
-                                              int Ny, int My, int64_t rr, bool active, Cx<T> *line, int t)
+                                              int Ny, int My, int64_t rr, bool active, Cx<T> *line, int t,
+                                              const RowTwiddles<TWR, T, L> &twr = {})
 {
     const int y = (int)(rr % Ny);
     const int64_t z = rr / Ny;
-    x_forward_row_at<T, L>(src + rr * Nx, W + ((size_t)z * My + y) * L, tw, rtw, Nx, active, line, t);
+    x_forward_row_at<T, L, TWR>(src + rr * Nx, W + ((size_t)z * My + y) * L, tw, rtw, Nx, active, line, t, twr);
 }
 
 // K5 body: packed half spectrum of row rr -> real row, cropped to x < Nx.
-template <typename T, int L, bool CG = false>
+template <typename T, int L, bool CG = false, bool TWR = false>
 __device__ __forceinline__ void x_inverse_row_at(const Cx<T> *in, In<T> *__restrict__ out, const Cx<T> *__restrict__ tw,
                                                  const Cx<T> *__restrict__ rtw, int Nx, bool active, Cx<T> *line,
-                                                 int t)
+                                                 int t, const RowTwiddles<TWR, T, L> &twr = {})
 {
     constexpr int E = XShape<T, L>::E, NT = L / E;
     // (The mirror point X[L-k] goes through shared memory here: a shuffle
@@ -442,7 +473,7 @@ __device__ __forceinline__ void x_inverse_row_at(const Cx<T> *in, In<T> *__restr
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = cswap(v[m]);
     RowXch<T, L, E> xch{line};
-    run_stages<T, L, E, false>(v, t, tw, xch, typename XShape<T, L>::Rad{});
+    z_fft<TWR, false, T, L, E>(v, t, twr, tw, xch, typename XShape<T, L>::Rad{});
     const bool vec = (Nx & 1) == 0;
 #pragma unroll
     for (int m = 0; m < E / 2; ++m) {
@@ -459,14 +490,15 @@ __device__ __forceinline__ void x_inverse_row_at(const Cx<T> *in, In<T> *__restr
     }
 }
 
-template <typename T, int L, bool CG = false>
+template <typename T, int L, bool CG = false, bool TWR = false>
 __device__ __forceinline__ void x_inverse_row(const Cx<T> *__restrict__ W, In<T> *__restrict__ phi,
                                               const Cx<T> *__restrict__ tw, const Cx<T> *__restrict__ rtw, int Nx,
-                                              int Ny, int My, int64_t rr, bool active, Cx<T> *line, int t)
+                                              int Ny, int My, int64_t rr, bool active, Cx<T> *line, int t,
+                                              const RowTwiddles<TWR, T, L> &twr = {})
 {
     const int y = (int)(rr % Ny);
     const int64_t z = rr / Ny;
-    x_inverse_row_at<T, L, CG>(W + ((size_t)z * My + y) * L, phi + rr * Nx, tw, rtw, Nx, active, line, t);
+    x_inverse_row_at<T, L, CG, TWR>(W + ((size_t)z * My + y) * L, phi + rr * Nx, tw, rtw, Nx, active, line, t, twr);
 }
 
 // K2 body: y forward of columns kx0 .. kx0 + TX - 1 of plane z.  Rows
@@ -529,7 +561,10 @@ __device__ __forceinline__ void y_inverse_tile(Cx<T> *__restrict__ W, const Cx<T
 }
 
 // ---------------------------------------------------------------------
-// K1 / K5: x passes, RowCfg::NL rows per CTA.
+// K1 / K5: x passes, RowCfg::NL rows per CTA and round.  With register
+// twiddles the grid is persistent (as many CTAs as are resident) and each
+// CTA walks groups of NL rows, loading its threads' twiddles once; otherwise
+// every CTA takes one group.
 // ---------------------------------------------------------------------
 template <typename T, int L>
 __global__ void __launch_bounds__(RowCfg<T, L>::THREADS)
@@ -540,9 +575,24 @@ k_x_forward(const In<T> *__restrict__ src, Cx<T> *__restrict__ W, const Cx<T> *_
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int t = threadIdx.x % C::NT, l = threadIdx.x / C::NT;
     Cx<T> *line = reinterpret_cast<Cx<T> *>(smem_raw) + l * RowPad<T, L>::LP;
-    const int64_t row = (int64_t)blockIdx.x * C::NL + l;  // row = z * Ny + y
-    const bool active = row < nrows;
-    x_forward_row<T, L>(src, W, tw, rtw, Nx, Ny, My, active ? row : 0, active, line, t);
+    if constexpr (C::TWR_F) {
+        RowTwiddles<true, T, L> twr;
+        twr.load(tw, t);
+        for (int64_t r0 = (int64_t)blockIdx.x * C::NL; r0 < nrows; r0 += (int64_t)gridDim.x * C::NL) {
+            const int64_t row = r0 + l;  // row = z * Ny + y
+            const bool active = row < nrows;
+            x_forward_row<T, L, true>(src, W, tw, rtw, Nx, Ny, My, active ? row : 0, active, line, t, twr);
+            // rows wider than a warp read their mirror points from `line`
+            // last: the next row's first exchange must wait for those reads
+            if constexpr (!(C::NT <= 32 && 32 % C::NT == 0)) {
+                if (r0 + (int64_t)gridDim.x * C::NL < nrows) __syncthreads();
+            }
+        }
+    } else {
+        const int64_t row = (int64_t)blockIdx.x * C::NL + l;
+        const bool active = row < nrows;
+        x_forward_row<T, L>(src, W, tw, rtw, Nx, Ny, My, active ? row : 0, active, line, t);
+    }
 }
 
 template <typename T, int L>
@@ -554,9 +604,19 @@ k_x_inverse(const Cx<T> *__restrict__ W, In<T> *__restrict__ phi, const Cx<T> *_
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int t = threadIdx.x % C::NT, l = threadIdx.x / C::NT;
     Cx<T> *line = reinterpret_cast<Cx<T> *>(smem_raw) + l * RowPad<T, L>::LP;
-    const int64_t row = (int64_t)blockIdx.x * C::NL + l;
-    const bool active = row < nrows;
-    x_inverse_row<T, L>(W, phi, tw, rtw, Nx, Ny, My, active ? row : 0, active, line, t);
+    if constexpr (C::TWR_I) {
+        RowTwiddles<true, T, L> twr;
+        twr.load(tw, t);
+        for (int64_t r0 = (int64_t)blockIdx.x * C::NL; r0 < nrows; r0 += (int64_t)gridDim.x * C::NL) {
+            const int64_t row = r0 + l;
+            const bool active = row < nrows;
+            x_inverse_row<T, L, false, true>(W, phi, tw, rtw, Nx, Ny, My, active ? row : 0, active, line, t, twr);
+        }
+    } else {
+        const int64_t row = (int64_t)blockIdx.x * C::NL + l;
+        const bool active = row < nrows;
+        x_inverse_row<T, L>(W, phi, tw, rtw, Nx, Ny, My, active ? row : 0, active, line, t);
+    }
 }
 
 // ---------------------------------------------------------------------
@@ -585,16 +645,6 @@ k_y_inverse(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx)
                                 threadIdx.x % C::TX, threadIdx.x / C::TX);
 }
 
-// Twiddles of the persistent column passes: held in registers across
-// tiles, or (TWR false) read from the table by each stage.
-template <bool TWR, typename T, int L, int E, typename Rad>
-struct ZTwiddles {
-    using type = typename TwRegsOf<T, L, E, Rad>::type;
-};
-template <typename T, int L, int E, typename Rad>
-struct ZTwiddles<false, T, L, E, Rad> {
-    using type = TwRegs<T, L, E, 1>;  // holds nothing
-};
 // z-pass exchanger.  With DB (two buffers, used in turn) an exchange needs a
 // single CTA barrier: a buffer is next written two exchanges later, after
 // the barrier of the exchange in between, which follows every read of its
@@ -629,15 +679,6 @@ struct ZXch {
     }
 };
 
-template <bool TWR, bool HALF, typename T, int L, int E, typename TW, typename Xch, typename Rad>
-__device__ __forceinline__ void z_fft(Cx<T> (&v)[E], int t, const TW &twr, const Cx<T> *__restrict__ tw, Xch &xch,
-                                      Rad)
-{
-    if constexpr (TWR)
-        run_stages_reg<T, L, E, HALF>(v, t, twr, xch, Rad{});
-    else
-        run_stages<T, L, E, HALF>(v, t, tw, xch, Rad{});
-}
 
 // ---------------------------------------------------------------------
 // K2 / K4, streamed form: persistent over column tiles (z, kx tile).  Thread 0

@@ -82,15 +82,24 @@ static EncodeTiledFn encode_tiled()
 
 
 #if ISOFFT_GROUP == 1
+// Row grid: one CTA per group of nl rows, at most `resident` when that is
+// set (persistent CTAs).
+static unsigned row_grid(int64_t nrows, int nl, int resident)
+{
+    const int64_t groups = (nrows + nl - 1) / nl;
+    return (unsigned)(resident > 0 && groups > resident ? resident : groups);
+}
 template <typename T, int L>
 static cudaError_t run_x_forward(const In<T> *src, void *W, const void *tw, const void *rtw, int Nx, int Ny,
                                  int My, int64_t nrows, cudaStream_t st)
 {
     using C = RowCfg<T, L>;
     static std::atomic<uint64_t> done{0};
+    static std::atomic<int> resident{0};
     cudaError_t e = ensure_smem(k_x_forward<T, L>, C::SMEM, done);
     if (e != cudaSuccess) return e;
-    const unsigned grid = (unsigned)((nrows + C::NL - 1) / C::NL);
+    const unsigned grid =
+        row_grid(nrows, C::NL, C::TWR_F ? resident_ctas(k_x_forward<T, L>, C::THREADS, C::SMEM, resident) : 0);
     k_x_forward<T, L><<<grid, C::THREADS, C::SMEM, st>>>(src, (Cx<T> *)W, (const Cx<T> *)tw,
                                                         (const Cx<T> *)rtw, Nx, Ny, My, nrows);
     count_launch();
@@ -102,9 +111,11 @@ static cudaError_t run_x_inverse(const void *W, In<T> *phi, const void *tw, cons
 {
     using C = RowCfg<T, L>;
     static std::atomic<uint64_t> done{0};
+    static std::atomic<int> resident{0};
     cudaError_t e = ensure_smem(k_x_inverse<T, L>, C::SMEM, done);
     if (e != cudaSuccess) return e;
-    const unsigned grid = (unsigned)((nrows + C::NL - 1) / C::NL);
+    const unsigned grid =
+        row_grid(nrows, C::NL, C::TWR_I ? resident_ctas(k_x_inverse<T, L>, C::THREADS, C::SMEM, resident) : 0);
     k_x_inverse<T, L><<<grid, C::THREADS, C::SMEM, st>>>((const Cx<T> *)W, phi, (const Cx<T> *)tw,
                                                         (const Cx<T> *)rtw, Nx, Ny, My, nrows);
     count_launch();
