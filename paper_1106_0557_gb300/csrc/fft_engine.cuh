@@ -257,6 +257,12 @@ struct DftHalf<T, 2> {
 // ---------------------------------------------------------------------
 template <int... Rs>
 struct Radices {};
+template <typename Rad>
+struct RadixCount;
+template <int... Rs>
+struct RadixCount<Radices<Rs...>> {
+    static constexpr int value = sizeof...(Rs);  // stages of the transform
+};
 
 template <int L, int E, int NS, int R>
 struct StageGeom {

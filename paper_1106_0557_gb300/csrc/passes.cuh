@@ -177,13 +177,16 @@ struct RowCfg {
 
 // Column tiles of the y passes: up to 128 bytes of complex per row and at
 // most 512 threads, so two or three tiles are resident per SM and one tile's
-// global loads overlap the others' butterflies.
+// global loads overlap the others' butterflies; rows of at least 32 bytes
+// (one sector) even where that takes more threads (FP32 2304-point lines).
 template <typename T, int L>
 struct ColCfg {
     static constexpr int E = Shape<T, L>::E;
     static constexpr int NT = L / E;
     static constexpr int TX0 = 128 / (int)sizeof(Cx<T>);
-    static constexpr int TX = TX0 * NT <= 512 ? TX0 : (512 / NT >= 1 ? 512 / NT : 1);
+    static constexpr int TXS = 32 / (int)sizeof(Cx<T>);  // one 32-byte sector
+    static constexpr int TXT = TX0 * NT <= 512 ? TX0 : (512 / NT >= 1 ? 512 / NT : 1);
+    static constexpr int TX = TXT >= TXS || TXS * NT > 1024 ? TXT : TXS;
     static constexpr int THREADS = TX * NT;
     static constexpr size_t SMEM = (size_t)L * TX * sizeof(Cx<T>);
     // FP32 forward: registers low enough for 3 resident CTAs per SM with 8
@@ -260,6 +263,13 @@ struct ZCfg {
     static constexpr size_t OFF_IN = NXB * XCH, OFF_G = OFF_IN + NIN * IN_SET, OFF_BAR = OFF_G + 2 * G_SET,
                             OFF_TW = OFF_BAR + 16;
     static constexpr size_t SMEM = OFF_TW + TWS;
+    // without DBX, two adjacent tiles share each box (k_z_convolve_pairs):
+    // the input set holds 2 TX columns, the spectrum sets both tiles' blocks
+    static constexpr int PTX = 2 * TX;
+    static constexpr size_t PIN_GROUP = (size_t)LH * PTX * sizeof(Cx<T>), PIN_SET = 2 * PIN_GROUP;
+    static_assert(DBX || (PIN_SET == NIN * IN_SET && PIN_GROUP % 128 == 0 &&
+                          ((size_t)BOXZ * PTX * sizeof(Cx<T>)) % 128 == 0),
+                  "paired z tiles: layout and 128-byte aligned copy destinations");
     // rows of 32 bytes or less put several positions on one bank row: the
     // lines that keep their twiddles in shared memory swizzle them (the
     // register-twiddle shapes would spill under the extra address registers;
@@ -648,8 +658,9 @@ k_y_inverse(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx)
 // z-pass exchanger.  With DB (two buffers, used in turn) an exchange needs a
 // single CTA barrier: a buffer is next written two exchanges later, after
 // the barrier of the exchange in between, which follows every read of its
-// previous use.  `hook` runs after the barrier of the tile's first exchange
-// (DB only); `free_buf()` is a buffer that no thread still reads.
+// previous use.  `hook(k)` runs after the (first) barrier of the tile's
+// exchange k, when every thread has finished what preceded that exchange;
+// `free_buf()` is a buffer that no thread still reads.
 template <typename T, int L, int E, int COLS, bool SWZ, bool DB, typename Hook>
 struct ZXch {
     using Rows = ColXch<T, L, E, COLS, SWZ>;
@@ -669,9 +680,7 @@ struct ZXch {
 #pragma unroll
             for (int r = 0; r < R; ++r) s[Rows::row(G::out_pos(t, q, r)) * COLS + c] = v[q + r * G::B];
         __syncthreads();
-        if constexpr (DB) {
-            if (k == 0) hook();
-        }
+        hook(k);
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = s[Rows::row(t + m * G::NT) * COLS + c];
         if constexpr (!DB) __syncthreads();
@@ -766,7 +775,7 @@ k_y_pass(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, const C
             tma_load_3d(s_in + set * IN + (size_t)b * BOX * TX * sizeof(Cx<T>), &tmW, xt * TX * C::EPC, b * BOX, z,
                         &bar[set]);
     };
-    auto no_hook = [] {};
+    auto no_hook = [](int) {};
     using Rad = typename Shape<T, L>::Rad;
     typename ZTwiddles<C::TW_REGS, T, L, E, Rad>::type twr;
     twr.load(tw, t);
@@ -1043,6 +1052,84 @@ k_yx_inverse(Cx<T> *__restrict__ W, In<T> *__restrict__ phi, const Cx<T> *__rest
     }
 }
 
+// One tile of the z pass on staged data: the forward transforms of the
+// thread's line, the multiply by the Green's spectrum, the inverse
+// transforms and the store of z < Nz.  `sin`: the thread's line group as
+// staged, [z < L/2][IS] (IS = TX, or 2 TX where a box holds two tiles),
+// offset to the tile's first column; `sg`: the spectrum block of the
+// thread's line, [kz'][TX].  `before_g` runs before the spectrum is read and
+// returns false (the same on every thread) to abandon the tile.
+template <typename T, int L, int IS, typename TWR, typename Xch, typename BeforeG>
+__device__ __forceinline__ bool z_tile(const Cx<T> *sin, const T *sg, int pr, int xt, Cx<T> *__restrict__ W,
+                                       const T *__restrict__ Gs, T gscale, int Nz, int My, int Kx, int c, int g,
+                                       int t, const TWR &twr, const Cx<T> *twz, Xch &xch, BeforeG before_g)
+{
+    using C = ZCfg<T, L>;
+    using Rad = typename ZShape<T, L>::Rad;
+    constexpr int E = C::E, NT = C::NT, TX = C::TX, COLS = C::COLS, Lh = L / 2;
+    const int col = g * TX + c;
+    const int ky = g == 0 ? pr : (pr == 0 ? My / 2 : My - pr);
+    const int kx = xt * TX + c;
+    const bool active = kx < Kx;
+    const int kyp = ky <= My - ky ? ky : My - ky;
+
+    // z < Lh from the staged boxes (zeros past Nz), the upper half is zero
+    sin += t * IS + c;
+    Cx<T> v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = m < E / 2 ? sin[m * NT * IS] : Cx<T>{(T)0, (T)0};
+
+    z_fft<C::TWR, true, T, L, E>(v, t, twr, twz, xch, Rad{});
+    if (!before_g()) return false;
+
+    // spectrum at kz = t + m NT: kz' = kz below Lh, L - kz from Lh on
+    const T *g_lo = sg + t * TX + c;
+    const T *g_hi = sg + (L - t) * TX + c;
+    auto gval = [&](int m) -> T { return m < E / 2 ? g_lo[m * NT * TX] : g_hi[-m * NT * TX]; };
+    const bool packed = xt == 0 && c == 0;  // the kx = 0 / Mx/2 column
+    if (xt == 0) {
+        // the packed column needs the partner bin (-ky, -kz)
+        Cx<T> *sp = xch.free_buf();
+        if (c == 0) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) sp[(t + m * NT) * COLS + col] = v[m];
+        }
+        __syncthreads();
+        if (c == 0) {
+            const int gp = pr == 0 ? g : 1 - g;
+            const T *gsrow = Gs + (size_t)kyp * (Lh + 1);
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int kz = t + m * NT;
+                const int kzp = kz <= L - kz ? kz : L - kz;
+                const Cx<T> partner = cconj(sp[(kz == 0 ? 0 : L - kz) * COLS + gp * TX]);
+                const T gp_ = gval(m) * gscale;
+                const T gm_ = gsrow[kzp] * gscale;
+                v[m] = {v[m].x * gp_ + partner.x * gm_, v[m].y * gp_ + partner.y * gm_};
+            }
+        }
+        __syncthreads();
+    }
+    if (!packed) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = cscale(v[m], gval(m) * gscale);
+    }
+
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = cswap(v[m]);
+    z_fft<C::TWR, false, T, L, E>(v, t, twr, twz, xch, Rad{});
+    if (active) {
+        Cx<T> *base = W + (size_t)ky * Kx + kx;
+        const size_t zstride = (size_t)My * Kx;
+#pragma unroll
+        for (int m = 0; m < E / 2; ++m) {
+            const int z = t + m * NT;
+            if (z < Nz) base[(size_t)z * zstride] = cswap(v[m]);
+        }
+    }
+    return true;
+}
+
 // ---------------------------------------------------------------------
 // K3: z forward, multiply by the Green's spectrum, z inverse.
 // Tiles: (pair p, kx tile xt), tile = p * ntx + xt; pair p holds the lines
@@ -1056,12 +1143,11 @@ k_yx_inverse(Cx<T> *__restrict__ W, In<T> *__restrict__ phi, const Cx<T> *__rest
 // 256 planes of W (tmW: 8-byte elements, dims {Kx EPC, My, Nz}; planes
 // z >= Nz and columns kx >= Kx read as zero) and a bulk copy of the tile's
 // spectrum block (a second one for the pair p = 0, whose line My/2 has its
-// own k_y').  The spectrum set is the tile's parity.  With two input sets
-// (one mbarrier each) the next tile's copies are issued at the top of the
-// tile, into the set the previous tile read; with one (and two exchange
-// buffers) they are issued after the barrier of the tile's first exchange,
-// which every thread reaches after reading its input.  Either way the reads
-// of a set precede a CTA barrier that precedes its refill.
+// own k_y').  The input has one staging set, the spectrum two (the tile's
+// parity); both complete on one mbarrier, once per tile.  The next tile's
+// copies are issued after the barrier of the tile's first exchange, which
+// every thread reaches after reading its input; the other spectrum set was
+// last read by the previous tile, before the barriers of its transforms.
 // ---------------------------------------------------------------------
 template <typename T, int L>
 __global__ void __launch_bounds__(ZCfg<T, L>::THREADS, ZCfg<T, L>::MIN_BLOCKS)
@@ -1070,13 +1156,14 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
              unsigned *__restrict__ status, unsigned test_extra_tx)
 {
     using C = ZCfg<T, L>;
-    constexpr int E = C::E, NT = C::NT, TX = C::TX, COLS = C::COLS;
+    static_assert(C::DBX, "lines without room for two exchange buffers take k_z_convolve_pairs");
+    constexpr int E = C::E, TX = C::TX, COLS = C::COLS;
     constexpr int Lh = L / 2;
     extern __shared__ __align__(128) unsigned char zsmem[];
-    Cx<T> *sm = reinterpret_cast<Cx<T> *>(zsmem);             // exchange buffer(s)
-    unsigned char *s_in = zsmem + C::OFF_IN;                   // [set][g][z < Lh][TX]
+    Cx<T> *sm = reinterpret_cast<Cx<T> *>(zsmem);             // two exchange buffers
+    unsigned char *s_in = zsmem + C::OFF_IN;                   // [g][z < Lh][TX]
     T *s_g = reinterpret_cast<T *>(zsmem + C::OFF_G);          // [set][2][GBLK]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(zsmem + C::OFF_BAR);  // one per input set
+    uint64_t *bar = reinterpret_cast<uint64_t *>(zsmem + C::OFF_BAR);
     // thread -> (column c, group g, position t): a warp holds both groups of
     // a few positions, so each position row of the exchange buffer is written
     // whole and the warp's shared-memory accesses are conflict-free
@@ -1086,7 +1173,6 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
     const int t = tid / COLS;
     const int col = g * TX + c;
     const int ntx = (Kx + TX - 1) / TX;
-    const size_t zstride = (size_t)My * Kx;
     const ZSpecLayout lay{TX, ntx, Lh + 1, C::GBLK};
 
     // tensor copies need 128-byte aligned destinations (uniform per CTA)
@@ -1095,7 +1181,7 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
         return;
     }
     if (tid == 0) {
-        for (int i = 0; i < C::NIN; ++i) mbar_init(&bar[i], 1);
+        mbar_init(&bar[0], 1);
         mbar_init_fence();
     }
     const Cx<T> *twz = tw;  // the twiddle table the stages read
@@ -1106,29 +1192,25 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
     }
     __syncthreads();
 
-    // copies of a tile into spectrum set `set` (and input set `set` when
-    // there are two), issued by thread 0
+    // copies of a tile into the input set and spectrum set `set`, issued by
+    // thread 0
     auto issue = [&](int tile, int set, uint32_t extra) {
         const int pr = tile / ntx, xt = tile - pr * ntx;
         const int ky1 = pr == 0 ? My / 2 : My - pr;
-        const int is = C::DBX ? 0 : set;
-        uint64_t *b = &bar[is];
-        mbar_arrive_expect_tx(b, (uint32_t)(C::IN_SET + (pr == 0 ? 2 : 1) * C::G_BLK) + extra);
-        unsigned char *dst = s_in + is * C::IN_SET;
+        mbar_arrive_expect_tx(&bar[0], (uint32_t)(C::IN_SET + (pr == 0 ? 2 : 1) * C::G_BLK) + extra);
 #pragma unroll
         for (int zb = 0; zb < C::NZB; ++zb) {
             const size_t off = (size_t)zb * C::BOXZ * TX * sizeof(Cx<T>);
-            tma_load_3d(dst + off, &tmW, xt * TX * C::EPC, pr, zb * C::BOXZ, b);
-            tma_load_3d(dst + C::IN_GROUP + off, &tmW, xt * TX * C::EPC, ky1, zb * C::BOXZ, b);
+            tma_load_3d(s_in + off, &tmW, xt * TX * C::EPC, pr, zb * C::BOXZ, &bar[0]);
+            tma_load_3d(s_in + C::IN_GROUP + off, &tmW, xt * TX * C::EPC, ky1, zb * C::BOXZ, &bar[0]);
         }
         T *gdst = s_g + (size_t)set * 2 * C::GBLK;
-        bulk_load(gdst, G + lay.block(pr, xt), (uint32_t)C::G_BLK, b);
-        if (pr == 0) bulk_load(gdst + C::GBLK, G + lay.block(My / 2, xt), (uint32_t)C::G_BLK, b);
+        bulk_load(gdst, G + lay.block(pr, xt), (uint32_t)C::G_BLK, &bar[0]);
+        if (pr == 0) bulk_load(gdst + C::GBLK, G + lay.block(My / 2, xt), (uint32_t)C::G_BLK, &bar[0]);
     };
 
     using Rad = typename ZShape<T, L>::Rad;
-    constexpr bool TWR = C::TWR;
-    typename ZTwiddles<TWR, T, L, E, Rad>::type twr;  // this thread's twiddles, for every tile (when TW_REGS)
+    typename ZTwiddles<C::TWR, T, L, E, Rad>::type twr;  // this thread's twiddles, for every tile (when TW_REGS)
     twr.load(tw, t);
     int tile = blockIdx.x, it = 0;
     bool ok = true;
@@ -1138,93 +1220,149 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
     for (; tile < ntiles; tile += gridDim.x, ++it) {
         const int next = tile + gridDim.x;
         const int set = it & 1;
-        auto next_copies = [&]() {
-            if (tid == 0 && next < ntiles) issue(next, set ^ 1, 0u);
+        auto hook = [&](int k) {
+            if (k == 0 && tid == 0 && next < ntiles) issue(next, set ^ 1, 0u);
         };
-        ZXch<T, L, E, COLS, C::SWZ, C::DBX, decltype(next_copies)> xch{sm, col, next_copies};
-        // two input sets: the next tile's copies go out now, and each set's
-        // barrier completes every other tile; one set: they go out after the
-        // first exchange, and its barrier completes once per tile
-        if constexpr (!C::DBX) next_copies();
-        const bool landed = C::DBX ? mbar_wait_bounded(&bar[0], (uint32_t)it & 1u, kCopyWaitNs)
-                                   : mbar_wait_bounded(&bar[set], (uint32_t)(it >> 1) & 1u, kCopyWaitNs);
-        if (!__syncthreads_and(landed)) {
+        ZXch<T, L, E, COLS, C::SWZ, true, decltype(hook)> xch{sm, col, hook};
+        if (!__syncthreads_and(mbar_wait_bounded(&bar[0], (uint32_t)it & 1u, kCopyWaitNs))) {
             ok = false;
             break;
         }
         const int pr = tile / ntx, xt = tile - pr * ntx;
-        const int ky = g == 0 ? pr : (pr == 0 ? My / 2 : My - pr);
-        const int kx = xt * TX + c;
-        const bool active = kx < Kx;
-        const int kyp = ky <= My - ky ? ky : My - ky;
-
-        // z < Lh from the staged boxes (zeros past Nz), the upper half is zero
-        const Cx<T> *sin = reinterpret_cast<const Cx<T> *>(s_in + (C::DBX ? 0 : set) * C::IN_SET + g * C::IN_GROUP) +
-                           t * TX + c;
-        Cx<T> v[E];
-#pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = m < E / 2 ? sin[m * NT * TX] : Cx<T>{(T)0, (T)0};
-
-        z_fft<TWR, true, T, L, E>(v, t, twr, twz, xch, Rad{});
-
-        // spectrum at kz = t + m NT: kz' = kz below Lh, L - kz from Lh on
+        const Cx<T> *sin = reinterpret_cast<const Cx<T> *>(s_in + g * C::IN_GROUP);
         const T *sg = s_g + ((size_t)set * 2 + (pr == 0 ? g : 0)) * C::GBLK;
-        const T *g_lo = sg + t * TX + c;
-        const T *g_hi = sg + (L - t) * TX + c;
-        auto gval = [&](int m) -> T { return m < E / 2 ? g_lo[m * NT * TX] : g_hi[-m * NT * TX]; };
-        const bool packed = xt == 0 && c == 0;  // the kx = 0 / Mx/2 column
-        if (xt == 0) {
-            // the packed column needs the partner bin (-ky, -kz)
-            Cx<T> *sp = xch.free_buf();
-            if (c == 0) {
-#pragma unroll
-                for (int m = 0; m < E; ++m) sp[(t + m * NT) * COLS + col] = v[m];
-            }
-            __syncthreads();
-            if (c == 0) {
-                const int gp = pr == 0 ? g : 1 - g;
-                const T *gsrow = Gs + (size_t)kyp * (Lh + 1);
-#pragma unroll
-                for (int m = 0; m < E; ++m) {
-                    const int kz = t + m * NT;
-                    const int kzp = kz <= L - kz ? kz : L - kz;
-                    const Cx<T> partner = cconj(sp[(kz == 0 ? 0 : L - kz) * COLS + gp * TX]);
-                    const T gp_ = gval(m) * gscale;
-                    const T gm_ = gsrow[kzp] * gscale;
-                    v[m] = {v[m].x * gp_ + partner.x * gm_, v[m].y * gp_ + partner.y * gm_};
-                }
-            }
-            __syncthreads();
-        }
-        if (!packed) {
-#pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = cscale(v[m], gval(m) * gscale);
-        }
-
-#pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = cswap(v[m]);
-        z_fft<TWR, false, T, L, E>(v, t, twr, twz, xch, Rad{});
-        if (active) {
-            Cx<T> *base = W + (size_t)ky * Kx + kx;
-#pragma unroll
-            for (int m = 0; m < E / 2; ++m) {
-                const int z = t + m * NT;
-                if (z < Nz) base[(size_t)z * zstride] = cswap(v[m]);
-            }
-        }
+        z_tile<T, L, TX>(sin, sg, pr, xt, W, Gs, gscale, Nz, My, Kx, c, g, t, twr, twz, xch, [] { return true; });
     }
     if (!ok && tid == 0) {
-        // a wait gave up: flag it, then let the copies in flight land
-        // (bounded again) before the CTA's shared memory is freed: this
-        // tile's, and with two input sets the next tile's
+        // a wait gave up: flag it, then let this tile's copies land (bounded
+        // again) before the CTA's shared memory is freed
         if (status) atomicOr(status, 1u);
-        if constexpr (C::DBX) {
-            mbar_wait_bounded(&bar[0], (uint32_t)it & 1u, kCopyWaitNs);
-        } else {
-            mbar_wait_bounded(&bar[it & 1], (uint32_t)(it >> 1) & 1u, kCopyWaitNs);
-            if (tile + (int)gridDim.x < ntiles)
-                mbar_wait_bounded(&bar[(it + 1) & 1], (uint32_t)((it + 1) >> 1) & 1u, kCopyWaitNs);
+        mbar_wait_bounded(&bar[0], (uint32_t)it & 1u, kCopyWaitNs);
+    }
+}
+
+// K3 for lines whose tile leaves no room for a second exchange buffer (2304
+// points).  Their tiles are only 16 bytes wide per row, so the CTA takes
+// two adjacent tiles at a time: one box of 2 TX columns (32-byte rows) per
+// line group and 256 planes, and one bulk copy of both tiles' spectrum
+// blocks (adjacent in the cache layout), then computes the tiles in turn on
+// one exchange buffer.  Input and spectrum have one staging set each, on
+// their own mbarrier (one phase per pair).  The next pair's input is issued
+// after the barrier of the second tile's first exchange, its spectrum after
+// the barrier of the second tile's first inverse exchange: by then every
+// thread has read the current pair's input, and its spectrum, respectively.
+// When ntx is odd the last pair of a line pair has one tile.
+template <typename T, int L>
+__global__ void __launch_bounds__(ZCfg<T, L>::THREADS, ZCfg<T, L>::MIN_BLOCKS)
+k_z_convolve_pairs(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw,
+                   const T *__restrict__ G, const T *__restrict__ Gs, T gscale, int Nz, int My, int Kx,
+                   int npairs, unsigned *__restrict__ status, unsigned test_extra_tx)
+{
+    using C = ZCfg<T, L>;
+    static_assert(!C::DBX, "lines with room for two exchange buffers take k_z_convolve");
+    constexpr int E = C::E, TX = C::TX, COLS = C::COLS, PTX = C::PTX;
+    constexpr int Lh = L / 2;
+    using Rad = typename ZShape<T, L>::Rad;
+    constexpr int NXF = RadixCount<Rad>::value - 1;  // exchanges of one transform
+    extern __shared__ __align__(128) unsigned char zsmem[];
+    Cx<T> *sm = reinterpret_cast<Cx<T> *>(zsmem);                 // exchange buffer
+    unsigned char *s_in = zsmem + C::OFF_IN;                       // [g][z < Lh][2 TX]
+    T *s_g = reinterpret_cast<T *>(zsmem + C::OFF_G);              // [line group j][tile s][GBLK]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(zsmem + C::OFF_BAR);  // input, spectrum
+    const int tid = threadIdx.x;
+    const int c = tid % TX;
+    const int g = (tid / TX) & 1;
+    const int t = tid / COLS;
+    const int col = g * TX + c;
+    const int ntx = (Kx + TX - 1) / TX;
+    const int npx = (ntx + 1) / 2;  // tile pairs per line pair
+    const ZSpecLayout lay{TX, ntx, Lh + 1, C::GBLK};
+
+    if (smem_addr(zsmem) & 127u) {
+        if (tid == 0 && status) atomicOr(status, 2u);
+        return;
+    }
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
+    }
+    const Cx<T> *twz = tw;
+    if constexpr (!C::TWR) {
+        Cx<T> *s_tw = reinterpret_cast<Cx<T> *>(zsmem + C::OFF_TW);
+        for (int i = tid; i < L; i += C::THREADS) s_tw[i] = tw[i];
+        twz = s_tw;
+    }
+    __syncthreads();
+
+    // thread 0 issues; n_in / n_g count the phases issued on each barrier
+    int n_in = 0, n_g = 0;
+    auto issue_in = [&](int pair, uint32_t extra) {
+        const int pr = pair / npx, xt0 = 2 * (pair - pr * npx);
+        const int ky1 = pr == 0 ? My / 2 : My - pr;
+        mbar_arrive_expect_tx(&bar[0], (uint32_t)C::PIN_SET + extra);
+#pragma unroll
+        for (int zb = 0; zb < C::NZB; ++zb) {
+            const size_t off = (size_t)zb * C::BOXZ * PTX * sizeof(Cx<T>);
+            tma_load_3d(s_in + off, &tmW, xt0 * TX * C::EPC, pr, zb * C::BOXZ, &bar[0]);
+            tma_load_3d(s_in + C::PIN_GROUP + off, &tmW, xt0 * TX * C::EPC, ky1, zb * C::BOXZ, &bar[0]);
         }
+        ++n_in;
+    };
+    auto issue_g = [&](int pair) {
+        const int pr = pair / npx, xt0 = 2 * (pair - pr * npx);
+        const uint32_t bytes = (uint32_t)((ntx - xt0 < 2 ? 1 : 2) * C::G_BLK);
+        mbar_arrive_expect_tx(&bar[1], (pr == 0 ? 2u : 1u) * bytes);
+        bulk_load(s_g, G + lay.block(pr, xt0), bytes, &bar[1]);
+        if (pr == 0) bulk_load(s_g + 2 * C::GBLK, G + lay.block(My / 2, xt0), bytes, &bar[1]);
+        ++n_g;
+    };
+
+    typename ZTwiddles<C::TWR, T, L, E, Rad>::type twr;
+    twr.load(tw, t);
+    int pair = blockIdx.x, it = 0;
+    bool ok = true, in_done = false;
+    if (tid == 0 && pair < npairs) {
+        issue_in(pair, test_extra_tx);
+        issue_g(pair);
+    }
+    for (; pair < npairs; pair += gridDim.x, ++it) {
+        const int next = pair + gridDim.x;
+        in_done = false;
+        if (!__syncthreads_and(mbar_wait_bounded(&bar[0], (uint32_t)it & 1u, kCopyWaitNs))) {
+            ok = false;
+            break;
+        }
+        in_done = true;
+        const int pr = pair / npx, xt0 = 2 * (pair - pr * npx);
+        const int nsub = ntx - xt0 < 2 ? 1 : 2;
+        for (int s = 0; s < nsub; ++s) {
+            const bool last = s == nsub - 1;
+            auto hook = [&](int k) {
+                if (!last || tid != 0 || next >= npairs) return;
+                if (k == 0) issue_in(next, 0u);
+                if (k == NXF) issue_g(next);
+            };
+            ZXch<T, L, E, COLS, C::SWZ, false, decltype(hook)> xch{sm, col, hook};
+            auto spectrum_landed = [&]() -> bool {
+                return s != 0 || __syncthreads_and(mbar_wait_bounded(&bar[1], (uint32_t)it & 1u, kCopyWaitNs));
+            };
+            const Cx<T> *sin = reinterpret_cast<const Cx<T> *>(s_in + g * C::PIN_GROUP) + s * TX;
+            const T *sg = s_g + ((size_t)(pr == 0 ? g : 0) * 2 + s) * C::GBLK;
+            if (!z_tile<T, L, PTX>(sin, sg, pr, xt0 + s, W, Gs, gscale, Nz, My, Kx, c, g, t, twr, twz, xch,
+                                   spectrum_landed)) {
+                ok = false;
+                break;
+            }
+        }
+        if (!ok) break;
+    }
+    if (!ok && tid == 0) {
+        // a wait gave up: flag it, then let the copies still in flight land
+        // (bounded again): at most one phase per barrier is outstanding
+        if (status) atomicOr(status, 1u);
+        if (n_in > it + (in_done ? 1 : 0)) mbar_wait_bounded(&bar[0], (uint32_t)(n_in - 1) & 1u, kCopyWaitNs);
+        if (n_g > it) mbar_wait_bounded(&bar[1], (uint32_t)(n_g - 1) & 1u, kCopyWaitNs);
     }
 }
 

@@ -324,36 +324,46 @@ template cudaError_t launch_yx_inverse<Real>(int, void *, In<Real> *, const void
 #endif
 
 #if ISOFFT_GROUP == 3
+// The z pass: k_z_convolve on tiles of TX columns, or k_z_convolve_pairs on
+// pairs of adjacent tiles (one box of 2 TX columns) where the line leaves no
+// room for two exchange buffers.
 template <typename T, int L>
 static cudaError_t run_z(void *W, const void *tw, const T *G, const T *Gs, T gscale, int Nz, int My, int Kx,
                          unsigned *status, unsigned test_extra_tx, cudaStream_t st)
 {
     using C = ZCfg<T, L>;
+    constexpr auto kernel = []() {
+        if constexpr (C::DBX)
+            return k_z_convolve<T, L>;
+        else
+            return k_z_convolve_pairs<T, L>;
+    }();
     static std::atomic<uint64_t> done{0};
     static std::atomic<int> slots{0};
     if (((uintptr_t)W & 15) || ((uintptr_t)G & 15)) return cudaErrorMisalignedAddress;
-    cudaError_t e = ensure_smem(k_z_convolve<T, L>, C::SMEM, done);
+    cudaError_t e = ensure_smem(kernel, C::SMEM, done);
     if (e != cudaSuccess) return e;
     const int ntx = (Kx + C::TX - 1) / C::TX;
-    const int ntiles = ntx * (My / 2);
-    int grid = resident_ctas(k_z_convolve<T, L>, C::THREADS, C::SMEM, slots);
+    // work units: tiles, or tile pairs
+    const int units = (C::DBX ? ntx : (ntx + 1) / 2) * (My / 2);
+    int grid = resident_ctas(kernel, C::THREADS, C::SMEM, slots);
     if (grid <= 0) return cudaErrorInvalidConfiguration;
-    if (grid > ntiles) grid = ntiles;
-    // W as 8-byte elements [Nz][My][Kx * EPC]; one box = TX columns of one
-    // line for BOXZ planes
+    if (grid > units) grid = units;
+    // W as 8-byte elements [Nz][My][Kx * EPC]; one box = TX (pairs: 2 TX)
+    // columns of one line for BOXZ planes
     EncodeTiledFn encode = encode_tiled();
     if (!encode) return cudaErrorNotSupported;
     CUtensorMap map;
     const cuuint64_t dims[3] = {(cuuint64_t)Kx * C::EPC, (cuuint64_t)My, (cuuint64_t)Nz};
     const cuuint64_t strides[2] = {(cuuint64_t)Kx * sizeof(Cx<T>), (cuuint64_t)My * Kx * sizeof(Cx<T>)};
-    const cuuint32_t box[3] = {(cuuint32_t)(C::TX * C::EPC), 1u, (cuuint32_t)C::BOXZ};
+    const cuuint32_t box[3] = {(cuuint32_t)((C::DBX ? C::TX : C::PTX) * C::EPC), 1u, (cuuint32_t)C::BOXZ};
     const cuuint32_t estr[3] = {1u, 1u, 1u};
     if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, W, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
-    k_z_convolve<T, L><<<grid, C::THREADS, C::SMEM, st>>>(map, (Cx<T> *)W, (const Cx<T> *)tw, G, Gs, gscale, Nz,
-                                                         My, Kx, ntiles, status, test_extra_tx);
+    kernel<<<grid, C::THREADS, C::SMEM, st>>>(map, (Cx<T> *)W, (const Cx<T> *)tw, G, Gs, gscale, Nz, My, Kx, units,
+                                             status, test_extra_tx);
     count_launch();
     return cudaGetLastError();
 }

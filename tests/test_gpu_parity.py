@@ -199,6 +199,7 @@ LONG_SHAPES = [
     ((1000, 9, 8), (1.0, 1.0, 1.0)),     # Mx = 2304 (rows of 1152)
     ((9, 1100, 8), (1.0, 2.0, 1.0)),     # My = 2304
     ((8, 9, 1152), (1.0, 1.0, 0.5)),     # Mz = 2304, the largest N
+    ((60, 30, 1100), (1.0, 1.0, 1.0)),   # Mz = 2304, several tile pairs per CTA
     ((5, 3, 2), (1.0, 1.0, 1.0)),        # every axis padded up to 32
 ]
 
@@ -400,14 +401,16 @@ def test_tuned_forms_are_written_to_the_tune_file(tmp_path, monkeypatch):
     assert len(rows) == 1 and rows[0][6:] == [fwd, inv]
 
 
-def test_bounded_wait_runout_reports_timeout_and_the_gpu_stays_usable():
+@pytest.mark.parametrize("N", [(64, 64, 64), (8, 9, 1152)])
+def test_bounded_wait_runout_reports_timeout_and_the_gpu_stays_usable(N):
     """The z pass's copy waits are bounded: with the run-out test hook the
-    first tile of every CTA expects more bytes than its copies deliver, the
-    wait gives up after its time limit, the pass lets its copies land and
-    returns, and ipf_plan_check reports IPF_TIMEOUT once.  Solves afterwards,
-    on another plan, match the oracle."""
+    first tile (or tile pair, on the 2304-point lines of the second mesh) of
+    every CTA expects more bytes than its copies deliver, the wait gives up
+    after its time limit, the pass lets its copies land and returns, and
+    ipf_plan_check reports IPF_TIMEOUT once.  Solves afterwards, on another
+    plan, match the oracle."""
     from paper_1106_0557_gb300 import Plan
-    N, h = (64, 64, 64), (1.0, 1.0, 1.0)
+    h = (1.0, 1.0, 1.0)
     src = rand_src(N, 9)
     d = torch.from_numpy(src.astype(np.float32)).cuda()
     with Plan(N, h, "f32", flags=native.IPF_FLAG_TEST_WAIT_RUNOUT) as p:
