@@ -703,10 +703,13 @@ struct YCfg {
     static constexpr int NT = L / E;
     static constexpr int CB = (int)sizeof(Cx<T>);
     static constexpr size_t smem_i(int tx) { return (size_t)3 * L * tx * CB + 16; }
+    // the column tile's width, halved while its exchange buffer and two
+    // input sets exceed shared memory (which keeps the 2304-point lines at
+    // 32-byte rows: 221 KB)
     static constexpr int width()
     {
         int tx = ColCfg<T, L>::TX;
-        while (tx > 1 && smem_i(tx) > 200 * 1024) tx /= 2;
+        while (tx > 1 && smem_i(tx) > 226 * 1024) tx /= 2;
         return tx;
     }
     static constexpr int TX = width();

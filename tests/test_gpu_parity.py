@@ -365,7 +365,7 @@ def test_async_host_solves_in_flight_together(dtype):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f64", "df64"])
-@pytest.mark.parametrize("N", [(64, 64, 64), (37, 200, 13), (256, 256, 40), (20, 300, 17), (9, 700, 8)])
+@pytest.mark.parametrize("N", [(64, 64, 64), (37, 200, 13), (256, 256, 40), (20, 300, 17), (9, 700, 8), (9, 1100, 8)])
 def test_y_pass_forms_are_bitwise_equal(N, dtype):
     """The tile and streamed forms of the y passes run the same arithmetic in
     the same order: forcing either gives bitwise the same potential, and a
