@@ -159,9 +159,9 @@ struct RowXch {
     }
 };
 
-template <typename T, int L>
+template <typename T, int L, typename SH = XShape<T, L>>
 struct RowCfg {
-    static constexpr int E = XShape<T, L>::E;
+    static constexpr int E = SH::E;
     static constexpr int NT = L / E;
     static constexpr int NL = NT >= 256 ? 1 : 256 / NT;  // rows per CTA
     static constexpr int THREADS = NL * NT;
@@ -169,10 +169,10 @@ struct RowCfg {
     // Stage twiddles held in registers across the rows of a persistent CTA
     // (K1: TWR_F, K5: TWR_I) where that measured faster than reading the
     // table in every stage: FP32 forward rows of 192 and 384 points, inverse
-    // rows of 128 and 384.  Elsewhere the extra registers cost more
-    // occupancy than the table reads do.
+    // rows of 128, 384, 768 and 1152.  Elsewhere the extra registers cost
+    // more occupancy than the table reads do.
     static constexpr bool TWR_F = sizeof(T) == 4 && (L == 192 || L == 384);
-    static constexpr bool TWR_I = sizeof(T) == 4 && (L == 128 || L == 384);
+    static constexpr bool TWR_I = sizeof(T) == 4 && (L == 128 || L == 384 || L == 768 || L == 1152);
 };
 
 // Column tiles of the y passes: up to 128 bytes of complex per row and at
@@ -372,16 +372,17 @@ __device__ __forceinline__ void z_fft(Cx<T> (&v)[E], int t, const TW &twr, const
     else
         run_stages<T, L, E, HALF>(v, t, tw, xch, Rad{});
 }
-template <bool TWR, typename T, int L>
-using RowTwiddles = typename ZTwiddles<TWR, T, L, XShape<T, L>::E, typename XShape<T, L>::Rad>::type;
+template <bool TWR, typename T, int L, typename SH = XShape<T, L>>
+using RowTwiddles = typename ZTwiddles<TWR, T, L, SH::E, typename SH::Rad>::type;
 
-template <typename T, int L, bool TWR = false>
+// K1 body: real row -> packed half spectrum (row shape SH).
+template <typename T, int L, bool TWR = false, typename SH = XShape<T, L>>
 __device__ __forceinline__ void x_forward_row_at(const In<T> *in, Cx<T> *__restrict__ out,
                                                  const Cx<T> *__restrict__ tw, const Cx<T> *__restrict__ rtw, int Nx,
                                                  bool active, Cx<T> *line, int t,
-                                                 const RowTwiddles<TWR, T, L> &twr = {})
+                                                 const RowTwiddles<TWR, T, L, SH> &twr = {})
 {
-    constexpr int E = XShape<T, L>::E, NT = L / E;
+    constexpr int E = SH::E, NT = L / E;
     using IO = IoReal<T>;
 
     // pairs (x[2p], x[2p+1]) as one complex point; p >= L/2 is padding
@@ -402,7 +403,7 @@ __device__ __forceinline__ void x_forward_row_at(const In<T> *in, Cx<T> *__restr
         }
     }
     RowXch<T, L, E> xch{line};
-    z_fft<TWR, true, T, L, E>(v, t, twr, tw, xch, typename XShape<T, L>::Rad{});
+    z_fft<TWR, true, T, L, E>(v, t, twr, tw, xch, typename SH::Rad{});
 
     // split the half-length transform Z into the real row's spectrum:
     //   2X[k] = (Z[k] + conj Z[L-k]) + W_2L^k (-i)(Z[k] - conj Z[L-k]),
@@ -433,15 +434,16 @@ __device__ __forceinline__ void x_forward_row_at(const In<T> *in, Cx<T> *__restr
     }
 }
 
-template <typename T, int L, bool TWR = false>
+template <typename T, int L, bool TWR = false, typename SH = XShape<T, L>>
 __device__ __forceinline__ void x_forward_row(const In<T> *__restrict__ src, Cx<T> *__restrict__ W,
                                               const Cx<T> *__restrict__ tw, const Cx<T> *__restrict__ rtw, int Nx,
                                               int Ny, int My, int64_t rr, bool active, Cx<T> *line, int t,
-                                              const RowTwiddles<TWR, T, L> &twr = {})
+                                              const RowTwiddles<TWR, T, L, SH> &twr = {})
 {
     const int y = (int)(rr % Ny);
     const int64_t z = rr / Ny;
-    x_forward_row_at<T, L, TWR>(src + rr * Nx, W + ((size_t)z * My + y) * L, tw, rtw, Nx, active, line, t, twr);
+    x_forward_row_at<T, L, TWR, SH>(src + rr * Nx, W + ((size_t)z * My + y) * L, tw, rtw, Nx, active, line, t,
+                                    twr);
 }
 
 // K5 body: packed half spectrum of row rr -> real row, cropped to x < Nx.
@@ -577,21 +579,22 @@ __device__ __forceinline__ void y_inverse_tile(Cx<T> *__restrict__ W, const Cx<T
 // every CTA takes one group.
 // ---------------------------------------------------------------------
 template <typename T, int L>
-__global__ void __launch_bounds__(RowCfg<T, L>::THREADS)
+__global__ void __launch_bounds__(RowCfg<T, L, XShapeF<T, L>>::THREADS)
 k_x_forward(const In<T> *__restrict__ src, Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw,
             const Cx<T> *__restrict__ rtw, int Nx, int Ny, int My, int64_t nrows)
 {
-    using C = RowCfg<T, L>;
+    using SH = XShapeF<T, L>;
+    using C = RowCfg<T, L, SH>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int t = threadIdx.x % C::NT, l = threadIdx.x / C::NT;
     Cx<T> *line = reinterpret_cast<Cx<T> *>(smem_raw) + l * RowPad<T, L>::LP;
     if constexpr (C::TWR_F) {
-        RowTwiddles<true, T, L> twr;
+        RowTwiddles<true, T, L, SH> twr;
         twr.load(tw, t);
         for (int64_t r0 = (int64_t)blockIdx.x * C::NL; r0 < nrows; r0 += (int64_t)gridDim.x * C::NL) {
             const int64_t row = r0 + l;  // row = z * Ny + y
             const bool active = row < nrows;
-            x_forward_row<T, L, true>(src, W, tw, rtw, Nx, Ny, My, active ? row : 0, active, line, t, twr);
+            x_forward_row<T, L, true, SH>(src, W, tw, rtw, Nx, Ny, My, active ? row : 0, active, line, t, twr);
             // rows wider than a warp read their mirror points from `line`
             // last: the next row's first exchange must wait for those reads
             if constexpr (!(C::NT <= 32 && 32 % C::NT == 0)) {
@@ -601,7 +604,7 @@ k_x_forward(const In<T> *__restrict__ src, Cx<T> *__restrict__ W, const Cx<T> *_
     } else {
         const int64_t row = (int64_t)blockIdx.x * C::NL + l;
         const bool active = row < nrows;
-        x_forward_row<T, L>(src, W, tw, rtw, Nx, Ny, My, active ? row : 0, active, line, t);
+        x_forward_row<T, L, false, SH>(src, W, tw, rtw, Nx, Ny, My, active ? row : 0, active, line, t);
     }
 }
 

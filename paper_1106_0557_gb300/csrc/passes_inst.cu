@@ -93,7 +93,7 @@ template <typename T, int L>
 static cudaError_t run_x_forward(const In<T> *src, void *W, const void *tw, const void *rtw, int Nx, int Ny,
                                  int My, int64_t nrows, cudaStream_t st)
 {
-    using C = RowCfg<T, L>;
+    using C = RowCfg<T, L, XShapeF<T, L>>;
     static std::atomic<uint64_t> done{0};
     static std::atomic<int> resident{0};
     cudaError_t e = ensure_smem(k_x_forward<T, L>, C::SMEM, done);
