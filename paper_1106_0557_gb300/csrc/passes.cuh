@@ -207,9 +207,9 @@ struct ColCfg {
 constexpr size_t z_smem(int tx, int L, int rb)
 {
     return (size_t)L * 2 * tx * 2 * rb                                  // exchange buffer
-           + 2 * (size_t)2 * (L / 2) * tx * 2 * rb                      // input, two slot sets
+           + 2 * (size_t)2 * (L / 2) * tx * 2 * rb                      // input, two sets
            + 2 * 2 * (size_t)z_spec_block(tx, L / 2 + 1, rb) * rb  // spectrum blocks, two sets
-           + 16;                                                      // the sets' mbarriers
+           + 16;                                                      // mbarriers
 }
 constexpr int z_tile_width(int rb, int nt, int L, int e)
 {
@@ -255,11 +255,12 @@ struct ZCfg {
     // instead of two; the input is then staged once per tile (the next
     // tile's copies start after the first exchange's barrier, when every
     // thread has read its input).  Taken wherever the extra buffer fits the
-    // CTAs per SM (every length but 2304); otherwise two input sets.
+    // CTAs per SM (k_z_convolve; every length but 2304).  Otherwise one
+    // exchange buffer and an input set twice as wide (k_z_convolve_pairs).
     static constexpr size_t SMEM_DBX = 2 * XCH + IN_SET + 2 * G_SET + 16 + TWS;
     static constexpr bool DBX = SMEM_DBX <= 227 * 1024 && MIN_BLOCKS * (SMEM_DBX + 1024) <= 228 * 1024;
     static constexpr int NXB = DBX ? 2 : 1;  // exchange buffers
-    static constexpr int NIN = DBX ? 1 : 2;  // input sets
+    static constexpr int NIN = DBX ? 1 : 2;  // input sets of one tile's width
     static constexpr size_t OFF_IN = NXB * XCH, OFF_G = OFF_IN + NIN * IN_SET, OFF_BAR = OFF_G + 2 * G_SET,
                             OFF_TW = OFF_BAR + 16;
     static constexpr size_t SMEM = OFF_TW + TWS;
