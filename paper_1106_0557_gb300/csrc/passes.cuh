@@ -31,7 +31,9 @@
 //
 // K3 and the streamed form of K2/K4 are persistent and receive their tiles
 // through the tensor memory accelerator (tma.cuh); K1, K5 and the tile form
-// of K2/K4 load with plain coalesced accesses, many CTAs per SM.
+// of K2/K4 load with plain coalesced accesses, many CTAs per SM (K1 and K5
+// run a persistent grid on the lengths that keep their twiddles in
+// registers).
 #pragma once
 #include "fft_engine.cuh"
 #include "launch.h"
