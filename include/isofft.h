@@ -149,13 +149,12 @@ int ipf_solve_host(ipf_plan_t plan, const void *h_src, void *h_phi, void *stream
  *                 unread until ipf_plan_host_wait.
  *   stream        the passes run on it, after the work already enqueued there;
  *                 the copies run on two streams of the plan.
- * The source is copied in z-plane chunks into one of three device staging
- * buffers of the plan (allocated on the first host solve), the x and y passes
- * of each chunk start as it lands, and each chunk's potential is copied back
- * as soon as its inverse passes finish.  Consecutive host solves on a plan
- * take the buffers in turn, so one solve's copies overlap the passes of the
- * solves before and after it.  The copy of h_src does not wait for earlier
- * work on `stream`. */
+ * The source is copied whole into one of three device staging buffers of the
+ * plan (allocated on the first host solve), the passes start when it lands,
+ * and the potential is copied back when they finish.  Consecutive host
+ * solves on a plan take the buffers in turn, so one solve's copies overlap
+ * the passes of the solves before and after it.  The copy of h_src does not
+ * wait for earlier work on `stream`. */
 int ipf_solve_host_async(ipf_plan_t plan, const void *h_src, void *h_phi, void *stream);
 
 /* Wait until every host solve enqueued on the plan has written its potential

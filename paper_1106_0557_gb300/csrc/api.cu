@@ -122,7 +122,7 @@ struct ipf_plan_s {
     // solve's copies overlap its neighbours' passes (with three sets a
     // solve's upload waits only on the download of the solve two before it);
     // per-chunk events
-    static constexpr int kChunks = 8, kAsyncChunks = 2, kSets = 3;
+    static constexpr int kChunks = 8, kAsyncChunks = 1, kSets = 3;
     void *stage[kSets] = {};
     int stage_set = 0;
     cudaStream_t h2d_st = nullptr, d2h_st = nullptr;

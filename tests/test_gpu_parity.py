@@ -347,8 +347,8 @@ def test_host_buffer_solve_equals_device_solve(N, dtype):
 
 @pytest.mark.parametrize("dtype", ["f32", "df64"])
 def test_async_host_solves_in_flight_together(dtype):
-    """Several host solves enqueued back to back on one plan (they alternate
-    between its two staging buffers, and each one's copies overlap its
+    """Several host solves enqueued back to back on one plan (they take its
+    three staging buffers in turn, and each one's copies overlap its
     neighbours' passes) each return the potential of their own source,
     bitwise the device solve's."""
     from paper_1106_0557_gb300 import Plan
