@@ -701,7 +701,8 @@ struct ZXch {
 // dims {Kx EPC, Ny, Nz}, so rows y >= Ny arrive as zeros; K4: {Kx EPC, My,
 // Nz}) into the other of two staging sets while the CTA transforms the
 // current tile; completion and bounded waits as in the z pass.  Twiddles
-// stay in registers across tiles.
+// stay in registers across tiles (lines up to 1024 points), and the
+// exchanges alternate between two buffers where both fit (ZXch).
 // ---------------------------------------------------------------------
 template <typename T, int L>
 struct YCfg {
