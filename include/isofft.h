@@ -79,14 +79,27 @@ enum {
                                        (neither flag: the plan times both forms
                                        and keeps the faster, see
                                        ipf_plan_variants) */
-    IPF_FLAG_TEST_WAIT_RUNOUT = 1u << 3 /* test hook: the z pass's first tile
+    IPF_FLAG_TEST_WAIT_RUNOUT = 1u << 3, /* test hook: the z pass's first tile
                                        on each CTA expects 16 bytes more than
                                        its copies deliver, so its bounded wait
                                        runs out (about 4 s) and the solve
                                        reports IPF_TIMEOUT through
                                        ipf_plan_check; its potential is then
                                        unspecified */
+    IPF_FLAG_TEST_CANARY = 1u << 4  /* test hook: before every solve the
+                                       plan's workspace is filled with NaN
+                                       bytes, so a pass that read an element
+                                       no earlier pass of that solve wrote
+                                       would show in the potential */
 };
+/* Two more test hooks are read from the environment:
+ *   ISOFFT_TEST_FAIL_ALLOC=workspace|tables|spectrum|staging  the device
+ *       allocation of that buffer fails as if the device were out of memory
+ *       (ipf_plan_create, or the first host-buffer solve for staging, then
+ *       returns IPF_OUT_OF_MEMORY and frees what it had allocated);
+ *   ISOFFT_NVTX=1  (read at plan creation) the plan's solves push one NVTX
+ *       range per pass around its launches ("isofft K1 x forward", ...), so
+ *       a profiler can select the kernels of one pass. */
 
 /* Create a solver for an Nx x Ny x Nz mesh of widths h (paper Sec. 3.2,
  * `Create(PoissonSolver, CellWidth, nTotalCells, ...)`).

@@ -19,6 +19,8 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/isofft.h"
 #include "launch.h"
 
@@ -39,6 +41,32 @@ static int cuda_status(cudaError_t e)
     }
     return IPF_CUDA_ERROR;
 }
+
+// Device allocation of a plan's buffers.  The test hook
+// ISOFFT_TEST_FAIL_ALLOC names one kind ("workspace", "tables", "spectrum",
+// "staging") whose allocation then fails as if the device were out of memory.
+static cudaError_t dev_alloc(void **ptr, size_t bytes, const char *kind)
+{
+    const char *f = getenv("ISOFFT_TEST_FAIL_ALLOC");
+    if (f && strcmp(f, kind) == 0) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(ptr, bytes);
+}
+
+// NVTX range around one pass's launches (plans created with ISOFFT_NVTX=1)
+struct PassRange {
+    bool on;
+    PassRange(bool enabled, const char *name) : on(enabled)
+    {
+        if (on) nvtxRangePushA(name);
+    }
+    ~PassRange()
+    {
+        if (on) nvtxRangePop();
+    }
+};
 
 static void logf(int level, int verbosity, const char *fmt, ...)
 {
@@ -114,6 +142,7 @@ struct ipf_plan_s {
     double gscale;
     void *W = nullptr;
     size_t W_bytes = 0;
+    bool nvtx = false;  // NVTX range per pass (ISOFFT_NVTX=1 at creation)
     void *tables = nullptr;  // tw_x | rtw | tw_y | tw_z
     const void *tw_x = nullptr, *rtw = nullptr, *tw_y = nullptr, *tw_z = nullptr;
     unsigned *status = nullptr;  // device word after the tables: bit 0 = a bounded wait gave up
@@ -205,7 +234,7 @@ int upload_tables(ipf_plan_s *p, cudaStream_t st)
     fill_roots<T>(h, oy, My, My);
     fill_roots<T>(h, oz, Mz, Mz);
     const size_t tbytes = (tot * sizeof(T) + 15) / 16 * 16;
-    cudaError_t e = cudaMalloc(&p->tables, tbytes + 16);
+    cudaError_t e = dev_alloc(&p->tables, tbytes + 16, "tables");
     if (e != cudaSuccess) return cuda_status(e);
     p->status = (unsigned *)((char *)p->tables + tbytes);
     e = cudaMemcpyAsync(p->tables, h.data(), tot * sizeof(T), cudaMemcpyHostToDevice, st);
@@ -377,7 +406,7 @@ int acquire_spectrum(ipf_plan_s *p, cudaStream_t st)
     if (it == g_cache.end()) {
         SpecEntry e;
         e.bytes = spectrum_bytes(p->M, p->dtype);
-        cudaError_t ce = cudaMalloc(&e.G, e.bytes);
+        cudaError_t ce = dev_alloc(&e.G, e.bytes, "spectrum");
         if (ce != cudaSuccess) return cuda_status(ce);
         const size_t es = elem_size(p->dtype);
         const size_t Y = p->M[1] / 2 + 1, Z = p->M[2] / 2 + 1;
@@ -448,9 +477,15 @@ cudaError_t enqueue_solve(ipf_plan_s *p, const void *src, void *phi, cudaStream_
         ev = p->ev[p->solves % ipf_plan_s::kSlots];
         p->solves += 1;
     }
+    // test hook: NaN bytes in every workspace element before the passes
+    if (p->flags & IPF_FLAG_TEST_CANARY) {
+        e = cudaMemsetAsync(p->W, 0xff, p->W_bytes, st);
+        if (e != cudaSuccess) return e;
+    }
     if (ev_on) cudaEventRecord(ev[0], st);
     bool fused = false;
     if (p->fuse_xy) {
+        PassRange r(p->nvtx, "isofft K1+K2 xy forward");
         e = launch_xy_forward<T>(Lx, (const IoT *)src, p->W, p->tw_x, p->rtw, p->tw_y, Nx, Ny, Nz, st);
         if (e == cudaSuccess) {
             fused = true;
@@ -460,20 +495,26 @@ cudaError_t enqueue_solve(ipf_plan_s *p, const void *src, void *phi, cudaStream_
         }
     }
     if (!fused) {
+        PassRange r(p->nvtx, "isofft K1 x forward");
         e = launch_x_forward<T>(Lx, (const IoT *)src, p->W, p->tw_x, p->rtw, Nx, Ny, My, nrows, st);
         if (e != cudaSuccess) return e;
     }
     if (ev_on) cudaEventRecord(ev[1], st);
     if (!fused) {
+        PassRange r(p->nvtx, "isofft K2 y forward");
         e = launch_y_forward<T>(My, p->W, p->tw_y, Ny, Lx, Nz, p->status, p->yvar[0], st);
         if (e != cudaSuccess) return e;
     }
     if (ev_on) cudaEventRecord(ev[2], st);
-    e = launch_z_convolve<T>(Mz, p->W, p->tw_z, (const T *)p->spec->G, (const T *)p->spec->Gs,
-                             (T)p->gscale, Nz, My, Lx, p->status, runout_bytes(p), st);
-    if (e != cudaSuccess) return e;
+    {
+        PassRange r(p->nvtx, "isofft K3 z convolve");
+        e = launch_z_convolve<T>(Mz, p->W, p->tw_z, (const T *)p->spec->G, (const T *)p->spec->Gs,
+                                 (T)p->gscale, Nz, My, Lx, p->status, runout_bytes(p), st);
+        if (e != cudaSuccess) return e;
+    }
     if (ev_on) cudaEventRecord(ev[3], st);
     if (fused) {
+        PassRange r(p->nvtx, "isofft K4+K5 yx inverse");
         e = launch_yx_inverse<T>(Lx, p->W, (IoT *)phi, p->tw_x, p->rtw, p->tw_y, Nx, Ny, Nz, st);
         if (e != cudaSuccess) {
             cudaGetLastError();  // refused: finish this solve, and later ones, with the separate passes
@@ -482,11 +523,13 @@ cudaError_t enqueue_solve(ipf_plan_s *p, const void *src, void *phi, cudaStream_
         }
     }
     if (!fused) {
+        PassRange r(p->nvtx, "isofft K4 y inverse");
         e = launch_y_inverse<T>(My, p->W, p->tw_y, Ny, Lx, Nz, p->status, p->yvar[1], st);
         if (e != cudaSuccess) return e;
     }
     if (ev_on) cudaEventRecord(ev[4], st);
     if (!fused) {
+        PassRange r(p->nvtx, "isofft K5 x inverse");
         e = launch_x_inverse<T>(Lx, p->W, (IoT *)phi, p->tw_x, p->rtw, Nx, Ny, My, nrows, st);
         if (e != cudaSuccess) return e;
     }
@@ -526,6 +569,8 @@ cudaError_t enqueue_solve_host(ipf_plan_s *p, const void *h_src, void *h_phi, in
     const size_t cs = 2 * sizeof(T);  // bytes of one workspace complex
     // the set's previous potential has left before its staging is refilled
     cudaError_t e = cudaStreamWaitEvent(p->h2d_st, p->ev_free[s], 0);
+    // test hook: NaN bytes in every workspace element before the passes
+    if (e == cudaSuccess && (p->flags & IPF_FLAG_TEST_CANARY)) e = cudaMemsetAsync(p->W, 0xff, p->W_bytes, st);
     for (int k = 0; k < chunks && e == cudaSuccess; ++k) {
         const int z0 = k * per, nz = z0 + per <= Nz ? per : Nz - z0;
         if (nz <= 0) break;
@@ -567,7 +612,7 @@ int host_solve_setup(ipf_plan_s *p)
     cudaError_t e = cudaSuccess;
     for (int s = 0; s < ipf_plan_s::kSets && e == cudaSuccess; ++s)
         if (!p->stage[s]) {
-            e = cudaMalloc(&p->stage[s], bytes);
+            e = dev_alloc(&p->stage[s], bytes, "staging");
             if (e != cudaSuccess) p->stage[s] = nullptr;
         }
     if (e == cudaSuccess && !p->h2d_st) {
@@ -643,7 +688,8 @@ int ipf_plan_create(ipf_plan_t *out, const int64_t n[3], const double h[3], int 
     *out = nullptr;
     int rc = validate(n, h, dtype);
     if (rc) return rc;
-    if (flags & ~(uint32_t)(IPF_FLAG_PASS_EVENTS | IPF_FLAG_Y_TILES | IPF_FLAG_Y_STREAM | IPF_FLAG_TEST_WAIT_RUNOUT))
+    if (flags & ~(uint32_t)(IPF_FLAG_PASS_EVENTS | IPF_FLAG_Y_TILES | IPF_FLAG_Y_STREAM | IPF_FLAG_TEST_WAIT_RUNOUT |
+                            IPF_FLAG_TEST_CANARY))
         return IPF_INVALID_ARG;
     if ((flags & IPF_FLAG_Y_TILES) && (flags & IPF_FLAG_Y_STREAM)) return IPF_INVALID_ARG;
     if (verbosity < IPF_CONSOLE_ERROR || verbosity > IPF_CONSOLE_INFO_2) return IPF_INVALID_ARG;
@@ -669,6 +715,10 @@ int ipf_plan_create(ipf_plan_t *out, const int64_t n[3], const double h[3], int 
     }
     p->verbosity = verbosity;
     p->spec = nullptr;
+    {
+        const char *nv = getenv("ISOFFT_NVTX");
+        p->nvtx = nv && nv[0] == '1';
+    }
     cudaError_t ce = cudaGetDevice(&p->device);
     if (ce != cudaSuccess) {
         delete p;
@@ -682,7 +732,7 @@ int ipf_plan_create(ipf_plan_t *out, const int64_t n[3], const double h[3], int 
     for (int a = 0; a < 3; ++a) p->key.M[a] = p->M[a];
 
     p->W_bytes = 2 * elem_size(dtype) * (size_t)p->N[2] * (size_t)p->M[1] * (size_t)(p->M[0] / 2);
-    ce = cudaMalloc(&p->W, p->W_bytes);
+    ce = dev_alloc(&p->W, p->W_bytes, "workspace");
     if (ce != cudaSuccess) {
         rc = cuda_status(ce);
         ipf_plan_destroy(p);

@@ -34,6 +34,7 @@ IPF_FLAG_PASS_EVENTS = 1
 IPF_FLAG_Y_TILES = 2
 IPF_FLAG_Y_STREAM = 4
 IPF_FLAG_TEST_WAIT_RUNOUT = 8
+IPF_FLAG_TEST_CANARY = 16
 
 DTYPES = {"f32": IPF_F32, "f64": IPF_F64, "df64": IPF_DF64, IPF_F32: IPF_F32, IPF_F64: IPF_F64,
           IPF_DF64: IPF_DF64}
