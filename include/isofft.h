@@ -251,7 +251,12 @@ int ipf_plan_variants(const ipf_plan_t plan, int v[2]);
 
 /* Bytes held by the library's cache of Green's spectra, and a trim of
  * unreferenced entries (least recently used first) until the cache holds
- * at most `budget` bytes. */
+ * at most `budget` bytes.  With the environment variable ISOFFT_SPECTRUM_DIR
+ * naming a directory, every spectrum the cache builds is also written there
+ * (one file per mesh, width ratios and dtype, with a checksum), and a plan
+ * whose spectrum is not in memory reads a matching file instead of
+ * rebuilding it: the restart of a job skips the spectrum build, the
+ * solver's only state.  Files that do not match are ignored. */
 int ipf_greens_cache_bytes(size_t *bytes);
 int ipf_greens_cache_trim(size_t budget);
 

@@ -8,6 +8,7 @@
 // it, scaled by min(h)^2 (the Green's function of Eq. 6 scales as h^2).
 #include <math.h>
 #include <stdarg.h>
+#include <unistd.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -399,6 +400,117 @@ int tune_y(ipf_plan_s *p, cudaStream_t st)
     return IPF_OK;
 }
 
+// ---------------------------------------------------------------------------
+// On-disk copies of the Green's spectrum (ISOFFT_SPECTRUM_DIR): the only
+// state of a solver, kept so that a restarted job skips K0.  One file per
+// cache key: a header naming the key, the layout (the z tile width the
+// spectrum is tiled for) and an FNV-1a checksum of the payload, then the
+// device buffer's bytes.  A file whose header or checksum does not match is
+// ignored (and replaced after the rebuild).
+// ---------------------------------------------------------------------------
+struct SpecFileHeader {
+    char magic[8];
+    uint32_t version;
+    int32_t dtype;
+    int64_t M[3];
+    double hn[3];
+    int32_t tile;
+    int32_t pad;
+    uint64_t bytes;
+    uint64_t checksum;
+};
+
+static const char kSpecMagic[8] = {'I', 'S', 'O', 'F', 'F', 'T', 'G', 'S'};
+
+static uint64_t fnv1a(const unsigned char *d, size_t n)
+{
+    uint64_t h = 1469598103934665603ull;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= d[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+static int spectrum_tile(const SpecKey &k)
+{
+    const int mz = (int)k.M[2];
+    return k.dtype == IPF_F32 ? z_tile_for<float>(mz) : (k.dtype == IPF_F64 ? z_tile_for<double>(mz) : z_tile_for<df64>(mz));
+}
+
+static bool spectrum_path(const SpecKey &k, char *path, size_t n)
+{
+    const char *dir = getenv("ISOFFT_SPECTRUM_DIR");
+    if (!dir || !dir[0]) return false;
+    uint64_t hb[3];
+    memcpy(hb, k.hn, sizeof hb);
+    const int w = snprintf(path, n, "%s/isofft_spectrum_%d_%lldx%lldx%lld_%016llx%016llx%016llx.bin", dir, k.dtype,
+                           (long long)k.M[0], (long long)k.M[1], (long long)k.M[2], (unsigned long long)hb[0],
+                           (unsigned long long)hb[1], (unsigned long long)hb[2]);
+    return w > 0 && (size_t)w < n;
+}
+
+static SpecFileHeader spectrum_header(const SpecKey &k, size_t bytes)
+{
+    SpecFileHeader h;
+    memset(&h, 0, sizeof h);
+    memcpy(h.magic, kSpecMagic, sizeof h.magic);
+    h.version = 1;
+    h.dtype = k.dtype;
+    for (int a = 0; a < 3; ++a) {
+        h.M[a] = k.M[a];
+        h.hn[a] = k.hn[a];
+    }
+    h.tile = spectrum_tile(k);
+    h.bytes = bytes;
+    return h;
+}
+
+// Loads the key's file into the device buffer; false if there is none or it
+// does not match.
+static bool spectrum_load(const SpecKey &k, SpecEntry &e, cudaStream_t st)
+{
+    char path[4096];
+    if (!spectrum_path(k, path, sizeof path)) return false;
+    FILE *f = fopen(path, "rb");
+    if (!f) return false;
+    SpecFileHeader h, want = spectrum_header(k, e.bytes);
+    std::vector<unsigned char> buf;
+    bool ok = fread(&h, sizeof h, 1, f) == 1;
+    if (ok) {
+        want.checksum = h.checksum;
+        ok = memcmp(&h, &want, sizeof h) == 0;
+    }
+    if (ok) {
+        buf.resize(e.bytes);
+        ok = fread(buf.data(), 1, e.bytes, f) == e.bytes && fnv1a(buf.data(), e.bytes) == h.checksum;
+    }
+    fclose(f);
+    if (ok) ok = cudaMemcpyAsync(e.G, buf.data(), e.bytes, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+                 cudaStreamSynchronize(st) == cudaSuccess;
+    return ok;
+}
+
+// Writes the device buffer to the key's file (through a temporary file, so
+// a reader never sees a partial one).  Failures only cost the next restart
+// a rebuild.
+static void spectrum_save(const SpecKey &k, const SpecEntry &e, cudaStream_t st)
+{
+    char path[4096], tmp[4200];
+    if (!spectrum_path(k, path, sizeof path)) return;
+    std::vector<unsigned char> buf(e.bytes);
+    if (cudaMemcpyAsync(buf.data(), e.G, e.bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return;
+    SpecFileHeader h = spectrum_header(k, e.bytes);
+    h.checksum = fnv1a(buf.data(), e.bytes);
+    snprintf(tmp, sizeof tmp, "%s.%d.tmp", path, (int)getpid());
+    FILE *f = fopen(tmp, "wb");
+    if (!f) return;
+    const bool ok = fwrite(&h, sizeof h, 1, f) == 1 && fwrite(buf.data(), 1, e.bytes, f) == e.bytes;
+    if (fclose(f) != 0 || !ok || rename(tmp, path) != 0) remove(tmp);
+}
+
 int acquire_spectrum(ipf_plan_s *p, cudaStream_t st)
 {
     std::lock_guard<std::mutex> lk(g_cache_mu);
@@ -411,18 +523,24 @@ int acquire_spectrum(ipf_plan_s *p, cudaStream_t st)
         const size_t es = elem_size(p->dtype);
         const size_t Y = p->M[1] / 2 + 1, Z = p->M[2] / 2 + 1;
         e.Gs = (char *)e.G + e.bytes - es * Y * Z;
-        logf(IPF_CONSOLE_INFO_1, p->verbosity, "building Green's spectrum for mesh %lldx%lldx%lld (%s)",
-             (long long)p->M[0], (long long)p->M[1], (long long)p->M[2],
-             p->dtype == IPF_F32 ? "f32" : (p->dtype == IPF_F64 ? "f64" : "df64"));
-        if (p->dtype == IPF_F32)
-            ce = build_green_spectrum<float>(p->M, p->key.hn, (float *)e.G, (float *)e.Gs, st);
-        else if (p->dtype == IPF_F64)
-            ce = build_green_spectrum<double>(p->M, p->key.hn, (double *)e.G, (double *)e.Gs, st);
-        else
-            ce = build_green_spectrum<df64>(p->M, p->key.hn, (df64 *)e.G, (df64 *)e.Gs, st);
-        if (ce != cudaSuccess) {
-            free_entry(e);
-            return cuda_status(ce);
+        const char *dn = p->dtype == IPF_F32 ? "f32" : (p->dtype == IPF_F64 ? "f64" : "df64");
+        if (spectrum_load(p->key, e, st)) {
+            logf(IPF_CONSOLE_INFO_1, p->verbosity, "loaded Green's spectrum for mesh %lldx%lldx%lld (%s) from disk",
+                 (long long)p->M[0], (long long)p->M[1], (long long)p->M[2], dn);
+        } else {
+            logf(IPF_CONSOLE_INFO_1, p->verbosity, "building Green's spectrum for mesh %lldx%lldx%lld (%s)",
+                 (long long)p->M[0], (long long)p->M[1], (long long)p->M[2], dn);
+            if (p->dtype == IPF_F32)
+                ce = build_green_spectrum<float>(p->M, p->key.hn, (float *)e.G, (float *)e.Gs, st);
+            else if (p->dtype == IPF_F64)
+                ce = build_green_spectrum<double>(p->M, p->key.hn, (double *)e.G, (double *)e.Gs, st);
+            else
+                ce = build_green_spectrum<df64>(p->M, p->key.hn, (df64 *)e.G, (df64 *)e.Gs, st);
+            if (ce != cudaSuccess) {
+                free_entry(e);
+                return cuda_status(ce);
+            }
+            spectrum_save(p->key, e, st);
         }
         it = g_cache.emplace(p->key, e).first;
     }

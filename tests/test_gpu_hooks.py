@@ -126,3 +126,41 @@ def test_nvtx_ranges_leave_the_potential_unchanged(monkeypatch):
     monkeypatch.setenv("ISOFFT_NVTX", "1")
     traced, _ = device_solves(N, h, "f32", 0, src, count=1)
     assert torch.equal(traced[0], plain[0])
+
+
+@pytest.mark.parametrize("dtype", ["f32", "df64"])
+def test_spectrum_directory_lets_a_restart_skip_the_build(dtype, tmp_path, monkeypatch, capfd):
+    """With ISOFFT_SPECTRUM_DIR set, the first plan builds the spectrum and
+    writes it; once the in-memory cache is trimmed, the next plan reads the
+    file (no build) and solves bitwise the same; a corrupted file is
+    ignored, rebuilt and replaced."""
+    from paper_1106_0557_gb300 import Plan
+    N = (30, 26, 22)
+    h = (1.0, 1.3, 0.9) if dtype == "f32" else (1.0, 1.3, 0.8)  # width ratios no other test uses
+    monkeypatch.setenv("ISOFFT_SPECTRUM_DIR", str(tmp_path))
+    monkeypatch.delenv("ISOFFT_VERBOSITY", raising=False)
+    d = torch.from_numpy(rand_src(N, 11).astype(NP[dtype])).cuda()
+
+    def restart():
+        with Plan(N, h, dtype, verbosity=native.IPF_CONSOLE_INFO_1) as p:
+            out = p.solve(d).cpu().numpy()
+            p.check()
+        native.ipf_greens_cache_trim(0)  # the next plan finds no spectrum in memory
+        return out, capfd.readouterr().err
+
+    first, log = restart()
+    assert "building Green's spectrum" in log
+    files = list(tmp_path.glob("isofft_spectrum_*.bin"))
+    assert len(files) == 1
+    second, log = restart()
+    assert "loaded Green's spectrum" in log and "building Green's spectrum" not in log
+    assert np.array_equal(second, first)
+    raw = bytearray(files[0].read_bytes())
+    raw[-5] ^= 0xFF
+    files[0].write_bytes(bytes(raw))
+    third, log = restart()
+    assert "building Green's spectrum" in log
+    assert np.array_equal(third, first)
+    fourth, log = restart()
+    assert "loaded Green's spectrum" in log
+    assert np.array_equal(fourth, first)
