@@ -124,8 +124,8 @@ enum {
 int ipf_plan_create(ipf_plan_t *out, const int64_t n[3], const double h[3], int dtype,
                     uint32_t flags, int verbosity, void *stream);
 
-/* Release a plan, its workspace and its reference to the cached spectrum.
- * Waits for nothing: the caller must not destroy a plan with work still in
+/* Release a plan, its workspace and its reference to the cached spectrum
+ * (paper Sec. 3.2, `Destroy(PoissonSolver)`).  Waits for nothing: the caller must not destroy a plan with work still in
  * flight.  NULL is accepted and ignored. */
 int ipf_plan_destroy(ipf_plan_t plan);
 
@@ -134,12 +134,15 @@ int ipf_plan_destroy(ipf_plan_t plan);
 int ipf_plan_padded_shape(const ipf_plan_t plan, int64_t m[3]);
 
 /* Device bytes the plan owns (its workspace), and the bytes of the cached
- * Green's spectrum it references, for admission against a memory budget. */
+ * Green's spectrum it references, for admission against a memory budget.
+ * Not in the paper (which has one solver per process and no admission); the
+ * spectrum is the transform the paper computes once and keeps (Sec. 2.2.2). */
 int ipf_plan_workspace_bytes(const ipf_plan_t plan, size_t *bytes);
 int ipf_plan_spectrum_bytes(const ipf_plan_t plan, size_t *bytes);
 
 /* Device bytes a plan of this shape and dtype would need (workspace plus the
- * spectrum if it is not cached yet), without creating it. */
+ * spectrum if it is not cached yet), without creating it.  Not in the
+ * paper: an admission aid for serving. */
 int ipf_estimate_bytes(const int64_t n[3], const double h[3], int dtype, size_t *bytes);
 
 /* One solve (paper Sec. 3.2, `Solve(PoissonSolver, SourceSolution)`):
@@ -200,10 +203,14 @@ int ipf_plan_check(ipf_plan_t plan, void *stream);
  * device it is loaded on until the process exits; the spectrum is rebuilt on
  * every call.  A mesh whose tables, spectrum and workspace exceed 64 MiB is
  * rejected with IPF_BUDGET_EXCEEDED before any device work (FP32 fits up to
- * about 128^3 cells, FP64 up to about 96^3).  Every call overwrites the whole
- * array (nothing in it needs to start at zero), so calls whose work overlaps
- * on the GPU -- on different streams, or from different threads -- race and
- * must be serialised by the caller.  The first call on each device looks up
+ * about 128^3 cells, FP64 up to about 96^3).  The array's first word is a
+ * status word: it starts at zero (static initialisation), the passes' bounded
+ * waits set bits in it, and only ipf_noalloc_check reads and clears it, so a
+ * flag raised by one call stays set for later calls until that check runs.
+ * Every other byte the solve uses is written before it is read on every
+ * call.  Calls whose work overlaps on the GPU -- on different streams, or
+ * from different threads -- race on the array and must be serialised by the
+ * caller.  The first call on each device looks up
  * the array's device address and sets kernel attributes; make that first
  * call before any stream capture.  Asynchronous on `stream`. */
 int ipf_solve_noalloc(const int64_t n[3], const double h[3], int dtype, const void *d_src, void *d_phi,
@@ -214,7 +221,9 @@ int ipf_solve_noalloc(const int64_t n[3], const double h[3], int dtype, const vo
 int ipf_noalloc_check(void *stream);
 
 /* Submit `count` independent solves, possibly of different shapes and
- * dtypes; plans[i] solves d_src[i] into d_phi[i].  A plan may appear only
+ * dtypes; plans[i] solves d_src[i] into d_phi[i].  Not in the paper, which
+ * runs one solve at a time per communicator; each solve is the Sec. 2.2.2
+ * sequence of ipf_solve.  A plan may appear only
  * once per batch (each owns one workspace).  The solves are spread over up to
  * 8 internal streams of the library that fork from and join back into
  * `stream`: the batch starts after the work already enqueued on `stream`, and
@@ -250,6 +259,10 @@ int ipf_plan_pass_times(ipf_plan_t plan, float ms[5]);
 int ipf_plan_variants(const ipf_plan_t plan, int v[2]);
 
 /* Bytes held by the library's cache of Green's spectra, and a trim of
+ * unreferenced entries.  The paper computes the transform of the Green's
+ * function once at initialisation and keeps it for every later solve
+ * (Sec. 2.2.2); the cache keeps one such transform per doubled mesh, width
+ * ratios and dtype, shared by the plans that need it.  Trim frees
  * unreferenced entries (least recently used first) until the cache holds
  * at most `budget` bytes.  With the environment variable ISOFFT_SPECTRUM_DIR
  * naming a directory, every spectrum the cache builds is also written there
@@ -267,7 +280,8 @@ int ipf_launch_count(uint64_t *count);
 /* The last CUDA error code seen by the library on this thread (0 if none). */
 int ipf_last_cuda_error(void);
 
-/* Static description of a status code; never NULL. */
+/* Static description of a status code; never NULL.  Not in the paper (its
+ * Fortran interface reports errors through the console). */
 const char *ipf_status_string(int status);
 
 #ifdef __cplusplus

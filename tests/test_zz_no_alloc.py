@@ -31,13 +31,15 @@ def _rel(a, b):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
-def test_noalloc_matches_plan_solve_on_consecutive_calls(dtype):
+def test_noalloc_matches_plan_solve_on_consecutive_calls(dtype, oracle_mod):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_1106_0557_gb300 import Plan
     stream = torch.cuda.current_stream().cuda_stream
+    # (16, 300, 16): 768-point y lines, which FP32 runs in the streamed y form
+    # (tensor maps over the static array); the others take the tile form
     cases = [((40, 33, 24), (1.0, 1.0, 1.0), 1), ((32, 20, 17), (0.5, 0.25, 1.0), 2),
-             ((40, 33, 24), (1.0, 1.0, 1.0), 3)]
+             ((40, 33, 24), (1.0, 1.0, 1.0), 3), ((16, 300, 16), (1.0, 0.5, 1.0), 4)]
     for N, h, seed in cases:
         src = _src(N, seed, dtype)
         got = torch.empty_like(src)
@@ -47,6 +49,10 @@ def test_noalloc_matches_plan_solve_on_consecutive_calls(dtype):
         torch.cuda.synchronize()
         native.ipf_noalloc_check(stream)  # no bounded device wait gave up
         assert _rel(got, ref) <= TOL[dtype], (N, h, dtype)
+        # and against the FP64 oracle on the same (dtype-rounded) source
+        want = oracle_mod.solve(src.double().cpu().numpy(), h)
+        err = oracle_mod.max_rel_error(got.double().cpu().numpy(), want)
+        assert err <= TOL[dtype], (N, h, dtype, err)
 
 
 def test_noalloc_rejects_oversize_and_bad_arguments():
