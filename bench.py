@@ -244,7 +244,11 @@ def reduce_sum(value, ws, device=None):
 # ---------------------------------------------------------------------------
 # CPU oracle timing (the reference arm and the cpu_baseline field)
 # ---------------------------------------------------------------------------
-def time_oracle(n, steps, budget_s, warmup=0):
+def time_oracle(n, steps, budget_s, warmup=0, keep=False):
+    """Times full oracle solves of the workload.  With `keep`, also returns
+    the oracle's potentials of the workload's FP64 source and of that source
+    rounded to FP32 (the exact input of the FP32 GPU solve), the references
+    of the GPU results' error statement."""
     import oracle
     from paper_1106_0557_gb300 import sources
     w = sources.multi_sphere(n, seed=0)
@@ -254,14 +258,33 @@ def time_oracle(n, steps, budget_s, warmup=0):
     for _ in range(warmup):
         oracle.solve_with_spectrum(src, M, Gt)
     times = []
+    phi = None
     t_start = time.perf_counter()
     for _ in range(steps):
         t0 = time.perf_counter()
-        oracle.solve_with_spectrum(src, M, Gt)
+        phi = oracle.solve_with_spectrum(src, M, Gt)
         times.append(time.perf_counter() - t0)
         if time.perf_counter() - t_start > budget_s:
             break
-    return len(times), sum(times), oracle.num_threads()
+    if not keep:
+        return len(times), sum(times), oracle.num_threads()
+    refs = {"f64": phi, "f32": oracle.solve_with_spectrum(src.astype(np.float32).astype(np.float64), M, Gt)}
+    return len(times), sum(times), oracle.num_threads(), refs
+
+
+def potential_errors(potentials, refs):
+    """Normwise max|phi - ref| / max|ref| and pointwise max |phi - ref| / |ref|
+    (well defined: the potential of a non-negative source is negative
+    everywhere) of each dtype's GPU potential against the FP64 oracle on the
+    same input; FP64 and df64 solve the FP64 source, FP32 its FP32 rounding."""
+    tol = {"f32": 1e-5, "f64": 1e-12, "df64": 1e-12}
+    out = {}
+    for dt, phi in potentials.items():
+        ref = refs["f32" if dt == "f32" else "f64"]
+        d = np.abs(phi - ref)
+        out[dt] = {"normwise": float(d.max() / np.abs(ref).max()), "pointwise": float((d / np.abs(ref)).max()),
+                   "tol": tol[dt], "cells": int(ref.size), "ref": "full-grid FP64 oracle solve"}
+    return out
 
 
 def run_reference(args, ws, rank):
@@ -486,6 +509,7 @@ def run_isofft(args, ws, rank, local):
     stream = torch.cuda.current_stream()
 
     forms = {}  # y-pass forms the plans picked
+    potentials = {}  # the last timed solve's potential per dtype (host, FP64)
 
     def timed_solves(dtype, steps, warmup, pool=4):
         tdt = torch.float32 if dtype == "f32" else torch.float64  # df64 reads and writes FP64 arrays
@@ -515,6 +539,7 @@ def run_isofft(args, ws, rank, local):
         M = plan.padded_shape
         phi = outs[(steps - 1) % pool]
         finite = bool(torch.isfinite(phi).all().item())
+        potentials[dtype] = phi.double().cpu().numpy()
         plan.close()
         del srcs, outs
         torch.cuda.empty_cache()
@@ -601,11 +626,13 @@ def run_isofft(args, ws, rank, local):
     serve = None if args.no_serve else run_serving(args.serve_requests, args.serve_slots)
 
     cpu = None
+    errors = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        done, secs, cores = time_oracle(n, 1, budget_s=60.0)
+        done, secs, cores, refs = time_oracle(n, 1, budget_s=60.0, keep=True)
         cpu = {"value": done / secs, "unit": "solves/s", "cores": cores, "kind": "oracle",
                "sample": "%d full %d^3 FP64 oracle solve (doubled mesh %d^3), Green's spectrum built "
                          "before timing" % (done, n, 2 * n)}
+        errors = potential_errors(potentials, refs)
 
     if rank != 0:
         return
@@ -640,6 +667,7 @@ def run_isofft(args, ws, rank, local):
         "serving": serve,
         "paper_scale": paper_scale,
         "cpu_baseline": cpu,
+        "max_rel_err": errors,
         "gpu_launches": launches,
         "clocks": clocks,
         "finite": finite32 and finite64 and finitedf,

@@ -266,10 +266,13 @@ int ipf_plan_variants(const ipf_plan_t plan, int v[2]);
  * unreferenced entries (least recently used first) until the cache holds
  * at most `budget` bytes.  With the environment variable ISOFFT_SPECTRUM_DIR
  * naming a directory, every spectrum the cache builds is also written there
- * (one file per mesh, width ratios and dtype, with a checksum), and a plan
+ * (one file per mesh, width ratios and dtype, with a checksum and a digest
+ * of the library code that builds and lays out the spectrum), and a plan
  * whose spectrum is not in memory reads a matching file instead of
  * rebuilding it: the restart of a job skips the spectrum build, the
- * solver's only state.  Files that do not match are ignored. */
+ * solver's only state.  Files that do not match (another mesh, corrupted,
+ * or written by a library whose spectrum code differs) are ignored and
+ * rebuilt. */
 int ipf_greens_cache_bytes(size_t *bytes);
 int ipf_greens_cache_trim(size_t budget);
 

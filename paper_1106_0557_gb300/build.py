@@ -23,8 +23,21 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxe
          "-I", INCLUDE, "-I", CSRC]
 
 
+def _spectrum_code():
+    """32-bit digest of the sources that define the cached Green's spectrum
+    (its build and layout); spectrum files written by other code are
+    rejected (see ISOFFT_SPECTRUM_DIR in include/isofft.h)."""
+    import hashlib
+    h = hashlib.sha256()
+    for fn in ("greens.cu", "launch.h", "fft_engine.cuh", "passes.cuh"):
+        with open(os.path.join(CSRC, fn), "rb") as f:
+            h.update(f.read())
+    return "0x%08x" % (int(h.hexdigest()[:8], 16) | 1)
+
+
 def _units():
-    units = [("api", "api.cu", []), ("greens", "greens.cu", []), ("noalloc", "noalloc.cu", [])]
+    units = [("api", "api.cu", ["-DISOFFT_SPECTRUM_CODE=%s" % _spectrum_code()]), ("greens", "greens.cu", []),
+             ("noalloc", "noalloc.cu", [])]
     for real, tag in (("float", "f32"), ("double", "f64"), ("isofft::df64", "df64")):
         for group, gname in ((1, "x"), (2, "y"), (3, "z"), (4, "xy")):
             units.append(("passes_%s_%s" % (gname, tag), "passes_inst.cu",

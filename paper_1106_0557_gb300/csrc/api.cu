@@ -421,6 +421,9 @@ struct SpecFileHeader {
 };
 
 static const char kSpecMagic[8] = {'I', 'S', 'O', 'F', 'F', 'T', 'G', 'S'};
+#ifndef ISOFFT_SPECTRUM_CODE
+#error "the build passes ISOFFT_SPECTRUM_CODE (a digest of the spectrum code)"
+#endif
 
 static uint64_t fnv1a(const unsigned char *d, size_t n)
 {
@@ -455,7 +458,7 @@ static SpecFileHeader spectrum_header(const SpecKey &k, size_t bytes)
     SpecFileHeader h;
     memset(&h, 0, sizeof h);
     memcpy(h.magic, kSpecMagic, sizeof h.magic);
-    h.version = 1;
+    h.version = ISOFFT_SPECTRUM_CODE;  // digest of the spectrum's build and layout code
     h.dtype = k.dtype;
     for (int a = 0; a < 3; ++a) {
         h.M[a] = k.M[a];

@@ -82,14 +82,15 @@ size_t spectrum_elems(const int64_t M[3]);
 // Green's spectrum (FP64 build).  M = doubled mesh, hn = widths divided by
 // their minimum.  Writes G [My/2+1][Mz/2+1][Mx/2] and Gs [My/2+1][Mz/2+1] of
 // type T in the z pass's tiled layout, pre-divided by 2 Mx My Mz (see
-// passes.cuh).  Allocates and frees
-// its FP64 scratch; synchronises `st` before returning.
+// passes.cuh).  Allocates and frees its FP64 scratch; synchronises `st`
+// before returning.
 template <typename T>
 cudaError_t build_green_spectrum(const int64_t M[3], const double hn[3], T *G, T *Gs, cudaStream_t st);
 
 // The same spectrum enqueued without allocating or synchronising, in caller
-// scratch: `oct` holds 2 * green_octant_elems(M) doubles, `ct` holds
-// green_cos_elems(M) doubles (cosine tables, computed on the device).
+// scratch: `oct` holds green_octant_elems(M) doubles (the FP64 octant,
+// transformed in place), `ct` holds green_cos_elems(M) doubles (the root
+// tables of the three axes, computed on the device).
 template <typename T>
 cudaError_t enqueue_green_spectrum(const int64_t M[3], const double hn[3], T *G, T *Gs, double *oct,
                                    double *ct, cudaStream_t st);

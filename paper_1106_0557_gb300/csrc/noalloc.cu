@@ -91,7 +91,7 @@ Carve carve(const int64_t N[3], const int64_t M[3])
     off += align256(spectrum_elems<T>(M) * sizeof(T));
     // the workspace and the FP64 spectrum-build scratch are never live at once
     const size_t work = (size_t)N[2] * M[1] * Lx * cs;
-    const size_t build = (2 * green_octant_elems(M) + green_cos_elems(M)) * sizeof(double);
+    const size_t build = (green_octant_elems(M) + green_cos_elems(M)) * sizeof(double);
     c.work = off;
     off += align256(work > build ? work : build);
     c.total = off;
@@ -127,7 +127,7 @@ int solve_noalloc(const int64_t N[3], const int64_t M[3], const double hn[3], do
     count_launch();
     // the spectrum, built in the workspace region before the workspace is used
     double *oct = (double *)W;
-    double *ct = oct + 2 * green_octant_elems(M);
+    double *ct = oct + green_octant_elems(M);
     e = enqueue_green_spectrum<T>(M, hn, G, Gs, oct, ct, st);
     if (e == cudaSuccess)
         e = launch_x_forward<T>(Lx, (const T *)src, W, tw_x, rtw, Nx, Ny, My, (int64_t)Ny * Nz, st);

@@ -111,6 +111,30 @@ def test_multisphere_256_sampled_direct_sum(dtype):
     assert np.max(np.abs(phi.ravel()[cells] - ref)) / scale <= TOL[dtype]
 
 
+@pytest.fixture(scope="module")
+def multisphere_256_refs():
+    """Full-grid FP64 oracle potentials (route 2) of the 256^3 multi-sphere
+    workload: of its FP64 source and of that source rounded to FP32."""
+    w = sources.multi_sphere(256, seed=0)
+    s = w.source()
+    return w, {"f64": oracle.solve(s, w.h), "f32": oracle.solve(s.astype(np.float32).astype(np.float64), w.h)}
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64", "df64"])
+def test_multisphere_256_full_grid(dtype, multisphere_256_refs):
+    """The benchmark workload at full size: every one of the 16.7 M cells
+    against the oracle, in the launch configuration the benchmark times
+    (a plan, device buffers).  Normwise within the dtype's tolerance; the
+    pointwise relative error (the potential is negative everywhere) within
+    ten times it."""
+    w, refs = multisphere_256_refs
+    phi, _ = gpu_solve(w.source(), w.h, dtype)
+    ref = refs["f32" if dtype == "f32" else "f64"]
+    d = np.abs(phi - ref)
+    assert d.max() / np.abs(ref).max() <= TOL[dtype]
+    assert (d / np.abs(ref)).max() <= 10 * TOL[dtype]
+
+
 def test_linearity_translation_on_gpu():
     N, h = (96, 80, 64), (1.0, 1.0, 1.0)
     a, b = rand_src(N, 1), rand_src(N, 2)
