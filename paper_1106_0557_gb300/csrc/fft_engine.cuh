@@ -69,60 +69,13 @@ __host__ __device__ constexpr double cos48(int j)
 }
 __host__ __device__ constexpr double sin48(int j) { return cos48(12 - j); }
 
-// cos(2 pi j / 32) for j in [0, 8], for the 32nd roots (radix 32 split in
-// the z pass); other angles by the same exact symmetries.
-__host__ __device__ constexpr double cos32_base(int j)
-{
-    constexpr double b[9] = {1.0, 0.98078528040323044913, 0.92387953251128675613, 0.83146961230254523708,
-                             0.70710678118654752440, 0.55557023301960222474, 0.38268343236508977173,
-                             0.19509032201612826785, 0.0};
-    return b[j];
-}
-__host__ __device__ constexpr double cos32(int j)
-{
-    j %= 32;
-    if (j < 0) j += 32;
-    if (j > 16) j = 32 - j;
-    return j > 8 ? -cos32_base(16 - j) : cos32_base(j);
-}
-__host__ __device__ constexpr double sin32(int j) { return cos32(8 - j); }
-
-// Multiply by W_32^j = e^{-2 pi i j / 32}.
-template <typename T, int j>
-ISOFFT_HD Cx<T> mul_root32(Cx<T> a)
-{
-    constexpr int jj = ((j % 32) + 32) % 32;
-    if constexpr (jj == 0) {
-        return a;
-    } else if constexpr (jj == 8) {
-        return cmul_mi(a);
-    } else if constexpr (jj == 16) {
-        return {-a.x, -a.y};
-    } else if constexpr (jj == 24) {
-        return {-a.y, a.x};
-    } else if constexpr (jj % 8 == 4) {
-        constexpr T r = (T)0.7071067811865476;
-        constexpr bool cp = cos32(jj) > 0, sp = sin32(jj) > 0;
-        const T cx = cp ? a.x : -a.x, cy = cp ? a.y : -a.y;
-        const T sx = sp ? a.x : -a.x, sy = sp ? a.y : -a.y;
-        return {(cx + sy) * r, (cy - sx) * r};
-    } else {
-        constexpr T c = (T)cos32(jj);
-        constexpr T s = (T)sin32(jj);
-        return {a.x * c + a.y * s, a.y * c - a.x * s};
-    }
-}
-
-// Multiply by the compile-time root W_R^e = e^{-2 pi i e / R} (48 % R == 0,
-// or R = 32).
+// Multiply by the compile-time root W_R^e = e^{-2 pi i e / R} (48 % R == 0).
 template <typename T, int R, int e>
 ISOFFT_HD Cx<T> mul_root(Cx<T> a)
 {
     constexpr int ee = ((e % R) + R) % R;
-    constexpr int j = 48 % R == 0 ? ee * (48 / R) : 0;  // angle in units of 2 pi / 48
-    if constexpr (R == 32) {
-        return mul_root32<T, e>(a);
-    } else if constexpr (j == 0) {
+    constexpr int j = ee * (48 / R);  // angle in units of 2 pi / 48
+    if constexpr (j == 0) {
         return a;
     } else if constexpr (j == 12) {
         return cmul_mi(a);  // -i

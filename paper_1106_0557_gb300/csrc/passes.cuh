@@ -35,11 +35,8 @@
 // run a persistent grid on the lengths that keep their twiddles in
 // registers).
 #pragma once
-#include <type_traits>
-
 #include "fft_engine.cuh"
 #include "launch.h"
-#include "pf2.cuh"
 #include "tma.cuh"
 
 namespace isofft {
@@ -227,15 +224,12 @@ constexpr int z_tile_width(int rb, int nt, int L, int e)
     return tx;
 }
 
-// FORM: 0 the radix-8 tile of the z pass, 1 the split 512-point tile
-// (z_tile_split) on the same tile shape, 2 the split tile on 4-column tiles
-// of 256 threads, two CTAs per SM (FP32 512-point lines).
-template <typename T, int L, int FORM = 0>
+template <typename T, int L>
 struct ZCfg {
     static constexpr int E = ZShape<T, L>::E;
     static constexpr int NT = L / E;
     static constexpr int LH = L / 2;
-    static constexpr int TX = FORM == 2 ? 4 : z_tile_width((int)sizeof(T), NT, L, E);
+    static constexpr int TX = z_tile_width((int)sizeof(T), NT, L, E);
     static constexpr int COLS = 2 * TX;
     static constexpr int THREADS = COLS * NT;
     // tensor boxes: NZB equal boxes of at most 256 planes per line group
@@ -258,7 +252,7 @@ struct ZCfg {
     // shared memory (read by every stage, loaded once per CTA)
     static constexpr bool TWR = ZShape<T, L>::TW_REGS;
     static constexpr size_t TWS = TWR ? 0 : (size_t)L * sizeof(Cx<T>);
-    static constexpr int MIN_BLOCKS = FORM == 2 ? 2 : (sizeof(T) == 8 && E == 12 && NT >= 32 && NT <= 64 ? 3 : 1);
+    static constexpr int MIN_BLOCKS = sizeof(T) == 8 && E == 12 && NT >= 32 && NT <= 64 ? 3 : 1;
     // Two exchange buffers used in turn need one CTA barrier per exchange
     // instead of two; the input is then staged once per tile (the next
     // tile's copies start after the first exchange's barrier, when every
@@ -698,20 +692,6 @@ struct ZXch {
         if constexpr (!DB) __syncthreads();
         ++k;
     }
-    // Exchanges with other patterns: write positions of cur(), then mid()
-    // (the barrier and the hook), read positions, then done().
-    __device__ __forceinline__ Cx<T> *cur() const { return buf(k); }
-    __device__ __forceinline__ Cx<T> &at(Cx<T> *s, int pos) const { return s[Rows::row(pos) * COLS + c]; }
-    __device__ __forceinline__ void mid()
-    {
-        __syncthreads();
-        hook(k);
-    }
-    __device__ __forceinline__ void done()
-    {
-        if constexpr (!DB) __syncthreads();
-        ++k;
-    }
 };
 
 
@@ -1082,25 +1062,44 @@ k_yx_inverse(Cx<T> *__restrict__ W, In<T> *__restrict__ phi, const Cx<T> *__rest
     }
 }
 
-// The spectrum multiply of a z tile: thread t holds the bins kz = t + m NT
-// of its line (column c of group g, k_y' = kyp) in v.  `sg`: the spectrum
-// block of the thread's line, [kz'][TX] (kz' = kz below L/2, L - kz from L/2
-// on).  The packed column kx = 0 / Mx/2 (xt == 0, c == 0) also needs the
-// partner bin (-ky, -kz), which it takes from the other line group through
-// `sp`, an exchange buffer no thread is reading (two CTA barriers).
-template <typename T, int L, int FORM = 0>
-__device__ __forceinline__ void z_spectrum_mul(Cx<T> (&v)[ZCfg<T, L>::E], const T *sg, int pr, int xt,
-                                               const T *__restrict__ Gs, T gscale, int c, int g, int t, int kyp,
-                                               Cx<T> *sp)
+// One tile of the z pass on staged data: the forward transforms of the
+// thread's line, the multiply by the Green's spectrum, the inverse
+// transforms and the store of z < Nz.  `sin`: the thread's line group as
+// staged, [z < L/2][IS] (IS = TX, or 2 TX where a box holds two tiles),
+// offset to the tile's first column; `sg`: the spectrum block of the
+// thread's line, [kz'][TX].  `before_g` runs before the spectrum is read and
+// returns false (the same on every thread) to abandon the tile.
+template <typename T, int L, int IS, typename TWR, typename Xch, typename BeforeG>
+__device__ __forceinline__ bool z_tile(const Cx<T> *sin, const T *sg, int pr, int xt, Cx<T> *__restrict__ W,
+                                       const T *__restrict__ Gs, T gscale, int Nz, int My, int Kx, int c, int g,
+                                       int t, const TWR &twr, const Cx<T> *twz, Xch &xch, BeforeG before_g)
 {
-    using C = ZCfg<T, L, FORM>;
+    using C = ZCfg<T, L>;
+    using Rad = typename ZShape<T, L>::Rad;
     constexpr int E = C::E, NT = C::NT, TX = C::TX, COLS = C::COLS, Lh = L / 2;
     const int col = g * TX + c;
+    const int ky = g == 0 ? pr : (pr == 0 ? My / 2 : My - pr);
+    const int kx = xt * TX + c;
+    const bool active = kx < Kx;
+    const int kyp = ky <= My - ky ? ky : My - ky;
+
+    // z < Lh from the staged boxes (zeros past Nz), the upper half is zero
+    sin += t * IS + c;
+    Cx<T> v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = m < E / 2 ? sin[m * NT * IS] : Cx<T>{(T)0, (T)0};
+
+    z_fft<C::TWR, true, T, L, E>(v, t, twr, twz, xch, Rad{});
+    if (!before_g()) return false;
+
+    // spectrum at kz = t + m NT: kz' = kz below Lh, L - kz from Lh on
     const T *g_lo = sg + t * TX + c;
     const T *g_hi = sg + (L - t) * TX + c;
     auto gval = [&](int m) -> T { return m < E / 2 ? g_lo[m * NT * TX] : g_hi[-m * NT * TX]; };
     const bool packed = xt == 0 && c == 0;  // the kx = 0 / Mx/2 column
     if (xt == 0) {
+        // the packed column needs the partner bin (-ky, -kz)
+        Cx<T> *sp = xch.free_buf();
         if (c == 0) {
 #pragma unroll
             for (int m = 0; m < E; ++m) sp[(t + m * NT) * COLS + col] = v[m];
@@ -1125,37 +1124,6 @@ __device__ __forceinline__ void z_spectrum_mul(Cx<T> (&v)[ZCfg<T, L>::E], const 
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = cscale(v[m], gval(m) * gscale);
     }
-}
-
-// One tile of the z pass on staged data: the forward transforms of the
-// thread's line, the multiply by the Green's spectrum, the inverse
-// transforms and the store of z < Nz.  `sin`: the thread's line group as
-// staged, [z < L/2][IS] (IS = TX, or 2 TX where a box holds two tiles),
-// offset to the tile's first column; `sg`: the spectrum block of the
-// thread's line, [kz'][TX].  `before_g` runs before the spectrum is read and
-// returns false (the same on every thread) to abandon the tile.
-template <typename T, int L, int IS, typename TWR, typename Xch, typename BeforeG>
-__device__ __forceinline__ bool z_tile(const Cx<T> *sin, const T *sg, int pr, int xt, Cx<T> *__restrict__ W,
-                                       const T *__restrict__ Gs, T gscale, int Nz, int My, int Kx, int c, int g,
-                                       int t, const TWR &twr, const Cx<T> *twz, Xch &xch, BeforeG before_g)
-{
-    using C = ZCfg<T, L>;
-    using Rad = typename ZShape<T, L>::Rad;
-    constexpr int E = C::E, NT = C::NT, TX = C::TX;
-    const int ky = g == 0 ? pr : (pr == 0 ? My / 2 : My - pr);
-    const int kx = xt * TX + c;
-    const bool active = kx < Kx;
-    const int kyp = ky <= My - ky ? ky : My - ky;
-
-    // z < Lh from the staged boxes (zeros past Nz), the upper half is zero
-    sin += t * IS + c;
-    Cx<T> v[E];
-#pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = m < E / 2 ? sin[m * NT * IS] : Cx<T>{(T)0, (T)0};
-
-    z_fft<C::TWR, true, T, L, E>(v, t, twr, twz, xch, Rad{});
-    if (!before_g()) return false;
-    z_spectrum_mul<T, L>(v, sg, pr, xt, Gs, gscale, c, g, t, kyp, xch.free_buf());
 
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = cswap(v[m]);
@@ -1166,128 +1134,6 @@ __device__ __forceinline__ bool z_tile(const Cx<T> *sin, const T *sg, int pr, in
 #pragma unroll
         for (int m = 0; m < E / 2; ++m) {
             const int z = t + m * NT;
-            if (z < Nz) base[(size_t)z * zstride] = cswap(v[m]);
-        }
-    }
-    return true;
-}
-
-// Twiddles of the split 512-point z lines, W_512^{r t} for r = 1..15, kept
-// in registers across tiles.
-template <typename T>
-struct ZSplitTw {
-    Cx<T> w[15];
-    __device__ __forceinline__ void load(const Cx<T> *__restrict__ tw, int t)
-    {
-#pragma unroll
-        for (int r = 1; r < 16; ++r) w[r - 1] = tw[r * t];
-    }
-};
-
-template <typename T, int r = 1>
-__device__ __forceinline__ void mul_w32_all(Cx<T> (&v)[16])
-{
-    v[r] = mul_root32<T, r>(v[r]);
-    if constexpr (r < 15) mul_w32_all<T, r + 1>(v);
-}
-
-// One 512-point z tile in two exchanges instead of four (512 = 32 x 16).
-// * Forward: the line is zero past L/2, so its first stage is a radix-32
-//   stage with inputs only at r < 16 (positions j + 16 r, butterflies
-//   j < 16): its even outputs are the 16-point DFT of the inputs, its odd
-//   outputs the 16-point DFT of the inputs times W_32^r.  Threads t < 16 form
-//   the even and t >= 16 the odd half of butterfly j = t mod 16 (t >= 16 is
-//   warp-uniform: a warp holds two adjacent positions).  After one exchange
-//   a radix-16 stage with twiddles W_512^{r t} leaves thread t with the bins
-//   t + 32 r in natural order, as the spectrum multiply expects.
-// * Inverse (swap(FFT(swap))): the same stages backwards.  A radix-16 stage
-//   on the bins in registers, the twiddles W_512^{r t} applied to its outputs
-//   before the exchange, then a radix-32 stage of which only the outputs
-//   z < L/2 are formed: even ones are the 16-point DFT of a_r + a_{r+16},
-//   odd ones that of (a_r - a_{r+16}) W_32^r, split over the two thread
-//   halves again.  Thread t then holds z = t + 32 s, s < 8, the layout the
-//   store of the eight-stage form has.
-// The arithmetic per point is that of the radix-8 form within a few per
-// cent; the exchanges (and CTA barriers) per tile halve.
-template <typename T, int L, int FORM, int IS, typename Xch, typename BeforeG>
-__device__ __forceinline__ bool z_tile_split(const Cx<T> *sin, const T *sg, int pr, int xt, Cx<T> *__restrict__ W,
-                                             const T *__restrict__ Gs, T gscale, int Nz, int My, int Kx, int c,
-                                             int g, int t, const ZSplitTw<T> &tw, Xch &xch, BeforeG before_g)
-{
-    using C = ZCfg<T, L, FORM>;
-    static_assert(L == 512 && C::E == 16 && C::NT == 32, "split z lines: 512 points, 16 per thread");
-    constexpr int TX = C::TX, COLS = C::COLS;
-    const int col = g * TX + c;
-    // Position rows narrower than 128 bytes put two positions on one bank
-    // row; a half-warp holds positions t and t + 1 (t even), whose rows the
-    // exchange writes 16 or 32 positions apart.  Flipping bit 0 of the row
-    // by bit 4 ^ bit 5 of the position separates them (and keeps the reads
-    // of adjacent positions apart).
-    auto at = [&](Cx<T> *s, int p) -> Cx<T> & {
-        if constexpr (COLS * sizeof(Cx<T>) >= 128)
-            return s[p * COLS + col];
-        else
-            return s[(p ^ (((p >> 4) ^ (p >> 5)) & 1)) * COLS + col];
-    };
-    const int ky = g == 0 ? pr : (pr == 0 ? My / 2 : My - pr);
-    const int kx = xt * TX + c;
-    const bool active = kx < Kx;
-    const int kyp = ky <= My - ky ? ky : My - ky;
-    const int j = t & 15;
-    const bool odd = t >= 16;
-
-    // forward, radix-32 half: inputs z = j + 16 m (all below L/2)
-    Cx<T> v[16];
-    sin += j * IS + c;
-#pragma unroll
-    for (int m = 0; m < 16; ++m) v[m] = sin[m * 16 * IS];
-    if (odd) mul_w32_all<T>(v);
-    Dft<T, 16>::run(v);
-    {
-        Cx<T> *s = xch.cur();
-#pragma unroll
-        for (int q = 0; q < 16; ++q) at(s, 32 * j + 2 * q + (odd ? 1 : 0)) = v[q];
-        xch.mid();
-#pragma unroll
-        for (int r = 0; r < 16; ++r) v[r] = at(s, t + 32 * r);
-        xch.done();
-    }
-    // forward, radix-16 stage
-#pragma unroll
-    for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], tw.w[r - 1]);
-    Dft<T, 16>::run(v);
-    if (!before_g()) return false;
-    z_spectrum_mul<T, L, FORM>(v, sg, pr, xt, Gs, gscale, c, g, t, kyp, xch.free_buf());
-
-    // inverse, radix-16 stage on the bins t + 32 r
-#pragma unroll
-    for (int m = 0; m < 16; ++m) v[m] = cswap(v[m]);
-    Dft<T, 16>::run(v);
-#pragma unroll
-    for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], tw.w[r - 1]);
-    {
-        Cx<T> *s = xch.cur();
-#pragma unroll
-        for (int r = 0; r < 16; ++r) at(s, 16 * t + r) = v[r];
-        xch.mid();
-        // inverse, radix-32 stage (outputs below L/2 only)
-        if (odd) {
-#pragma unroll
-            for (int r = 0; r < 16; ++r) v[r] = csub(at(s, j + 16 * r), at(s, j + 16 * r + 256));
-        } else {
-#pragma unroll
-            for (int r = 0; r < 16; ++r) v[r] = cadd(at(s, j + 16 * r), at(s, j + 16 * r + 256));
-        }
-        xch.done();
-    }
-    if (odd) mul_w32_all<T>(v);
-    Dft<T, 16>::run(v);
-    if (active) {
-        Cx<T> *base = W + (size_t)ky * Kx + kx;
-        const size_t zstride = (size_t)My * Kx;
-#pragma unroll
-        for (int m = 0; m < 8; ++m) {
-            const int z = t + m * 32;
             if (z < Nz) base[(size_t)z * zstride] = cswap(v[m]);
         }
     }
@@ -1313,14 +1159,13 @@ __device__ __forceinline__ bool z_tile_split(const Cx<T> *sin, const T *sg, int 
 // every thread reaches after reading its input; the other spectrum set was
 // last read by the previous tile, before the barriers of its transforms.
 // ---------------------------------------------------------------------
-template <typename T, int L, int FORM = 0>
-__global__ void __launch_bounds__(ZCfg<T, L, FORM>::THREADS, ZCfg<T, L, FORM>::MIN_BLOCKS)
+template <typename T, int L>
+__global__ void __launch_bounds__(ZCfg<T, L>::THREADS, ZCfg<T, L>::MIN_BLOCKS)
 k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw,
              const T *__restrict__ G, const T *__restrict__ Gs, T gscale, int Nz, int My, int Kx, int ntiles,
              unsigned *__restrict__ status, unsigned test_extra_tx)
 {
-    constexpr bool SPLIT = FORM != 0;
-    using C = ZCfg<T, L, FORM>;
+    using C = ZCfg<T, L>;
     static_assert(C::DBX, "lines without room for two exchange buffers take k_z_convolve_pairs");
     constexpr int E = C::E, TX = C::TX, COLS = C::COLS;
     constexpr int Lh = L / 2;
@@ -1375,9 +1220,7 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
     };
 
     using Rad = typename ZShape<T, L>::Rad;
-    // this thread's twiddles, for every tile (when TW_REGS, or split lines)
-    using TwR = std::conditional_t<SPLIT, ZSplitTw<T>, typename ZTwiddles<C::TWR, T, L, E, Rad>::type>;
-    TwR twr;
+    typename ZTwiddles<C::TWR, T, L, E, Rad>::type twr;  // this thread's twiddles, for every tile (when TW_REGS)
     twr.load(tw, t);
     int tile = blockIdx.x, it = 0;
     bool ok = true;
@@ -1398,221 +1241,11 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
         const int pr = tile / ntx, xt = tile - pr * ntx;
         const Cx<T> *sin = reinterpret_cast<const Cx<T> *>(s_in + g * C::IN_GROUP);
         const T *sg = s_g + ((size_t)set * 2 + (pr == 0 ? g : 0)) * C::GBLK;
-        if constexpr (SPLIT)
-            z_tile_split<T, L, FORM, TX>(sin, sg, pr, xt, W, Gs, gscale, Nz, My, Kx, c, g, t, twr, xch,
-                                         [] { return true; });
-        else
-            z_tile<T, L, TX>(sin, sg, pr, xt, W, Gs, gscale, Nz, My, Kx, c, g, t, twr, twz, xch, [] { return true; });
+        z_tile<T, L, TX>(sin, sg, pr, xt, W, Gs, gscale, Nz, My, Kx, c, g, t, twr, twz, xch, [] { return true; });
     }
     if (!ok && tid == 0) {
         // a wait gave up: flag it, then let this tile's copies land (bounded
         // again) before the CTA's shared memory is freed
-        if (status) atomicOr(status, 1u);
-        mbar_wait_bounded(&bar[0], (uint32_t)it & 1u, kCopyWaitNs);
-    }
-}
-
-// ---------------------------------------------------------------------
-// K3 on FP32 512-point lines with packed arithmetic (pf2.cuh): each thread
-// transforms the two lines of its column, k_y and M_y - k_y, as one line of
-// pairs, 8 points per line (512 = 8 x 8 x 8, 64 threads per line pair), so
-// every add, multiply and fused multiply-add of the butterflies, twiddles
-// and spectrum multiply issues once for both lines.  Tiles, copies and
-// waits are those of k_z_convolve; the exchange buffers hold one pair of
-// points (16 bytes) per position and column.
-// ---------------------------------------------------------------------
-struct ZPCfg {
-    static constexpr int L = 512, E = 8, NT = L / E, LH = L / 2;
-    static constexpr int TX = 8;                  // columns per tile (= the spectrum layout's tile width)
-    static constexpr int THREADS = TX * NT;       // one thread per (column, position)
-    static constexpr int NZB = 1, BOXZ = LH;      // one box of 256 planes per line group
-    static constexpr int GBLK = z_spec_block(TX, LH + 1, 4);
-    static constexpr size_t XCH = (size_t)L * TX * sizeof(Cx<pf2>);
-    static constexpr size_t IN_GROUP = (size_t)LH * TX * sizeof(Cx<float>);
-    static constexpr size_t IN_SET = 2 * IN_GROUP;
-    static constexpr size_t G_BLK = (size_t)GBLK * sizeof(float), G_SET = 2 * G_BLK;
-    static constexpr size_t OFF_IN = 2 * XCH, OFF_G = OFF_IN + IN_SET, OFF_BAR = OFF_G + 2 * G_SET;
-    static constexpr size_t SMEM = OFF_BAR + 16;
-    static_assert(SMEM <= 227 * 1024, "packed z tile exceeds shared memory");
-    static_assert(TX == ZCfg<float, 512>::TX, "the packed z pass reads the spectrum layout of the z pass");
-    static_assert(XCH % 128 == 0 && IN_GROUP % 128 == 0 && G_BLK % 16 == 0, "copy destinations");
-};
-
-// Stage twiddles of one thread, as pairs: W_64^{r (t mod 8)} (second
-// stage) and W_512^{r t} (third), r = 1..7.
-struct ZPTw {
-    PTw w2[7], w3[7];
-    __device__ __forceinline__ void load(const Cx<float> *__restrict__ tw, int t)
-    {
-#pragma unroll
-        for (int r = 1; r < 8; ++r) {
-            w2[r - 1] = ptw(tw[8 * r * (t & 7)]);
-            w3[r - 1] = ptw(tw[r * t]);
-        }
-    }
-};
-
-// 512 = 8 x 8 x 8 on pairs: first stage from `HALF` (inputs 4..7 zero)
-// or full, exchanges through xch, bins t + 64 r in natural order after.
-template <bool HALF, typename Xch>
-__device__ __forceinline__ void zp_fft(PCx (&v)[8], int t, const ZPTw &tw, Xch &xch)
-{
-    if constexpr (HALF)
-        pdft8_half(v);
-    else
-        pdft8(v);
-    xch.template exchange<1, 8>(v, t);
-#pragma unroll
-    for (int r = 1; r < 8; ++r) v[r] = pcmul(v[r], tw.w2[r - 1]);
-    pdft8(v);
-    xch.template exchange<8, 8>(v, t);
-#pragma unroll
-    for (int r = 1; r < 8; ++r) v[r] = pcmul(v[r], tw.w3[r - 1]);
-    pdft8(v);
-}
-
-template <typename Xch>
-__device__ __forceinline__ void z_tile_packed(const Cx<float> *sinA, const Cx<float> *sinB, const float *sgA,
-                                              const float *sgB, int pr, int xt, Cx<float> *__restrict__ W,
-                                              const float *__restrict__ Gs, float gscale, int Nz, int My, int Kx,
-                                              int c, int t, const ZPTw &tw, Xch &xch)
-{
-    using C = ZPCfg;
-    constexpr int L = C::L, NT = C::NT, TX = C::TX, Lh = C::LH;
-    const int kyA = pr, kyB = pr == 0 ? My / 2 : My - pr;
-    const int kx = xt * TX + c;
-
-    // z < L/2 of both lines (zeros past Nz from the staged boxes)
-    PCx v[8];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        const Cx<float> a = sinA[(t + m * NT) * TX + c], b = sinB[(t + m * NT) * TX + c];
-        v[m] = {pf2(a.x, b.x), pf2(a.y, b.y)};
-    }
-    zp_fft<true>(v, t, tw, xch);
-
-    // spectrum at kz = t + 64 m: kz' = kz below L/2, L - kz from L/2 on
-    auto gval = [&](const float *sg, int m) -> float {
-        return m < 4 ? sg[(t + m * NT) * TX + c] : sg[(L - t - m * NT) * TX + c];
-    };
-    if (xt == 0) {
-        // the packed column kx = 0 / Mx/2 also needs the partner bins
-        // (-ky, -kz): the other line's (for pr = 0, its own) at L - kz
-        PCx *sp = xch.free_buf();
-        if (c == 0) {
-#pragma unroll
-            for (int m = 0; m < 8; ++m) sp[(t + m * NT) * TX] = v[m];
-        }
-        __syncthreads();
-        if (c == 0) {
-            const float *gsA = Gs + (size_t)kyA * (Lh + 1);
-            const float *gsB = Gs + (size_t)(pr == 0 ? My / 2 : pr) * (Lh + 1);
-#pragma unroll
-            for (int m = 0; m < 8; ++m) {
-                const int kz = t + m * NT;
-                const int kzp = kz <= L - kz ? kz : L - kz;
-                const PCx q = sp[(kz == 0 ? 0 : L - kz) * TX];
-                const pf2 px = pr == 0 ? q.x : pf2(q.x.v.y, q.x.v.x);  // partner, re
-                const pf2 py = pr == 0 ? q.y : pf2(q.y.v.y, q.y.v.x);  // partner, im (conjugated below)
-                const pf2 gp(gval(sgA, m), gval(sgB, m));
-                const pf2 gm(gsA[kzp], gsB[kzp]), ngm(-gsA[kzp], -gsB[kzp]);
-                v[m] = {pf2_fma(px, gm, v[m].x * gp), pf2_fma(py, ngm, v[m].y * gp)};
-            }
-        }
-        __syncthreads();
-    }
-    if (!(xt == 0 && c == 0)) {
-#pragma unroll
-        for (int m = 0; m < 8; ++m) {
-            const pf2 g(gval(sgA, m), gval(sgB, m));
-            v[m] = {v[m].x * g, v[m].y * g};
-        }
-    }
-
-    // inverse: swap(FFT(swap(.))); keep z < L/2, times the width scale
-#pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = {v[m].y, v[m].x};
-    zp_fft<false>(v, t, tw, xch);
-    if (kx < Kx) {
-        const pf2 gs((double)gscale);
-        Cx<float> *baseA = W + (size_t)kyA * Kx + kx, *baseB = W + (size_t)kyB * Kx + kx;
-        const size_t zstride = (size_t)My * Kx;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const int z = t + m * NT;
-            if (z < Nz) {
-                const pf2 re = v[m].y * gs, im = v[m].x * gs;
-                baseA[(size_t)z * zstride] = {re.v.x, im.v.x};
-                baseB[(size_t)z * zstride] = {re.v.y, im.v.y};
-            }
-        }
-    }
-}
-
-// The persistent kernel: tiles, copies and bounded waits as k_z_convolve
-// (two exchange buffers, one input staging set, two spectrum sets).
-template <int L_>
-__global__ void __launch_bounds__(ZPCfg::THREADS, 1)
-k_z_packed(const __grid_constant__ CUtensorMap tmW, Cx<float> *__restrict__ W, const Cx<float> *__restrict__ tw,
-           const float *__restrict__ G, const float *__restrict__ Gs, float gscale, int Nz, int My, int Kx,
-           int ntiles, unsigned *__restrict__ status, unsigned test_extra_tx)
-{
-    using C = ZPCfg;
-    static_assert(L_ == C::L, "packed z pass: 512-point lines");
-    constexpr int TX = C::TX, L = C::L, Lh = C::LH;
-    extern __shared__ __align__(128) unsigned char zsmem[];
-    PCx *sm = reinterpret_cast<PCx *>(zsmem);
-    unsigned char *s_in = zsmem + C::OFF_IN;
-    float *s_g = reinterpret_cast<float *>(zsmem + C::OFF_G);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(zsmem + C::OFF_BAR);
-    const int tid = threadIdx.x;
-    const int c = tid % TX;  // a warp: 8 columns x 4 positions, so each
-    const int t = tid / TX;  // quarter-warp writes one 128-byte row
-    const int ntx = (Kx + TX - 1) / TX;
-    const ZSpecLayout lay{TX, ntx, Lh + 1, C::GBLK};
-    if (smem_addr(zsmem) & 127u) {
-        if (tid == 0 && status) atomicOr(status, 2u);
-        return;
-    }
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init_fence();
-    }
-    __syncthreads();
-    auto issue = [&](int tile, int set, uint32_t extra) {
-        const int pr = tile / ntx, xt = tile - pr * ntx;
-        const int ky1 = pr == 0 ? My / 2 : My - pr;
-        mbar_arrive_expect_tx(&bar[0], (uint32_t)(C::IN_SET + (pr == 0 ? 2 : 1) * C::G_BLK) + extra);
-        tma_load_3d(s_in, &tmW, xt * TX, pr, 0, &bar[0]);
-        tma_load_3d(s_in + C::IN_GROUP, &tmW, xt * TX, ky1, 0, &bar[0]);
-        float *gdst = s_g + (size_t)set * 2 * C::GBLK;
-        bulk_load(gdst, G + lay.block(pr, xt), (uint32_t)C::G_BLK, &bar[0]);
-        if (pr == 0) bulk_load(gdst + C::GBLK, G + lay.block(My / 2, xt), (uint32_t)C::G_BLK, &bar[0]);
-    };
-    ZPTw twr;
-    twr.load(tw, t);
-    int tile = blockIdx.x, it = 0;
-    bool ok = true;
-    if (tid == 0 && tile < ntiles) issue(tile, 0, test_extra_tx);
-    for (; tile < ntiles; tile += gridDim.x, ++it) {
-        const int next = tile + gridDim.x;
-        const int set = it & 1;
-        auto hook = [&](int k) {
-            if (k == 0 && tid == 0 && next < ntiles) issue(next, set ^ 1, 0u);
-        };
-        ZXch<pf2, L, C::E, TX, false, true, decltype(hook)> xch{sm, c, hook};
-        if (!__syncthreads_and(mbar_wait_bounded(&bar[0], (uint32_t)it & 1u, kCopyWaitNs))) {
-            ok = false;
-            break;
-        }
-        const int pr = tile / ntx, xt = tile - pr * ntx;
-        const Cx<float> *sinA = reinterpret_cast<const Cx<float> *>(s_in);
-        const Cx<float> *sinB = reinterpret_cast<const Cx<float> *>(s_in + C::IN_GROUP);
-        const float *sgA = s_g + (size_t)set * 2 * C::GBLK;
-        const float *sgB = pr == 0 ? sgA + C::GBLK : sgA;
-        z_tile_packed(sinA, sinB, sgA, sgB, pr, xt, W, Gs, gscale, Nz, My, Kx, c, t, twr, xch);
-    }
-    if (!ok && tid == 0) {
         if (status) atomicOr(status, 1u);
         mbar_wait_bounded(&bar[0], (uint32_t)it & 1u, kCopyWaitNs);
     }

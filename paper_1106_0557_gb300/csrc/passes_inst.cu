@@ -4,10 +4,7 @@
 //   -DISOFFT_GROUP=1|2|3|4       1: x passes (K1, K5), 2: y passes (K2, K4),
 //                                3: z pass (K3), 4: fused x+y passes
 // so that the instantiations compile in parallel.
-#include <stdlib.h>
-
 #include <atomic>
-#include <type_traits>
 
 #include "launch.h"
 #include "passes.cuh"
@@ -330,48 +327,14 @@ template cudaError_t launch_yx_inverse<Real>(int, void *, In<Real> *, const void
 // The z pass: k_z_convolve on tiles of TX columns, or k_z_convolve_pairs on
 // pairs of adjacent tiles (one box of 2 TX columns) where the line leaves no
 // room for two exchange buffers.
-// The z tile form (ZCfg FORM) of a line length: FP32 512-point lines run a
-// split form (two exchanges per tile, z_tile_split); ISOFFT_Z_FORM=0|1|2
-// in the environment picks one (read once per process: the cached spectrum
-// layout follows the form's tile width).
 template <typename T, int L>
-constexpr bool z_split_form = std::is_same<T, float>::value && L == 512;
-static int z_form_env()
+static cudaError_t run_z(void *W, const void *tw, const T *G, const T *Gs, T gscale, int Nz, int My, int Kx,
+                         unsigned *status, unsigned test_extra_tx, cudaStream_t st)
 {
-    static const int f = [] {
-        const char *e = getenv("ISOFFT_Z_FORM");
-        if (e && e[0] >= '0' && e[0] <= '3' && e[1] == 0) return e[0] - '0';
-        return 0;
-    }();
-    return f;
-}
-template <typename T, int L>
-static int z_form()
-{
-    if constexpr (z_split_form<T, L>)
-        return z_form_env();
-    else
-        return 0;
-}
-
-// Tile width of the form the z pass runs for this length.
-template <typename T, int L>
-static int z_tile_of()
-{
-    if constexpr (z_split_form<T, L>) {
-        if (z_form<T, L>() == 2) return ZCfg<T, L, 2>::TX;
-    }
-    return ZCfg<T, L>::TX;
-}
-
-template <typename T, int L, int FORM>
-static cudaError_t run_z_form(void *W, const void *tw, const T *G, const T *Gs, T gscale, int Nz, int My, int Kx,
-                              unsigned *status, unsigned test_extra_tx, cudaStream_t st)
-{
-    using C = ZCfg<T, L, FORM>;
+    using C = ZCfg<T, L>;
     constexpr auto kernel = []() {
         if constexpr (C::DBX)
-            return k_z_convolve<T, L, FORM>;
+            return k_z_convolve<T, L>;
         else
             return k_z_convolve_pairs<T, L>;
     }();
@@ -404,55 +367,6 @@ static cudaError_t run_z_form(void *W, const void *tw, const T *G, const T *Gs, 
     count_launch();
     return cudaGetLastError();
 }
-// The packed z pass (k_z_packed) on FP32 512-point lines.
-template <typename T>
-static cudaError_t run_z_packed(void *W, const void *tw, const T *G, const T *Gs, T gscale, int Nz, int My, int Kx,
-                                unsigned *status, unsigned test_extra_tx, cudaStream_t st)
-{
-    if constexpr (!std::is_same<T, float>::value) {
-        return cudaErrorInvalidValue;
-    } else {
-        using C = ZPCfg;
-        static std::atomic<uint64_t> done{0};
-        static std::atomic<int> slots{0};
-        if (((uintptr_t)W & 15) || ((uintptr_t)G & 15)) return cudaErrorMisalignedAddress;
-        cudaError_t e = ensure_smem(k_z_packed<512>, C::SMEM, done);
-        if (e != cudaSuccess) return e;
-        const int ntx = (Kx + C::TX - 1) / C::TX;
-        const int units = ntx * (My / 2);
-        int grid = resident_ctas(k_z_packed<512>, C::THREADS, C::SMEM, slots);
-        if (grid <= 0) return cudaErrorInvalidConfiguration;
-        if (grid > units) grid = units;
-        EncodeTiledFn encode = encode_tiled();
-        if (!encode) return cudaErrorNotSupported;
-        CUtensorMap map;
-        const cuuint64_t dims[3] = {(cuuint64_t)Kx, (cuuint64_t)My, (cuuint64_t)Nz};
-        const cuuint64_t strides[2] = {(cuuint64_t)Kx * sizeof(Cx<float>), (cuuint64_t)My * Kx * sizeof(Cx<float>)};
-        const cuuint32_t box[3] = {(cuuint32_t)C::TX, 1u, (cuuint32_t)C::BOXZ};
-        const cuuint32_t estr[3] = {1u, 1u, 1u};
-        if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, W, dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-            return cudaErrorInvalidValue;
-        k_z_packed<512><<<grid, C::THREADS, C::SMEM, st>>>(map, (Cx<float> *)W, (const Cx<float> *)tw, G, Gs, gscale, Nz,
-                                                       My, Kx, units, status, test_extra_tx);
-        count_launch();
-        return cudaGetLastError();
-    }
-}
-
-template <typename T, int L>
-static cudaError_t run_z(void *W, const void *tw, const T *G, const T *Gs, T gscale, int Nz, int My, int Kx,
-                         unsigned *status, unsigned test_extra_tx, cudaStream_t st)
-{
-    if constexpr (z_split_form<T, L>) {
-        const int f = z_form<T, L>();
-        if (f == 3) return run_z_packed(W, tw, G, Gs, gscale, Nz, My, Kx, status, test_extra_tx, st);
-        if (f == 1) return run_z_form<T, L, 1>(W, tw, G, Gs, gscale, Nz, My, Kx, status, test_extra_tx, st);
-        if (f == 2) return run_z_form<T, L, 2>(W, tw, G, Gs, gscale, Nz, My, Kx, status, test_extra_tx, st);
-    }
-    return run_z_form<T, L, 0>(W, tw, G, Gs, gscale, Nz, My, Kx, status, test_extra_tx, st);
-}
 template <typename R_>
 cudaError_t launch_z_convolve(int L, void *W, const void *tw, const R_ *G, const R_ *Gs, R_ gscale,
                                   int Nz, int My, int Kx, unsigned *status, unsigned test_extra_tx, cudaStream_t st)
@@ -470,7 +384,7 @@ int z_tile_for(int L)
 {
     switch (L) {
 #define X_(n) \
-    case n: return z_tile_of<R_, n>();
+    case n: return ZCfg<R_, n>::TX;
         ISOFFT_COL_LENGTHS(X_)
 #undef X_
     default: return 0;

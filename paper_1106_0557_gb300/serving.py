@@ -14,11 +14,19 @@ Memory accounting (the admission budget):
   mesh and dtype);
 * each in-flight request counts its output buffer.
 
+Plan creation (the Green's spectrum on a cache miss, the y-pass timing) can
+run off the admission path (``async_plans=True``): a request whose (N, dtype)
+has no idle plan reserves the plan's bytes and has it built on a background
+thread, and stays queued while requests behind it whose plans are ready are
+admitted (within a look-ahead window).  Its latency then includes the plan's
+creation: misses are served cold, not hidden by a warm-up.
+
 The device side is behind a small backend interface (``TorchBackend`` here;
 tests substitute a fake one), so the admission and pooling logic is plain
 host code.
 """
 import collections
+import concurrent.futures as cf
 import math
 import time
 
@@ -89,25 +97,58 @@ class PlanPool:
 
 
 class Server:
-    """Admission by memory budget over `slots` concurrent streams."""
+    """Admission by memory budget over `slots` concurrent streams.
 
-    def __init__(self, backend, budget_bytes=120e9, slots=8, keep_outputs=False):
+    on_finish: called with each completed request before its output is
+    dropped (unless keep_outputs), e.g. to check or copy it.
+    async_plans: create missing plans on a background thread; admission then
+    looks at up to `lookahead` queued requests for one whose plan is ready.
+    """
+
+    def __init__(self, backend, budget_bytes=120e9, slots=8, keep_outputs=False, on_finish=None,
+                 async_plans=False, lookahead=64):
         self.backend = backend
         self.budget = float(budget_bytes)
         self.slots = int(slots)
         self.keep_outputs = keep_outputs
+        self.on_finish = on_finish
         self.pool = PlanPool(backend)
         self.inflight_bytes = 0
         self.peak_bytes = 0
+        self.async_plans = async_plans
+        self.lookahead = int(lookahead) if async_plans else 1
+        self.pending = {}          # key -> (future, reserved bytes)
+        self.pending_bytes = 0
+        self.factory = cf.ThreadPoolExecutor(max_workers=1) if async_plans else None
 
     def used(self):
-        return self.pool.bytes + self.backend.spectrum_bytes() + self.inflight_bytes
+        return self.pool.bytes + self.backend.spectrum_bytes() + self.inflight_bytes + self.pending_bytes
+
+    def _collect_plans(self):
+        """Move finished background plan creations into the pool."""
+        for key, (fut, reserved) in list(self.pending.items()):
+            if not fut.done():
+                continue
+            del self.pending[key]
+            self.pending_bytes -= reserved
+            try:
+                plan, nbytes = fut.result()
+            except native.IsofftError as e:
+                self.failed[key] = e.status
+                continue
+            self.pool.add(plan, nbytes)
+            self.pool.release(key, plan)
 
     def _admit(self, req, slot):
         key = (req.n, req.dtype)
         out_bytes = self.backend.output_bytes(req.n, req.dtype)
+        if key in self.failed:
+            req.status = "error:%d" % self.failed.pop(key)
+            return "reject"
         plan = self.pool.take_idle(key)
         if plan is None:
+            if key in self.pending:
+                return "pending"
             need = self.backend.plan_bytes(req.n, req.dtype) + out_bytes
             if need > self.budget:
                 req.status = "budget_exceeded"
@@ -115,6 +156,12 @@ class Server:
             while self.used() + need > self.budget:
                 if not self.pool.evict_one():
                     return "wait"
+            if self.async_plans:
+                reserved = need - out_bytes
+                self.pending[key] = (self.factory.submit(self.backend.create_plan, req.n, req.dtype), reserved)
+                self.pending_bytes += reserved
+                self.peak_bytes = max(self.peak_bytes, self.used())
+                return "pending"
             try:
                 plan, nbytes = self.backend.create_plan(req.n, req.dtype)
             except native.IsofftError as e:
@@ -141,6 +188,8 @@ class Server:
         self.inflight_bytes -= self.backend.output_bytes(req.n, req.dtype)
         self.pool.release((req.n, req.dtype), req.plan)
         self.backend.retire(req)
+        if self.on_finish is not None:
+            self.on_finish(req)
         if not self.keep_outputs:
             req.out = None
 
@@ -149,9 +198,10 @@ class Server:
         completion; returns them with admitted/finished times and status."""
         clock = clock or time.perf_counter
         reqs = sorted(requests, key=lambda r: r.arrival)
-        queue = collections.deque()
+        queue = []
         free = list(range(self.slots))
         inflight = {}
+        self.failed = {}
         i = 0
         done = 0
         t0 = clock()
@@ -168,11 +218,18 @@ class Server:
                     free.append(slot)
                     done += 1
                     progressed = True
-            while queue and free:
-                req = queue[0]
+            if self.pending:
+                self._collect_plans()
+            # admission: the first `lookahead` queued requests in arrival
+            # order; one waiting for memory stops the scan (nothing behind
+            # it may take the memory it waits for), one whose plan is being
+            # built is passed over
+            j = 0
+            while j < len(queue) and j < self.lookahead and free:
+                req = queue[j]
                 slot = free[-1]
                 verdict = self._admit(req, slot)
-                if verdict == "wait" and not inflight:
+                if verdict == "wait" and not inflight and not self.pending:
                     # nothing will complete to make room: drop the cached
                     # spectra no plan references, then try once more
                     self.backend.trim_spectra()
@@ -182,7 +239,10 @@ class Server:
                         verdict = "reject"
                 if verdict == "wait":
                     break
-                queue.popleft()
+                if verdict == "pending":
+                    j += 1
+                    continue
+                queue.pop(j)
                 if verdict == "reject":
                     req.finished = clock() - t0
                     done += 1
@@ -192,13 +252,24 @@ class Server:
                     inflight[slot] = req
                 progressed = True
             if not progressed:
-                if not inflight and not queue and i < len(reqs):
+                if not inflight and not queue and not self.pending and i < len(reqs):
                     self.backend.wait_until(reqs[i].arrival + t0, clock)
                 elif idle_sleep:
                     time.sleep(idle_sleep)
         return reqs
 
     def close(self):
+        if self.factory is not None:
+            for fut, _ in self.pending.values():
+                try:
+                    plan, _ = fut.result()
+                    self.backend.destroy_plan(plan)
+                except native.IsofftError:
+                    pass
+            self.pending.clear()
+            self.pending_bytes = 0
+            self.factory.shutdown(wait=True)
+            self.factory = None
         self.pool.close()
 
 

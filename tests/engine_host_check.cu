@@ -1,9 +1,6 @@
 // engine_host_check.cu -- runs the FFT engine's stage code (fft_engine.cuh,
 // host-callable) on the CPU against a direct DFT in long double, for every
-// line shape the passes instantiate, in FP32, FP64 and float pairs.  It also
-// runs the split 512-point z line (radix 32 split over two thread halves,
-// then radix 16; passes.cuh z_tile_split) through the same building blocks
-// and checks the convolution it computes against a direct one.
+// line shape the passes instantiate, in FP32, FP64 and float pairs.
 //
 // Built and run by tests/test_engine_host.py (host code only; no GPU).
 // Prints one line per case: "<name> <max error / max |X|>".
@@ -122,99 +119,6 @@ static void check(const char *tag, const char *kind, unsigned seed)
     check_shape<T, L, SH::E, typename SH::Rad, true>(name, seed + 1);
 }
 
-// The split 512-point z line: forward transform of a half-zero line,
-// multiply by a real spectrum g, inverse, keep z < 256 -- against the direct
-// convolution sum.
-template <typename T>
-static void check_split(const char *tag)
-{
-    constexpr int L = 512;
-    srand(7);
-    std::vector<CL> xl(L, 0), gl(L);
-    std::vector<Cx<T>> x(L);
-    for (int i = 0; i < L; ++i) {
-        double a = i < 256 ? (double)rand() / RAND_MAX - 0.5 : 0.0;
-        double b = i < 256 ? (double)rand() / RAND_MAX - 0.5 : 0.0;
-        x[i] = {from_d<T>(a), from_d<T>(b)};
-        xl[i] = CL(to_ld(x[i].x), to_ld(x[i].y));
-    }
-    std::vector<T> g(L);
-    for (int k = 0; k <= L / 2; ++k) {
-        const double v = (double)rand() / RAND_MAX - 0.5;
-        g[k] = from_d<T>(v);
-        g[(L - k) % L] = g[k];
-    }
-    for (int k = 0; k < L; ++k) gl[k] = to_ld(g[k]);
-    const std::vector<Cx<T>> tw = table<T>(L);
-    auto swp = [](Cx<T> a) { return cswap(a); };
-    std::vector<Cx<T>> buf(L), X(L), buf2(L), out(256);
-    // forward, radix-32 half: butterfly j = t mod 16, even/odd outputs
-    for (int t = 0; t < 32; ++t) {
-        const int j = t & 15;
-        const bool odd = t >= 16;
-        Cx<T> v[16];
-        for (int m = 0; m < 16; ++m) v[m] = x[j + 16 * m];
-        if (odd) {
-            v[1] = mul_root32<T, 1>(v[1]);   v[2] = mul_root32<T, 2>(v[2]);   v[3] = mul_root32<T, 3>(v[3]);
-            v[4] = mul_root32<T, 4>(v[4]);   v[5] = mul_root32<T, 5>(v[5]);   v[6] = mul_root32<T, 6>(v[6]);
-            v[7] = mul_root32<T, 7>(v[7]);   v[8] = mul_root32<T, 8>(v[8]);   v[9] = mul_root32<T, 9>(v[9]);
-            v[10] = mul_root32<T, 10>(v[10]); v[11] = mul_root32<T, 11>(v[11]); v[12] = mul_root32<T, 12>(v[12]);
-            v[13] = mul_root32<T, 13>(v[13]); v[14] = mul_root32<T, 14>(v[14]); v[15] = mul_root32<T, 15>(v[15]);
-        }
-        Dft<T, 16>::run(v);
-        for (int q = 0; q < 16; ++q) buf[32 * j + 2 * q + (odd ? 1 : 0)] = v[q];
-    }
-    // forward, radix-16 stage with W_512^{r t}
-    for (int t = 0; t < 32; ++t) {
-        Cx<T> v[16];
-        for (int r = 0; r < 16; ++r) v[r] = buf[t + 32 * r];
-        for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], tw[r * t]);
-        Dft<T, 16>::run(v);
-        for (int r = 0; r < 16; ++r) X[t + 32 * r] = v[r];
-    }
-    // spectrum multiply, inverse radix-16 stage, twiddles before the exchange
-    for (int t = 0; t < 32; ++t) {
-        Cx<T> v[16];
-        for (int r = 0; r < 16; ++r) v[r] = swp(cscale(X[t + 32 * r], g[t + 32 * r]));
-        Dft<T, 16>::run(v);
-        for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], tw[r * t]);
-        for (int r = 0; r < 16; ++r) buf2[16 * t + r] = v[r];
-    }
-    // inverse radix-32 stage, outputs z < 256
-    for (int t = 0; t < 32; ++t) {
-        const int j = t & 15;
-        const bool odd = t >= 16;
-        Cx<T> v[16];
-        for (int r = 0; r < 16; ++r)
-            v[r] = odd ? csub(buf2[j + 16 * r], buf2[j + 16 * r + 256]) : cadd(buf2[j + 16 * r], buf2[j + 16 * r + 256]);
-        if (odd) {
-            v[1] = mul_root32<T, 1>(v[1]);   v[2] = mul_root32<T, 2>(v[2]);   v[3] = mul_root32<T, 3>(v[3]);
-            v[4] = mul_root32<T, 4>(v[4]);   v[5] = mul_root32<T, 5>(v[5]);   v[6] = mul_root32<T, 6>(v[6]);
-            v[7] = mul_root32<T, 7>(v[7]);   v[8] = mul_root32<T, 8>(v[8]);   v[9] = mul_root32<T, 9>(v[9]);
-            v[10] = mul_root32<T, 10>(v[10]); v[11] = mul_root32<T, 11>(v[11]); v[12] = mul_root32<T, 12>(v[12]);
-            v[13] = mul_root32<T, 13>(v[13]); v[14] = mul_root32<T, 14>(v[14]); v[15] = mul_root32<T, 15>(v[15]);
-        }
-        Dft<T, 16>::run(v);
-        for (int s = 0; s < 8; ++s) out[t + 32 * s] = swp(v[s]);
-    }
-    // direct: y[z] = sum_k X[k] g[k] e^{+2 pi i k z / L}, X the DFT of x
-    std::vector<CL> Xl(L);
-    for (int k = 0; k < L; ++k) {
-        CL s = 0;
-        for (int jj = 0; jj < L; ++jj) s += xl[jj] * root(L, (long)jj * k);
-        Xl[k] = s * gl[k];
-    }
-    long double emax = 0, ymax = 0;
-    for (int z = 0; z < 256; ++z) {
-        CL s = 0;
-        for (int k = 0; k < L; ++k) s += Xl[k] * std::conj(root(L, (long)k * z));
-        const CL got(to_ld(out[z].x), to_ld(out[z].y));
-        emax = fmaxl(emax, std::abs(got - s));
-        ymax = fmaxl(ymax, std::abs(s));
-    }
-    printf("zsplit_%s_512 %.3Le\n", tag, emax / ymax);
-}
-
 template <typename T>
 static void check_all(const char *tag)
 {
@@ -245,7 +149,6 @@ static void check_all(const char *tag)
     check<T, XShapeF<T, 1152>, 1152>(tag, "xf", 21);
     check<T, XShape<T, 1152>, 1152>(tag, "x", 22);
 #undef SH
-    check_split<T>(tag);
 }
 
 int main()
