@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--no-paper-scale", action="store_true",
                     help="skip the 1152^3 solve (the paper's largest ladder point)")
@@ -73,7 +73,6 @@ def pass_bytes(N, M, es):
         "z_convolve": 2 * wall + g,
         "y_inverse": wall + wy,
         "x_inverse": wy + src,
-        "_xy": src + wall,  # fused x+y (or y+x): source or potential plus the workspace after y
     }
 
 
@@ -82,19 +81,10 @@ KERNELS = {"x_forward": "k_x_forward", "y_forward": "k_y_forward", "z_convolve":
            "y_inverse": "k_y_inverse", "x_inverse": "k_x_inverse"}
 
 
-def kernel_times(passes, nbytes, fused):
-    """Mean device ms, algorithmic bytes and GB/s per kernel.  A plan with
-    My = Mx runs the x and y passes fused (k_xy_forward, k_yx_inverse); its
-    y-forward and x-inverse entries are then 0 and the fused kernel's bytes
-    are the source read plus the full workspace write (and the reverse).
-    `fused` says which layout the plan ran."""
+def kernel_times(passes, nbytes):
+    """Mean device ms, algorithmic bytes and GB/s per kernel."""
     out = {}
-    if fused:
-        items = [("k_xy_forward", passes[0], nbytes["_xy"]), ("k_z_convolve", passes[2], nbytes["z_convolve"]),
-                 ("k_yx_inverse", passes[3], nbytes["_xy"])]
-    else:
-        items = [(KERNELS[p], passes[i], nbytes[p]) for i, p in enumerate(PASSES)]
-    for name, ms, b in items:
+    for name, ms, b in [(KERNELS[p], passes[i], nbytes[p]) for i, p in enumerate(PASSES)]:
         out[name] = {"ms": ms, "bytes": b, "gbs": b / (ms / 1e3) / 1e9 if ms > 0 else 0.0}
     return out
 
@@ -362,21 +352,19 @@ def run_batch(steps=50, count=64):
     submitted without a graph."""
     import torch
 
-    from paper_1106_0557_gb300 import sources
+    from paper_1106_0557_gb300 import native, sources
     from paper_1106_0557_gb300.solver import BatchGraph, Plan, submit_batch
     wl = sources.ragged_batch(count)
     plans = [Plan(w.N, w.h, "f32") for w in wl]
     srcs = [torch.from_numpy(w.source(np.float32)).cuda() for w in wl]
     outs = [torch.empty_like(x) for x in srcs]
     nbytes = 0
-    fused = os.environ.get("ISOFFT_FUSE_XY") == "1"  # the fused x+y passes are opt-in
     for p, w in zip(plans, wl):
         b = pass_bytes(w.N, p.padded_shape, 4)
-        if fused and p.padded_shape[0] == p.padded_shape[1]:
-            nbytes += 2 * b["_xy"] + b["z_convolve"]
-        else:
-            nbytes += sum(b[k] for k in PASSES)
-    res = {"grids": count, "workload": "ragged batch, each axis from {32,48,64,96,128}, seed = grid index"}
+        nbytes += sum(b[k] for k in PASSES)
+    res = {"grids": count, "workload": "ragged batch, each axis from {32,48,64,96,128}, seed = grid index",
+           "how": "one launch per pass over a table of every grid's work items" if
+                  os.environ.get("ISOFFT_BATCH_FUSED", "1") != "0" else "per-grid passes on 8 library streams"}
     for mode in ("graph", "submit"):
         if mode == "graph":
             bg = BatchGraph(plans, srcs, outs)
@@ -387,6 +375,10 @@ def run_batch(steps=50, count=64):
         for _ in range(3):
             run()
         torch.cuda.synchronize()
+        l0 = native.ipf_launch_count()
+        run()
+        torch.cuda.synchronize()
+        launches = native.ipf_launch_count() - l0
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(steps):
@@ -395,19 +387,25 @@ def run_batch(steps=50, count=64):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
         res[mode] = {"ms_per_batch": round(ms, 4), "solves_per_s": round(count / (ms / 1e3), 1),
-                     "hbm_gbs_algorithmic": round(nbytes / (ms / 1e3) / 1e9, 1)}
+                     "hbm_gbs_algorithmic": round(nbytes / (ms / 1e3) / 1e9, 1),
+                     "launches_per_batch": None if mode == "graph" else launches}
     for p in plans:
         p.close()
     return res
 
 
 def run_serving(n_requests, slots, fp64_class="df64"):
-    """Config-5 style serving: cubic N log-uniform in [32, 384], 70 % FP32
-    (tolerance 1e-5) / 30 % FP64-class (tolerance 1e-12, served with the
-    `fp64_class` dtype), HBM budget 120 GB.  Saturated throughput (all
-    requests at t=0), then Poisson arrivals at 0.5, 0.8 and 0.95 x that rate
-    for p50/p99 latency (0.8 headlined); and the FP32 class served vs the same shapes solved one at a
-    time in plain FP64."""
+    """Config 5: cubic N log-uniform in [32, 384], 70 % FP32 (tolerance
+    1e-5) / 30 % FP64 class (tolerance 1e-12, served with the `fp64_class`
+    dtype), HBM budget 120 GB, continuous batching over `slots` streams with
+    plans created on the server's background thread.
+    * Saturated throughput: all requests at t = 0, warm (after one pass).
+    * Poisson arrivals at 0.5, 0.8 and 0.95 x that rate (0.8 headlined), each
+      load point from a cold start: a fresh server and an empty spectrum
+      cache, so every shape's first request waits for its plan and Green's
+      spectrum to be built (their latency counts).
+    * The FP32 class served vs the same shapes solved one at a time in plain
+      FP64 (plan set-up excluded)."""
     import torch
 
     from paper_1106_0557_gb300 import native, serving, sources
@@ -417,27 +415,41 @@ def run_serving(n_requests, slots, fp64_class="df64"):
     be = serving.TorchBackend(slots=slots)
     reqs = mk(np.zeros(len(spec)))
     be.prepare(reqs)
-    be.warm_spectra(reqs)
-    srv = serving.Server(be, budget_bytes=120e9, slots=slots)
+    srv = serving.Server(be, budget_bytes=120e9, slots=slots, async_plans=True)
+    serving.saturated_throughput(srv, be, reqs)  # warm-up pass: plans and spectra
     sat = serving.saturated_throughput(srv, be, reqs)
-    # Poisson arrivals at 0.5, 0.8 and 0.95 x the saturated rate; 0.8 is the
-    # headline
+    peak = srv.peak_bytes
+    srv.close()
     sweep = []
+    cold = {}
     for load in (0.5, 0.8, 0.95):
         r = load * sat["solves_per_s"]
+        native.ipf_greens_cache_trim(0)
+        srv = serving.Server(be, budget_bytes=120e9, slots=slots, async_plans=True)
         rq = mk(serving.poisson_arrivals(len(spec), r, seed=1))
         srv.run(rq)
+        peak = max(peak, srv.peak_bytes)
+        srv.close()
         st = serving.latency_stats(rq)
+        # requests that found no plan of their shape: the first of each shape
+        seen, first = set(), []
+        for q in sorted(rq, key=lambda q: q.arrival):
+            if (q.n, q.dtype) not in seen:
+                seen.add((q.n, q.dtype))
+                first.append(q.latency)
         sweep.append({"load": load, "rate": round(r, 1), "p50_ms": round(st["p50_ms"], 3),
-                      "p99_ms": round(st["p99_ms"], 3), "solves_per_s": round(st["solves_per_s"], 1)})
+                      "p99_ms": round(st["p99_ms"], 3), "solves_per_s": round(st["solves_per_s"], 1),
+                      "cold_shapes": len(first), "cold_p50_ms": round(float(np.percentile(first, 50)) * 1e3, 3)})
         if load == 0.8:
             rate, lat = r, st
-    # FP32 class served (saturated) vs plain unbatched FP64 on the same shapes
-    sub = [r for r in reqs if r.dtype == "f32"][:300]
+    # FP32 class served (saturated, warm) vs plain unbatched FP64 on the same shapes
+    sub = [q for q in reqs if q.dtype == "f32"][:300]
+    srv = serving.Server(be, budget_bytes=120e9, slots=slots, async_plans=True)
+    serving.saturated_throughput(srv, be, sub)
     served32 = serving.saturated_throughput(srv, be, sub)
     srv.close()
     # plain path: one FP64 solve at a time on one stream, plan set-up excluded
-    shapes = [r.n for r in sub]
+    shapes = [q.n for q in sub]
     plain_s = 0.0
     stream = torch.cuda.current_stream().cuda_stream
     for n in shapes:
@@ -453,13 +465,16 @@ def run_serving(n_requests, slots, fp64_class="df64"):
     plain64 = len(shapes) / plain_s
     return {"requests": len(spec), "slots": slots, "budget_gb": 120,
             "mix": "cubic N log-uniform [32,384], 70%% f32 / 30%% FP64-class served as %s" % fp64_class,
+            "plans": "created on a background thread; admission looks ahead past requests whose plan is "
+                     "being built",
             "saturated_solves_per_s": round(sat["solves_per_s"], 1),
             "poisson_rate": round(rate, 1), "p50_ms": round(lat["p50_ms"], 3), "p99_ms": round(lat["p99_ms"], 3),
-            "solves_per_s": round(lat["solves_per_s"], 1), "load_sweep": sweep,
+            "solves_per_s": round(lat["solves_per_s"], 1),
+            "load_sweep": sweep, "load_sweep_start": "cold: fresh server, empty spectrum cache",
             "f32_served_solves_per_s": round(served32["solves_per_s"], 1),
             "f64_plain_unbatched_solves_per_s": round(plain64, 1),
             "f32_served_over_f64_plain": round(served32["solves_per_s"] / plain64, 2),
-            "peak_bytes": int(srv.peak_bytes)}
+            "peak_bytes": int(peak)}
 
 
 # ---------------------------------------------------------------------------
@@ -560,10 +575,8 @@ def run_isofft(args, ws, rank, local):
     ms32 = reduce_max(ms32, ws, dev)
     total = reduce_sum(args.steps, ws, dev)
     value = total / (ms32 / 1e3)
-    fused = M[0] == M[1] and os.environ.get("ISOFFT_FUSE_XY", "") == "1"
     bytes32 = pass_bytes(N, M, 4)
-    gbs32 = sum(kernel_times(passes32, bytes32, fused)[k]["bytes"] for k in kernel_times(passes32, bytes32, fused)) / (
-        ms32 / args.steps / 1e3) / 1e9
+    gbs32 = sum(v["bytes"] for v in kernel_times(passes32, bytes32).values()) / (ms32 / args.steps / 1e3) / 1e9
 
     # FP64 (fewer steps: the FP64 units of this part are a small fraction of FP32)
     steps64 = max(3, args.steps // 10)
@@ -571,8 +584,7 @@ def run_isofft(args, ws, rank, local):
     ms64 = reduce_max(ms64, ws, dev)
     value64 = reduce_sum(steps64, ws, dev) / (ms64 / 1e3)
     bytes64 = pass_bytes(N, M, 8)
-    gbs64 = sum(kernel_times(passes64, bytes64, fused)[k]["bytes"] for k in kernel_times(passes64, bytes64, fused)) / (
-        ms64 / steps64 / 1e3) / 1e9
+    gbs64 = sum(v["bytes"] for v in kernel_times(passes64, bytes64).values()) / (ms64 / steps64 / 1e3) / 1e9
 
     # FP64-class float pairs on the FP32 units (same FP64 buffers)
     stepsdf = max(3, args.steps // 4)
@@ -580,7 +592,7 @@ def run_isofft(args, ws, rank, local):
     msdf = reduce_max(msdf, ws, dev)
     valuedf = reduce_sum(stepsdf, ws, dev) / (msdf / 1e3)
     bytesdf = pass_bytes(N, M, 8)
-    kdf = kernel_times(passesdf, bytesdf, fused)
+    kdf = kernel_times(passesdf, bytesdf)
     gbsdf = sum(kdf[k]["bytes"] for k in kdf) / (msdf / stepsdf / 1e3) / 1e9
 
     # end to end through the public host-buffer entry point
@@ -615,8 +627,8 @@ def run_isofft(args, ws, rank, local):
     copy_rates = host_copy_rates(hsrc, hphi, stream)
 
     # roofline of the dominant kernel (the longest mean device time)
-    k32 = kernel_times(passes32, bytes32, fused)
-    k64 = kernel_times(passes64, bytes64, fused)
+    k32 = kernel_times(passes32, bytes32)
+    k64 = kernel_times(passes64, bytes64)
     dname = max(k32, key=lambda k: k32[k]["ms"])
     achieved = k32[dname]["bytes"] / (k32[dname]["ms"] / 1e3) / 1e9
     traffic = profile_traffic(dname, "f32_%d" % n)
@@ -645,7 +657,7 @@ def run_isofft(args, ws, rank, local):
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": list(N), "M": list(M), "h": w.h[0], "fused_xy": fused,
+        "config": {"workload": WORKLOAD, "N": list(N), "M": list(M), "h": w.h[0],
                    "y_pass_forms": forms,
                    "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "4 rotating src/phi pairs (%d MB) > 129 MB L2" % (8 * 4 * n ** 3 // 2 ** 20)},

@@ -240,11 +240,7 @@ int ipf_submit_batch(const ipf_plan_t *plans, int count, const void *const *d_sr
  * x inverse) over the solves made on this plan since the previous call, then
  * a reset.  Events are recorded on the solving stream between the passes;
  * the call waits for them.  IPF_NOT_READY if no solve was made since the
- * previous call; IPF_INVALID_ARG without the flag.  When the x and y passes
- * run fused (environment ISOFFT_FUSE_XY=1 at plan creation and My = Mx: one
- * kernel per direction), the x-forward entry covers x+y forward and the
- * y-inverse entry covers y+x inverse, while the y-forward and x-inverse
- * entries are 0. */
+ * previous call; IPF_INVALID_ARG without the flag. */
 int ipf_plan_pass_times(ipf_plan_t plan, float ms[5]);
 
 /* The form each y pass of the plan runs in, v[0] for the forward and v[1]

@@ -37,9 +37,9 @@ def _spectrum_code():
 
 def _units():
     units = [("api", "api.cu", ["-DISOFFT_SPECTRUM_CODE=%s" % _spectrum_code()]), ("greens", "greens.cu", []),
-             ("noalloc", "noalloc.cu", [])]
+             ("noalloc", "noalloc.cu", []), ("batch", "batch.cu", [])]
     for real, tag in (("float", "f32"), ("double", "f64"), ("isofft::df64", "df64")):
-        for group, gname in ((1, "x"), (2, "y"), (3, "z"), (4, "xy")):
+        for group, gname in ((1, "x"), (2, "y"), (3, "z")):
             units.append(("passes_%s_%s" % (gname, tag), "passes_inst.cu",
                           ["-DISOFFT_REAL=%s" % real, "-DISOFFT_GROUP=%d" % group]))
     return units

@@ -163,8 +163,6 @@ struct ipf_plan_s {
     static constexpr int kSlots = 64;
     cudaEvent_t ev[kSlots][6] = {};
     bool have_events = false;
-    // x and y passes fused per z plane (square xy mesh; opt-in with ISOFFT_FUSE_XY=1)
-    bool fuse_xy = false;
     int yvar[2] = {kYTile, kYTile};  // form of the y forward / inverse pass
     uint64_t solves = 0, folded = 0;
     double pass_sum[5] = {0, 0, 0, 0, 0};
@@ -604,24 +602,13 @@ cudaError_t enqueue_solve(ipf_plan_s *p, const void *src, void *phi, cudaStream_
         if (e != cudaSuccess) return e;
     }
     if (ev_on) cudaEventRecord(ev[0], st);
-    bool fused = false;
-    if (p->fuse_xy) {
-        PassRange r(p->nvtx, "isofft K1+K2 xy forward");
-        e = launch_xy_forward<T>(Lx, (const IoT *)src, p->W, p->tw_x, p->rtw, p->tw_y, Nx, Ny, Nz, st);
-        if (e == cudaSuccess) {
-            fused = true;
-        } else {
-            cudaGetLastError();  // the cluster launch was refused: use the separate passes from now on
-            p->fuse_xy = false;
-        }
-    }
-    if (!fused) {
+    {
         PassRange r(p->nvtx, "isofft K1 x forward");
         e = launch_x_forward<T>(Lx, (const IoT *)src, p->W, p->tw_x, p->rtw, Nx, Ny, My, nrows, st);
         if (e != cudaSuccess) return e;
     }
     if (ev_on) cudaEventRecord(ev[1], st);
-    if (!fused) {
+    {
         PassRange r(p->nvtx, "isofft K2 y forward");
         e = launch_y_forward<T>(My, p->W, p->tw_y, Ny, Lx, Nz, p->status, p->yvar[0], st);
         if (e != cudaSuccess) return e;
@@ -634,22 +621,13 @@ cudaError_t enqueue_solve(ipf_plan_s *p, const void *src, void *phi, cudaStream_
         if (e != cudaSuccess) return e;
     }
     if (ev_on) cudaEventRecord(ev[3], st);
-    if (fused) {
-        PassRange r(p->nvtx, "isofft K4+K5 yx inverse");
-        e = launch_yx_inverse<T>(Lx, p->W, (IoT *)phi, p->tw_x, p->rtw, p->tw_y, Nx, Ny, Nz, st);
-        if (e != cudaSuccess) {
-            cudaGetLastError();  // refused: finish this solve, and later ones, with the separate passes
-            p->fuse_xy = false;
-            fused = false;
-        }
-    }
-    if (!fused) {
+    {
         PassRange r(p->nvtx, "isofft K4 y inverse");
         e = launch_y_inverse<T>(My, p->W, p->tw_y, Ny, Lx, Nz, p->status, p->yvar[1], st);
         if (e != cudaSuccess) return e;
     }
     if (ev_on) cudaEventRecord(ev[4], st);
-    if (!fused) {
+    {
         PassRange r(p->nvtx, "isofft K5 x inverse");
         e = launch_x_inverse<T>(Lx, p->W, (IoT *)phi, p->tw_x, p->rtw, Nx, Ny, My, nrows, st);
         if (e != cudaSuccess) return e;
@@ -776,6 +754,17 @@ struct BatchLanes {
 std::mutex g_lanes_mu;
 BatchLanes *g_lanes[64] = {};
 
+// ISOFFT_BATCH_FUSED=0 in the environment sends every solve of a batch to
+// the per-grid path (for comparison); read once.
+bool batch_fused_enabled()
+{
+    static const bool on = [] {
+        const char *v = getenv("ISOFFT_BATCH_FUSED");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
 int batch_lanes(BatchLanes **out)
 {
     int dev = 0;
@@ -826,14 +815,6 @@ int ipf_plan_create(ipf_plan_t *out, const int64_t n[3], const double h[3], int 
     }
     p->dtype = dtype;
     p->flags = flags;
-    {
-        const char *fz = getenv("ISOFFT_FUSE_XY");
-        const int lx = (int)(p->M[0] / 2);
-        const bool fits = dtype == IPF_F32   ? xy_fusable<float>(lx)
-                          : dtype == IPF_F64 ? xy_fusable<double>(lx)
-                                             : xy_fusable<df64>(lx);
-        p->fuse_xy = p->M[0] == p->M[1] && fits && fz && fz[0] == '1';
-    }
     p->verbosity = verbosity;
     p->spec = nullptr;
     {
@@ -1003,6 +984,26 @@ int ipf_submit_batch(const ipf_plan_t *plans, int count, const void *const *d_sr
     if (count == 0) return IPF_OK;
     cudaStream_t st = (cudaStream_t)stream;
     if (count == 1) return solve_impl(plans[0], d_src[0], d_phi[0], st);
+    // small FP32 grids: one launch per pass over all of them (batch.cu)
+    std::vector<BatchGridDesc> fused;
+    std::vector<int> rest;
+    for (int i = 0; i < count; ++i) {
+        const ipf_plan_s *p = plans[i];
+        const bool plain = !(p->flags & (IPF_FLAG_PASS_EVENTS | IPF_FLAG_TEST_WAIT_RUNOUT | IPF_FLAG_TEST_CANARY));
+        if (batch_fused_enabled() && plain && batch_fits(p->dtype == IPF_F32, p->M)) {
+            fused.push_back({d_src[i], d_phi[i], p->W, p->tw_x, p->rtw, p->tw_y, p->tw_z, p->spec->G, p->spec->Gs,
+                             p->gscale, (int)p->N[0], (int)p->N[1], (int)p->N[2], (int)p->M[0], (int)p->M[1],
+                             (int)p->M[2]});
+        } else {
+            rest.push_back(i);
+        }
+    }
+    if (fused.size() == 1) {  // a single grid runs its own kernels
+        for (int i = 0; i < count; ++i)
+            if (std::find(rest.begin(), rest.end(), i) == rest.end()) rest.push_back(i);
+        fused.clear();
+    }
+    if (rest.empty()) return cuda_status(batch_enqueue(fused.data(), (int)fused.size(), st));
     BatchLanes *bl = nullptr;
     int rc = batch_lanes(&bl);
     if (rc) return rc;
@@ -1010,16 +1011,20 @@ int ipf_submit_batch(const ipf_plan_t *plans, int count, const void *const *d_sr
     // fork: every lane waits for the work already on the caller's stream
     cudaError_t e = cudaEventRecord(bl->fork, st);
     if (e != cudaSuccess) return cuda_status(e);
-    const int lanes = count < BatchLanes::kLanes ? count : BatchLanes::kLanes;
+    const int nrest = (int)rest.size();
+    const int lanes = nrest < BatchLanes::kLanes ? nrest : BatchLanes::kLanes;
     for (int l = 0; l < lanes; ++l) {
         e = cudaStreamWaitEvent(bl->lane[l], bl->fork, 0);
         if (e != cudaSuccess) return cuda_status(e);
     }
-    // longest solves first, each to the least-loaded lane
-    std::vector<int> order(count);
-    std::vector<double> cost(count), load(lanes, 0.0);
-    for (int i = 0; i < count; ++i) {
-        order[i] = i;
+    if (!fused.empty()) {
+        e = batch_enqueue(fused.data(), (int)fused.size(), st);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    // the other solves longest first, each to the least-loaded lane
+    std::vector<int> order(rest);
+    std::vector<double> cost(count, 0.0), load(lanes, 0.0);
+    for (int i : rest) {
         const ipf_plan_s *p = plans[i];
         cost[i] = (double)p->M[0] * p->M[1] * p->N[2] * (p->dtype == IPF_F64 ? 16.0 : (p->dtype == IPF_DF64 ? 6.0 : 1.0));
     }

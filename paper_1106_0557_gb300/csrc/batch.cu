@@ -1,0 +1,444 @@
+// batch.cu -- many small solves in one launch per pass (ipf_submit_batch).
+//
+// A batch of independent solves of different mesh shapes runs the five
+// passes of Sec. 2.2.2 as five launches, each over a table of work items
+// drawn from every grid of the batch: K1 row groups, K2 column tiles, K3
+// z tiles, K4 column tiles, K5 row groups.  An item names its grid and its
+// line-length class; the CTA branches (uniformly) to that class's pass body
+// -- the same device functions the single-solve kernels run, so a batched
+// result is bitwise the single solve's.  Where a class's body needs fewer
+// threads than the launch has, the CTA runs several of its items side by
+// side (sub-groups with their own shared memory).  Each pass waits for the
+// previous one by stream order, so a batch costs five launches whatever its
+// size, instead of five per grid.
+//
+// Classes: FP32 grids whose doubled mesh is at most 256 on every axis
+// (row lengths Mx/2 of 16 to 128, column lengths 32 to 256).  Other grids
+// of a batch are solved by the per-grid path.
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "launch.h"
+#include "passes.cuh"
+
+namespace isofft {
+
+// One grid of a batch, as the batched kernels read it.
+struct BatchGrid {
+    const float *src;
+    float *phi;
+    Cx<float> *W;
+    const Cx<float> *tw_x, *rtw, *tw_y, *tw_z;
+    const float *G, *Gs;
+    float gscale;
+    int Nx, Ny, Nz, Kx, My, Mz;
+};
+
+// A work item: grid (16 bits), class (8 bits), and the item's index within
+// the grid's items of that pass (one CTA per item).
+struct BatchItem {
+    uint32_t grid_cls;
+    uint32_t idx;
+};
+
+// The line-length classes of the batched passes: row lengths (x passes,
+// Mx / 2) and column lengths (y and z passes).
+constexpr int kBatchRows[] = {16, 24, 32, 48, 64, 96, 128};
+constexpr int kBatchCols[] = {32, 48, 64, 96, 128, 192, 256};
+constexpr int kBatchClasses = 7;
+constexpr int kBatchXThreads = 256;
+constexpr int kBatchColThreads = 512;
+
+int batch_row_class(int L)
+{
+    for (int i = 0; i < kBatchClasses; ++i)
+        if (kBatchRows[i] == L) return i;
+    return -1;
+}
+int batch_col_class(int L)
+{
+    for (int i = 0; i < kBatchClasses; ++i)
+        if (kBatchCols[i] == L) return i;
+    return -1;
+}
+
+// ---------------------------------------------------------------------
+// K1 / K5 on a batch: the row groups of RowCfg (256 threads for every
+// class here).
+// ---------------------------------------------------------------------
+template <int L>
+struct BRow {
+    using C = RowCfg<float, L>;
+    static_assert(C::THREADS == kBatchXThreads, "batched row classes run 256 threads");
+    static constexpr size_t SMEM = (size_t)C::NL * RowPad<float, L>::LP * sizeof(Cx<float>);
+    __host__ __device__ static int64_t items(const BatchGrid &g) { return ((int64_t)g.Ny * g.Nz + C::NL - 1) / C::NL; }
+};
+
+template <int L, bool FWD>
+__device__ __forceinline__ void batch_row(const BatchGrid &g, uint32_t idx, unsigned char *smem)
+{
+    using C = RowCfg<float, L>;
+    const int t = threadIdx.x % C::NT, l = threadIdx.x / C::NT;
+    Cx<float> *line = reinterpret_cast<Cx<float> *>(smem) + l * RowPad<float, L>::LP;
+    const int64_t nrows = (int64_t)g.Ny * g.Nz;
+    const int64_t row = (int64_t)idx * C::NL + l;
+    const bool active = row < nrows;
+    if constexpr (FWD)
+        x_forward_row<float, L>(g.src, g.W, g.tw_x, g.rtw, g.Nx, g.Ny, g.My, active ? row : 0, active, line, t);
+    else
+        x_inverse_row<float, L>(g.W, g.phi, g.tw_x, g.rtw, g.Nx, g.Ny, g.My, active ? row : 0, active, line, t);
+}
+
+template <bool FWD>
+__global__ void __launch_bounds__(kBatchXThreads)
+k_batch_x(const BatchGrid *__restrict__ grids, const BatchItem *__restrict__ items)
+{
+    extern __shared__ __align__(16) unsigned char bsm[];
+    const BatchItem it = items[blockIdx.x];
+    const BatchGrid &g = grids[it.grid_cls >> 8];
+    switch (it.grid_cls & 255) {
+#define X_(i) \
+    case i: batch_row<kBatchRows[i], FWD>(g, it.idx, bsm); break;
+        X_(0) X_(1) X_(2) X_(3) X_(4) X_(5) X_(6)
+#undef X_
+    default: break;
+    }
+}
+
+// ---------------------------------------------------------------------
+// K2 / K4 on a batch: column tiles of ColCfg (TX columns of one z plane);
+// a CTA of 512 threads runs 512 / THREADS tiles side by side.
+// ---------------------------------------------------------------------
+template <int L>
+struct BCol {
+    using C = ColCfg<float, L>;
+    static constexpr int SUB = kBatchColThreads / C::THREADS;  // tiles per CTA
+    static_assert(SUB >= 1 && SUB * C::THREADS == kBatchColThreads, "batched column tiles fill the CTA");
+    static constexpr size_t SMEM = (size_t)SUB * C::SMEM;
+    __host__ __device__ static int64_t tiles(const BatchGrid &g) { return (int64_t)((g.Kx + C::TX - 1) / C::TX) * g.Nz; }
+    __host__ __device__ static int64_t items(const BatchGrid &g) { return (tiles(g) + SUB - 1) / SUB; }
+};
+
+template <int L, bool FWD>
+__device__ __forceinline__ void batch_col(const BatchGrid &g, uint32_t idx, unsigned char *smem)
+{
+    using B = BCol<L>;
+    using C = typename B::C;
+    const int s = threadIdx.x / C::THREADS, lt = threadIdx.x % C::THREADS;
+    const int ntx = (g.Kx + C::TX - 1) / C::TX;
+    const int64_t tile = (int64_t)idx * B::SUB + s;
+    const bool live = tile < B::tiles(g);
+    // a sub-group without a tile runs one with no columns (Kx = 0: nothing
+    // is read or written) so that it meets every barrier of the others
+    const int z = live ? (int)(tile / ntx) : 0, xt = live ? (int)(tile % ntx) : 0;
+    const int Kx = live ? g.Kx : 0;
+    Cx<float> *sm = reinterpret_cast<Cx<float> *>(smem + (size_t)s * C::SMEM);
+    if constexpr (FWD)
+        y_forward_tile<float, L, C::TX>(g.W, g.tw_y, g.Ny, Kx, z, xt * C::TX, sm, lt % C::TX, lt / C::TX);
+    else
+        y_inverse_tile<float, L, C::TX>(g.W, g.tw_y, g.Ny, Kx, z, xt * C::TX, sm, lt % C::TX, lt / C::TX);
+}
+
+// y_forward_tile and y_inverse_tile address W with the grid's Kx as row
+// pitch; a tile-less sub-group passes Kx = 0, so that pitch is 0 too and no
+// access happens (every access is guarded by kx < Kx).
+template <bool FWD>
+__global__ void __launch_bounds__(kBatchColThreads)
+k_batch_y(const BatchGrid *__restrict__ grids, const BatchItem *__restrict__ items)
+{
+    extern __shared__ __align__(16) unsigned char bsm[];
+    const BatchItem it = items[blockIdx.x];
+    const BatchGrid &g = grids[it.grid_cls >> 8];
+    switch (it.grid_cls & 255) {
+#define X_(i) \
+    case i: batch_col<kBatchCols[i], FWD>(g, it.idx, bsm); break;
+        X_(0) X_(1) X_(2) X_(3) X_(4) X_(5) X_(6)
+#undef X_
+    default: break;
+    }
+}
+
+// ---------------------------------------------------------------------
+// K3 on a batch: z tiles of ZCfg (TX columns of the line pair ky, My - ky),
+// staged into shared memory with plain loads (the single-solve kernel's
+// tensor copies need one tensor map per grid), then z_tile.
+// ---------------------------------------------------------------------
+template <int L>
+struct BZ {
+    using C = ZCfg<float, L>;
+    static constexpr int SUB = kBatchColThreads / C::THREADS;
+    static_assert(SUB >= 1 && SUB * C::THREADS == kBatchColThreads, "batched z tiles fill the CTA");
+    static constexpr size_t XCH2 = 2 * C::XCH;  // two exchange buffers
+    static constexpr size_t ONE = XCH2 + C::IN_SET + C::G_SET;
+    static constexpr size_t SMEM = (size_t)SUB * ONE;
+    static_assert(C::XCH % 16 == 0 && C::IN_SET % 16 == 0 && C::G_SET % 16 == 0, "16-byte aligned regions");
+    __host__ __device__ static int64_t tiles(const BatchGrid &g) { return (int64_t)((g.Kx + C::TX - 1) / C::TX) * (g.My / 2); }
+    __host__ __device__ static int64_t items(const BatchGrid &g) { return (tiles(g) + SUB - 1) / SUB; }
+};
+
+template <int L>
+__device__ __forceinline__ void batch_z(const BatchGrid &g, uint32_t idx, unsigned char *smem)
+{
+    using B = BZ<L>;
+    using C = typename B::C;
+    constexpr int TX = C::TX, COLS = C::COLS, Lh = L / 2, E = C::E;
+    using Rad = typename ZShape<float, L>::Rad;
+    const int s = threadIdx.x / C::THREADS, lt = threadIdx.x % C::THREADS;
+    const int c = lt % TX, grp = (lt / TX) & 1, t = lt / COLS;
+    const int ntx = (g.Kx + TX - 1) / TX;
+    const int64_t tile = (int64_t)idx * B::SUB + s;
+    const bool live = tile < B::tiles(g);
+    const int pr = live ? (int)(tile / ntx) : 0, xt = live ? (int)(tile % ntx) : 0;
+    const int Kx = live ? g.Kx : 0;
+    unsigned char *base = smem + (size_t)s * B::ONE;
+    Cx<float> *xch_buf = reinterpret_cast<Cx<float> *>(base);
+    Cx<float> *s_in = reinterpret_cast<Cx<float> *>(base + B::XCH2);
+    float *s_g = reinterpret_cast<float *>(base + B::XCH2 + C::IN_SET);
+    const ZSpecLayout lay{TX, ntx, Lh + 1, C::GBLK};
+    // stage the tile: planes z < Lh of both line groups (zeros from Nz on and
+    // past Kx), and the spectrum block(s)
+    const int ky1 = pr == 0 ? g.My / 2 : g.My - pr;
+    for (int i = lt; i < 2 * Lh * TX; i += C::THREADS) {
+        const int gi = i / (Lh * TX), r = i % (Lh * TX), z = r / TX, cc = r % TX;
+        const int kx = xt * TX + cc;
+        Cx<float> v = {0.0f, 0.0f};
+        if (z < g.Nz && kx < Kx) v = g.W[((size_t)z * g.My + (gi == 0 ? pr : ky1)) * g.Kx + kx];
+        s_in[i] = v;
+    }
+    for (int i = lt; i < 2 * C::GBLK; i += C::THREADS) {
+        const int b = i / C::GBLK, j = i % C::GBLK;
+        s_g[i] = (live && (b == 0 || pr == 0)) ? g.G[lay.block(b == 0 ? pr : g.My / 2, xt) + j] : 0.0f;
+    }
+    __syncthreads();
+    typename ZTwiddles<C::TWR, float, L, E, Rad>::type twr;
+    twr.load(g.tw_z, t);
+    auto hook = [](int) {};
+    ZXch<float, L, E, COLS, C::SWZ, true, decltype(hook)> xch{xch_buf, grp * TX + c, hook};
+    const float *sg = s_g + (pr == 0 ? grp : 0) * C::GBLK;
+    // every sub-group meets the packed column's barriers (the sub-groups'
+    // tiles differ in xt)
+    z_tile<float, L, TX, true>(s_in + grp * Lh * TX, sg, pr, xt, g.W, g.Gs, g.gscale, g.Nz, g.My, Kx, c, grp, t,
+                               twr, g.tw_z, xch, [] { return true; });
+}
+
+__global__ void __launch_bounds__(kBatchColThreads)
+k_batch_z(const BatchGrid *__restrict__ grids, const BatchItem *__restrict__ items)
+{
+    extern __shared__ __align__(16) unsigned char bsm[];
+    const BatchItem it = items[blockIdx.x];
+    const BatchGrid &g = grids[it.grid_cls >> 8];
+    switch (it.grid_cls & 255) {
+#define X_(i) \
+    case i: batch_z<kBatchCols[i]>(g, it.idx, bsm); break;
+        X_(0) X_(1) X_(2) X_(3) X_(4) X_(5) X_(6)
+#undef X_
+    default: break;
+    }
+}
+
+// ---------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------
+static int64_t row_items(int cls, const BatchGrid &g)
+{
+    switch (cls) {
+#define X_(i) \
+    case i: return BRow<kBatchRows[i]>::items(g);
+        X_(0) X_(1) X_(2) X_(3) X_(4) X_(5) X_(6)
+#undef X_
+    default: return 0;
+    }
+}
+static int64_t col_items(int cls, const BatchGrid &g)
+{
+    switch (cls) {
+#define X_(i) \
+    case i: return BCol<kBatchCols[i]>::items(g);
+        X_(0) X_(1) X_(2) X_(3) X_(4) X_(5) X_(6)
+#undef X_
+    default: return 0;
+    }
+}
+static int64_t z_items(int cls, const BatchGrid &g)
+{
+    switch (cls) {
+#define X_(i) \
+    case i: return BZ<kBatchCols[i]>::items(g);
+        X_(0) X_(1) X_(2) X_(3) X_(4) X_(5) X_(6)
+#undef X_
+    default: return 0;
+    }
+}
+
+static size_t row_smem()
+{
+    size_t m = 0;
+#define X_(i) m = std::max(m, BRow<kBatchRows[i]>::SMEM);
+    X_(0) X_(1) X_(2) X_(3) X_(4) X_(5) X_(6)
+#undef X_
+    return m;
+}
+static size_t col_smem()
+{
+    size_t m = 0;
+#define X_(i) m = std::max(m, BCol<kBatchCols[i]>::SMEM);
+    X_(0) X_(1) X_(2) X_(3) X_(4) X_(5) X_(6)
+#undef X_
+    return m;
+}
+static size_t z_smem_max()
+{
+    size_t m = 0;
+#define X_(i) m = std::max(m, BZ<kBatchCols[i]>::SMEM);
+    X_(0) X_(1) X_(2) X_(3) X_(4) X_(5) X_(6)
+#undef X_
+    return m;
+}
+
+// The device tables of one batch: grids, then the five passes' items.
+struct BatchTables {
+    void *dev = nullptr;
+    size_t bytes = 0;
+    const BatchGrid *grids = nullptr;
+    const BatchItem *items[5] = {};
+    int count[5] = {};
+};
+
+namespace {
+std::mutex g_batch_mu;
+// tables by (device, the batch's grid descriptors), at most kBatchCache of
+// them; the least recently used is freed first
+constexpr size_t kBatchCache = 64;
+struct BatchCacheEntry {
+    BatchTables tables;
+    uint64_t last_use = 0;
+};
+std::map<std::pair<int, std::vector<unsigned char>>, BatchCacheEntry> g_batch_tables;
+uint64_t g_batch_clock = 0;
+std::atomic<uint64_t> g_batch_attr{0};
+}  // namespace
+
+bool batch_fits(int dtype_is_f32, const int64_t M[3])
+{
+    return dtype_is_f32 && batch_row_class((int)(M[0] / 2)) >= 0 && batch_col_class((int)M[1]) >= 0 &&
+           batch_col_class((int)M[2]) >= 0;
+}
+
+cudaError_t batch_enqueue(const BatchGridDesc *descs, int count, cudaStream_t st)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = 1ull << (dev & 63);
+    if (!(g_batch_attr.load() & bit)) {
+        e = cudaFuncSetAttribute(k_batch_x<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_smem());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_batch_x<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_smem());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_batch_y<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_batch_y<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_batch_z, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)z_smem_max());
+        if (e != cudaSuccess) return e;
+        g_batch_attr.fetch_or(bit);
+    }
+    std::pair<int, std::vector<unsigned char>> key{dev, {}};
+    key.second.resize((size_t)count * sizeof(BatchGridDesc));
+    memcpy(key.second.data(), descs, key.second.size());
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    auto it = g_batch_tables.find(key);
+    if (it == g_batch_tables.end()) {
+        if (g_batch_tables.size() >= kBatchCache) {
+            auto victim = g_batch_tables.begin();
+            for (auto v = g_batch_tables.begin(); v != g_batch_tables.end(); ++v)
+                if (v->second.last_use < victim->second.last_use) victim = v;
+            cudaFree(victim->second.tables.dev);  // waits for the device
+            g_batch_tables.erase(victim);
+        }
+        // build the grids and the items of every pass (items of one class
+        // adjacent, longest classes first)
+        std::vector<BatchGrid> grids(count);
+        std::vector<BatchItem> items[5];
+        for (int i = 0; i < count; ++i) {
+            const BatchGridDesc &d = descs[i];
+            BatchGrid &g = grids[i];
+            g = {(const float *)d.src, (float *)d.phi, (Cx<float> *)d.W, (const Cx<float> *)d.tw_x,
+                 (const Cx<float> *)d.rtw, (const Cx<float> *)d.tw_y, (const Cx<float> *)d.tw_z,
+                 (const float *)d.G, (const float *)d.Gs, (float)d.gscale, d.Nx, d.Ny, d.Nz, d.Mx / 2, d.My, d.Mz};
+        }
+        for (int pass = 0; pass < 5; ++pass) {
+            for (int cls = kBatchClasses - 1; cls >= 0; --cls) {
+                for (int i = 0; i < count; ++i) {
+                    const BatchGrid &g = grids[i];
+                    int gc;
+                    int64_t n;
+                    if (pass == 0 || pass == 4) {
+                        gc = batch_row_class(g.Kx);
+                        n = gc == cls ? row_items(cls, g) : 0;
+                    } else if (pass == 2) {
+                        gc = batch_col_class(g.Mz);
+                        n = gc == cls ? z_items(cls, g) : 0;
+                    } else {
+                        gc = batch_col_class(g.My);
+                        n = gc == cls ? col_items(cls, g) : 0;
+                    }
+                    for (int64_t k = 0; k < n; ++k)
+                        items[pass].push_back({(uint32_t)(i << 8) | (uint32_t)cls, (uint32_t)k});
+                }
+            }
+        }
+        BatchTables tb;
+        tb.bytes = count * sizeof(BatchGrid);
+        size_t off[5];
+        for (int p = 0; p < 5; ++p) {
+            off[p] = tb.bytes;
+            tb.bytes += items[p].size() * sizeof(BatchItem);
+            tb.count[p] = (int)items[p].size();
+        }
+        std::vector<unsigned char> host(tb.bytes);
+        memcpy(host.data(), grids.data(), count * sizeof(BatchGrid));
+        for (int p = 0; p < 5; ++p) memcpy(host.data() + off[p], items[p].data(), items[p].size() * sizeof(BatchItem));
+        e = cudaMalloc(&tb.dev, tb.bytes);
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpy(tb.dev, host.data(), tb.bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(tb.dev);
+            return e;
+        }
+        tb.grids = (const BatchGrid *)tb.dev;
+        for (int p = 0; p < 5; ++p) tb.items[p] = (const BatchItem *)((unsigned char *)tb.dev + off[p]);
+        it = g_batch_tables.emplace(key, BatchCacheEntry{tb, 0}).first;
+    }
+    it->second.last_use = ++g_batch_clock;
+    const BatchTables &tb = it->second.tables;
+    if (tb.count[0]) {
+        k_batch_x<true><<<tb.count[0], kBatchXThreads, row_smem(), st>>>(tb.grids, tb.items[0]);
+        count_launch();
+    }
+    if (tb.count[1]) {
+        k_batch_y<true><<<tb.count[1], kBatchColThreads, col_smem(), st>>>(tb.grids, tb.items[1]);
+        count_launch();
+    }
+    if (tb.count[2]) {
+        k_batch_z<<<tb.count[2], kBatchColThreads, z_smem_max(), st>>>(tb.grids, tb.items[2]);
+        count_launch();
+    }
+    if (tb.count[3]) {
+        k_batch_y<false><<<tb.count[3], kBatchColThreads, col_smem(), st>>>(tb.grids, tb.items[3]);
+        count_launch();
+    }
+    if (tb.count[4]) {
+        k_batch_x<false><<<tb.count[4], kBatchXThreads, row_smem(), st>>>(tb.grids, tb.items[4]);
+        count_launch();
+    }
+    return cudaGetLastError();
+}
+
+
+}  // namespace isofft

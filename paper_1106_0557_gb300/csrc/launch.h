@@ -51,17 +51,6 @@ template <typename T>
 cudaError_t launch_z_convolve(int L, void *W, const void *tw, const T *G, const T *Gs, T gscale, int Nz,
                               int My, int Kx, unsigned *status, unsigned test_extra_tx, cudaStream_t st);
 
-// Fused x+y forward / y+x inverse for planes with My = Mx = 2 LX: one
-// cluster of 4 CTAs per z plane (see passes.cuh).
-template <typename T>
-bool xy_fusable(int LX);  // both fused kernels exist and fit for this LX
-template <typename T>
-cudaError_t launch_xy_forward(int LX, const typename IoReal<T>::type *src, void *W, const void *twx,
-                              const void *rtw, const void *twy, int Nx, int Ny, int Nz, cudaStream_t st);
-template <typename T>
-cudaError_t launch_yx_inverse(int LX, void *W, typename IoReal<T>::type *phi, const void *twx, const void *rtw,
-                              const void *twy, int Nx, int Ny, int Nz, cudaStream_t st);
-
 // Width (kx columns per tile) of the z pass for line length L; the cached
 // Green's spectrum is stored in tiles of this width (0: unsupported L).
 template <typename T>
@@ -99,6 +88,25 @@ int64_t green_cos_elems(const int64_t M[3]);
 
 // Device bytes of the FP64 scratch build_green_spectrum needs for mesh M.
 size_t green_build_scratch_bytes(const int64_t M[3]);
+
+// One grid of a batch run in one launch per pass (batch.cu): the plan's
+// buffers and sizes.
+struct BatchGridDesc {
+    const void *src;
+    void *phi;
+    void *W;
+    const void *tw_x, *rtw, *tw_y, *tw_z;
+    const void *G, *Gs;
+    double gscale;
+    int Nx, Ny, Nz, Mx, My, Mz;
+};
+// Whether a grid of this dtype and doubled mesh can join a batched launch
+// (FP32, every doubled length at most 256).
+bool batch_fits(int dtype_is_f32, const int64_t M[3]);
+// The five passes of `count` such grids, one launch each, on `st`.  The
+// first call for a given set of grids builds and uploads its work tables
+// (synchronously); later calls only launch.
+cudaError_t batch_enqueue(const BatchGridDesc *grids, int count, cudaStream_t st);
 
 // e^{-2 pi i k / n} for 0 <= k < count, by exact reduction to the first
 // octant (host, libm in double).

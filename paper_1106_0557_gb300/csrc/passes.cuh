@@ -837,231 +837,6 @@ k_y_pass(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, const C
     }
 }
 
-// ---------------------------------------------------------------------
-// Fused x+y forward (K12) and y+x inverse (K45) for planes with My = Mx:
-// a cluster of XY_CLUSTER CTAs owns one z plane.  Forward: each CTA
-// transforms its share of the plane's rows along x and writes them to W; a
-// cluster barrier (release/acquire at cluster scope) makes those rows
-// visible; each CTA then transforms its share of the plane's columns along y,
-// in place.  The x spectra of a plane are overwritten by the y pass
-// microseconds after they are written, so they live in L2 instead of making
-// an HBM round trip.  The inverse runs the same in reverse.
-// ---------------------------------------------------------------------
-constexpr int XY_CLUSTER = 4;
-
-template <typename T, int LX>
-struct XYCfg {
-    static constexpr int LY = 2 * LX;
-    static constexpr int THREADS = 512;
-    static constexpr int MIN_BLOCKS = sizeof(T) == 4 ? 2 : 1;  // FP32: two CTAs per SM
-    static constexpr int NTX = LX / XShape<T, LX>::E;
-    static constexpr int NL = THREADS / NTX;  // rows per round
-    static constexpr int NTY = LY / Shape<T, LY>::E;
-    static constexpr int TX = THREADS / NTY;  // columns per round
-    static_assert(NTX <= THREADS && NTY <= THREADS, "line too long for a fused tile");
-    static constexpr size_t CS = sizeof(Cx<T>);
-    // exchange buffers of the two phases
-    static constexpr size_t XCH_X = (size_t)NL * RowPad<T, LX>::LP * CS;
-    static constexpr size_t XCH_Y = (size_t)LY * TX * CS;
-    // one stage of prefetched input (each phase double-buffers its stage)
-    static constexpr size_t ROWS_F = (size_t)NL * LX * sizeof(In<T>);  // real source rows
-    static constexpr size_t ROWS_I = (size_t)NL * LX * CS;         // packed half-spectrum rows
-    static constexpr size_t COLS_F = (size_t)LX * TX * CS;         // half columns (y < My/2)
-    static constexpr size_t COLS_I = (size_t)LY * TX * CS;         // whole columns
-    static constexpr size_t mx(size_t a, size_t b) { return a > b ? a : b; }
-    static constexpr size_t SMEM_F = mx(XCH_X + 2 * ROWS_F, XCH_Y + 2 * COLS_F);
-    static constexpr size_t SMEM_I = mx(XCH_Y + 2 * COLS_I, XCH_X + 2 * ROWS_I);
-    // fused only where both kernels fit one SM's shared memory and a round
-    // is not a crowd of tiny rows
-    static constexpr bool OK = LX >= 64 && SMEM_F <= 227 * 1024 && SMEM_I <= 227 * 1024;
-};
-
-__device__ __forceinline__ void cluster_sync_release_acquire()
-{
-    __threadfence();
-    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
-    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
-}
-
-// Runs `rounds` rounds of `compute(j, buf)`, with round j + 1's inputs copied
-// by `issue(j + 1, buf')` into the other of two staging buffers while round j
-// computes.  All threads of the CTA call it with the same `rounds`.
-template <typename Issue, typename Compute>
-__device__ __forceinline__ void pipelined_rounds(int rounds, Issue issue, Compute compute)
-{
-    if (rounds > 0) issue(0, 0);
-    cp_async_commit();
-    for (int j = 0; j < rounds; ++j) {
-        if (j + 1 < rounds) issue(j + 1, (j + 1) & 1);
-        cp_async_commit();
-        cp_async_wait<1>();  // round j's copies have landed
-        __syncthreads();     // ... everyone's
-        compute(j, j & 1);
-        __syncthreads();     // buffer j & 1 is free for round j + 2
-    }
-    cp_async_wait<0>();
-}
-
-// Copy `rows` rows of `bytes` each (row r from src_row(r)) into consecutive
-// staging rows of `stride` bytes, 16 bytes per copy when every row start and
-// length allow it, else `es` bytes per copy.
-// A row whose source is null is zero-filled (nothing is read; `safe`, a
-// valid global address, stands in as the operand).
-template <int ES, typename SrcRow>
-__device__ __forceinline__ void stage_rows(unsigned char *dst, size_t stride, int rows, int bytes, SrcRow src_row,
-                                           bool vec16, const void *safe)
-{
-    const unsigned char *sf = reinterpret_cast<const unsigned char *>(safe);
-    if (vec16) {
-        const int per = bytes / 16;
-        for (int i = threadIdx.x; i < rows * per; i += blockDim.x) {
-            const int r = i / per, k = i - r * per;
-            const unsigned char *s = src_row(r);
-            cp_async<16>(dst + r * stride + 16 * k, s ? s + 16 * k : sf, s != nullptr);
-        }
-    } else {
-        const int per = bytes / ES;
-        for (int i = threadIdx.x; i < rows * per; i += blockDim.x) {
-            const int r = i / per, k = i - r * per;
-            const unsigned char *s = src_row(r);
-            cp_async<ES>(dst + r * stride + ES * k, s ? s + ES * k : sf, s != nullptr);
-        }
-    }
-}
-
-template <typename T, int LX>
-__global__ void __launch_bounds__(XYCfg<T, LX>::THREADS, XYCfg<T, LX>::MIN_BLOCKS)
-k_xy_forward(const In<T> *__restrict__ src, Cx<T> *__restrict__ W, const Cx<T> *__restrict__ twx,
-             const Cx<T> *__restrict__ rtw, const Cx<T> *__restrict__ twy, int Nx, int Ny)
-{
-    using C = XYCfg<T, LX>;
-    constexpr int LY = C::LY;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Cx<T> *xch = reinterpret_cast<Cx<T> *>(smem_raw);
-    const int z = blockIdx.x / XY_CLUSTER, r = blockIdx.x % XY_CLUSTER;
-
-    // phase 1: this CTA's rows along x, source rows prefetched
-    {
-        unsigned char *stage = smem_raw + C::XCH_X;
-        const int t = threadIdx.x % C::NTX, l = threadIdx.x / C::NTX;
-        const int per = (Ny + XY_CLUSTER - 1) / XY_CLUSTER;
-        const int y_lo = r * per, y_hi = min(Ny, y_lo + per);
-        const int rounds = y_hi > y_lo ? (y_hi - y_lo + C::NL - 1) / C::NL : 0;
-        const bool vec16 = ((size_t)Nx * sizeof(In<T>)) % 16 == 0;
-        auto issue = [&](int j, int buf) {
-            const int y0 = y_lo + j * C::NL;
-            stage_rows<sizeof(In<T>)>(
-                stage + buf * C::ROWS_F, LX * sizeof(In<T>), C::NL, Nx * (int)sizeof(In<T>),
-                [&](int rr) -> const unsigned char * {
-                    const int y = y0 + rr;
-                    return y < y_hi ? reinterpret_cast<const unsigned char *>(src + ((size_t)z * Ny + y) * Nx)
-                                    : nullptr;
-                },
-                vec16, src);
-        };
-        auto compute = [&](int j, int buf) {
-            const int y = y_lo + j * C::NL + l;
-            const bool active = y < y_hi;
-            const In<T> *in = reinterpret_cast<const In<T> *>(stage + buf * C::ROWS_F) + l * LX;
-            x_forward_row_at<T, LX>(in, W + ((size_t)z * LY + (active ? y : y_lo)) * LX, twx, rtw, Nx, active,
-                                    xch + l * RowPad<T, LX>::LP, t);
-        };
-        pipelined_rounds(rounds, issue, compute);
-    }
-    cluster_sync_release_acquire();
-    // phase 2: this CTA's columns along y, half columns prefetched from L2
-    {
-        unsigned char *stage = smem_raw + C::XCH_Y;
-        const int c = threadIdx.x % C::TX, t = threadIdx.x / C::TX;
-        const int tiles = (LX + C::TX - 1) / C::TX;
-        const int per = (tiles + XY_CLUSTER - 1) / XY_CLUSTER;
-        const int xt_lo = r * per, xt_hi = min(tiles, xt_lo + per);
-        const int rounds = xt_hi > xt_lo ? xt_hi - xt_lo : 0;
-        const int kx_n = min(C::TX, LX);  // columns of a tile inside the mesh
-        const bool vec16 = (kx_n * C::CS) % 16 == 0;
-        auto issue = [&](int j, int buf) {
-            const int kx0 = (xt_lo + j) * C::TX;
-            stage_rows<sizeof(Cx<T>)>(
-                stage + buf * C::COLS_F, C::TX * C::CS, Ny, kx_n * (int)C::CS,
-                [&](int y) -> const unsigned char * {
-                    return reinterpret_cast<const unsigned char *>(W + ((size_t)z * LY + y) * LX + kx0);
-                },
-                vec16, W);
-        };
-        auto compute = [&](int j, int buf) {
-            y_forward_tile<T, LY, C::TX>(W, twy, Ny, LX, z, (xt_lo + j) * C::TX, xch, c, t,
-                                         reinterpret_cast<const Cx<T> *>(stage + buf * C::COLS_F));
-        };
-        pipelined_rounds(rounds, issue, compute);
-    }
-}
-
-template <typename T, int LX>
-__global__ void __launch_bounds__(XYCfg<T, LX>::THREADS, XYCfg<T, LX>::MIN_BLOCKS)
-k_yx_inverse(Cx<T> *__restrict__ W, In<T> *__restrict__ phi, const Cx<T> *__restrict__ twx,
-             const Cx<T> *__restrict__ rtw, const Cx<T> *__restrict__ twy, int Nx, int Ny)
-{
-    using C = XYCfg<T, LX>;
-    constexpr int LY = C::LY;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Cx<T> *xch = reinterpret_cast<Cx<T> *>(smem_raw);
-    const int z = blockIdx.x / XY_CLUSTER, r = blockIdx.x % XY_CLUSTER;
-
-    // phase 1: this CTA's columns along y, whole columns prefetched
-    {
-        unsigned char *stage = smem_raw + C::XCH_Y;
-        const int c = threadIdx.x % C::TX, t = threadIdx.x / C::TX;
-        const int tiles = (LX + C::TX - 1) / C::TX;
-        const int per = (tiles + XY_CLUSTER - 1) / XY_CLUSTER;
-        const int xt_lo = r * per, xt_hi = min(tiles, xt_lo + per);
-        const int rounds = xt_hi > xt_lo ? xt_hi - xt_lo : 0;
-        const int kx_n = min(C::TX, LX);
-        const bool vec16 = (kx_n * C::CS) % 16 == 0;
-        auto issue = [&](int j, int buf) {
-            const int kx0 = (xt_lo + j) * C::TX;
-            stage_rows<sizeof(Cx<T>)>(
-                stage + buf * C::COLS_I, C::TX * C::CS, LY, kx_n * (int)C::CS,
-                [&](int y) -> const unsigned char * {
-                    return reinterpret_cast<const unsigned char *>(W + ((size_t)z * LY + y) * LX + kx0);
-                },
-                vec16, W);
-        };
-        auto compute = [&](int j, int buf) {
-            y_inverse_tile<T, LY, C::TX>(W, twy, Ny, LX, z, (xt_lo + j) * C::TX, xch, c, t,
-                                         reinterpret_cast<const Cx<T> *>(stage + buf * C::COLS_I));
-        };
-        pipelined_rounds(rounds, issue, compute);
-    }
-    cluster_sync_release_acquire();
-    // phase 2: this CTA's rows along x, packed rows prefetched from L2
-    {
-        unsigned char *stage = smem_raw + C::XCH_X;
-        const int t = threadIdx.x % C::NTX, l = threadIdx.x / C::NTX;
-        const int per = (Ny + XY_CLUSTER - 1) / XY_CLUSTER;
-        const int y_lo = r * per, y_hi = min(Ny, y_lo + per);
-        const int rounds = y_hi > y_lo ? (y_hi - y_lo + C::NL - 1) / C::NL : 0;
-        auto issue = [&](int j, int buf) {
-            const int y0 = y_lo + j * C::NL;
-            stage_rows<sizeof(Cx<T>)>(
-                stage + buf * C::ROWS_I, LX * C::CS, C::NL, LX * (int)C::CS,
-                [&](int rr) -> const unsigned char * {
-                    const int y = y0 + rr;
-                    return y < y_hi ? reinterpret_cast<const unsigned char *>(W + ((size_t)z * LY + y) * LX)
-                                    : nullptr;
-                },
-                true, W);
-        };
-        auto compute = [&](int j, int buf) {
-            const int y = y_lo + j * C::NL + l;
-            const bool active = y < y_hi;
-            const Cx<T> *in = reinterpret_cast<const Cx<T> *>(stage + buf * C::ROWS_I) + l * LX;
-            x_inverse_row_at<T, LX>(in, phi + ((size_t)z * Ny + (active ? y : y_lo)) * Nx, twx, rtw, Nx, active,
-                                    xch + l * RowPad<T, LX>::LP, t);
-        };
-        pipelined_rounds(rounds, issue, compute);
-    }
-}
-
 // One tile of the z pass on staged data: the forward transforms of the
 // thread's line, the multiply by the Green's spectrum, the inverse
 // transforms and the store of z < Nz.  `sin`: the thread's line group as
@@ -1069,7 +844,7 @@ k_yx_inverse(Cx<T> *__restrict__ W, In<T> *__restrict__ phi, const Cx<T> *__rest
 // offset to the tile's first column; `sg`: the spectrum block of the
 // thread's line, [kz'][TX].  `before_g` runs before the spectrum is read and
 // returns false (the same on every thread) to abandon the tile.
-template <typename T, int L, int IS, typename TWR, typename Xch, typename BeforeG>
+template <typename T, int L, int IS, bool SYNC_ALL = false, typename TWR, typename Xch, typename BeforeG>
 __device__ __forceinline__ bool z_tile(const Cx<T> *sin, const T *sg, int pr, int xt, Cx<T> *__restrict__ W,
                                        const T *__restrict__ Gs, T gscale, int Nz, int My, int Kx, int c, int g,
                                        int t, const TWR &twr, const Cx<T> *twz, Xch &xch, BeforeG before_g)
@@ -1097,15 +872,17 @@ __device__ __forceinline__ bool z_tile(const Cx<T> *sin, const T *sg, int pr, in
     const T *g_hi = sg + (L - t) * TX + c;
     auto gval = [&](int m) -> T { return m < E / 2 ? g_lo[m * NT * TX] : g_hi[-m * NT * TX]; };
     const bool packed = xt == 0 && c == 0;  // the kx = 0 / Mx/2 column
-    if (xt == 0) {
+    // SYNC_ALL: every thread of the CTA meets these barriers, whatever its
+    // tile (CTAs that run several tiles side by side)
+    if (SYNC_ALL || xt == 0) {
         // the packed column needs the partner bin (-ky, -kz)
         Cx<T> *sp = xch.free_buf();
-        if (c == 0) {
+        if (packed) {
 #pragma unroll
             for (int m = 0; m < E; ++m) sp[(t + m * NT) * COLS + col] = v[m];
         }
         __syncthreads();
-        if (c == 0) {
+        if (packed) {
             const int gp = pr == 0 ? g : 1 - g;
             const T *gsrow = Gs + (size_t)kyp * (Lh + 1);
 #pragma unroll

@@ -1,8 +1,8 @@
 // passes_inst.cu -- instantiates and launches the pass kernels for one real
 // type and one group of passes.  The build compiles this file several times:
 //   -DISOFFT_REAL=float|double|isofft::df64   the arithmetic type
-//   -DISOFFT_GROUP=1|2|3|4       1: x passes (K1, K5), 2: y passes (K2, K4),
-//                                3: z pass (K3), 4: fused x+y passes
+//   -DISOFFT_GROUP=1|2|3         1: x passes (K1, K5), 2: y passes (K2, K4),
+//                                3: z pass (K3)
 // so that the instantiations compile in parallel.
 #include <atomic>
 
@@ -39,9 +39,6 @@ static cudaError_t ensure_smem(F *func, size_t bytes, std::atomic<uint64_t> &don
     X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768) X(1152)
 #define ISOFFT_COL_LENGTHS(X) \
     X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768) X(1024) X(1536) X(2304)
-// row lengths with fused x+y kernels (their doubled length is a column length
-// up to 1536)
-#define ISOFFT_FUSED_LENGTHS(X) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768)
 
 // Resident CTAs per SM of a kernel on the current device (queried once).
 template <typename F>
@@ -231,96 +228,6 @@ cudaError_t launch_y_inverse(int L, void *W, const void *tw, int Ny, int Kx, int
 }
 template cudaError_t launch_y_forward<Real>(int, void *, const void *, int, int, int, unsigned *, int, cudaStream_t);
 template cudaError_t launch_y_inverse<Real>(int, void *, const void *, int, int, int, unsigned *, int, cudaStream_t);
-#endif
-
-#if ISOFFT_GROUP == 4
-template <typename K, typename... Args>
-static cudaError_t launch_cluster(K *kernel, unsigned grid, unsigned threads, size_t smem, cudaStream_t st,
-                                  Args... args)
-{
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(threads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = XY_CLUSTER;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, args...);
-}
-
-template <typename T, int LX>
-static cudaError_t run_xy(const In<T> *src, void *W, const void *twx, const void *rtw, const void *twy, int Nx, int Ny,
-                          int Nz, cudaStream_t st)
-{
-    using C = XYCfg<T, LX>;
-    if (!C::OK) return cudaErrorNotSupported;
-    static std::atomic<uint64_t> done{0};
-    cudaError_t e = ensure_smem(k_xy_forward<T, LX>, C::SMEM_F, done);
-    if (e != cudaSuccess) return e;
-    e = launch_cluster(k_xy_forward<T, LX>, (unsigned)(XY_CLUSTER * Nz), C::THREADS, C::SMEM_F, st, src,
-                       (Cx<T> *)W, (const Cx<T> *)twx, (const Cx<T> *)rtw, (const Cx<T> *)twy, Nx, Ny);
-    if (e == cudaSuccess) count_launch();
-    return e;
-}
-template <typename T, int LX>
-static cudaError_t run_yx(void *W, In<T> *phi, const void *twx, const void *rtw, const void *twy, int Nx, int Ny, int Nz,
-                          cudaStream_t st)
-{
-    using C = XYCfg<T, LX>;
-    if (!C::OK) return cudaErrorNotSupported;
-    static std::atomic<uint64_t> done{0};
-    cudaError_t e = ensure_smem(k_yx_inverse<T, LX>, C::SMEM_I, done);
-    if (e != cudaSuccess) return e;
-    e = launch_cluster(k_yx_inverse<T, LX>, (unsigned)(XY_CLUSTER * Nz), C::THREADS, C::SMEM_I, st, (Cx<T> *)W, phi,
-                       (const Cx<T> *)twx, (const Cx<T> *)rtw, (const Cx<T> *)twy, Nx, Ny);
-    if (e == cudaSuccess) count_launch();
-    return e;
-}
-template <typename R_>
-cudaError_t launch_xy_forward(int LX, const In<R_> *src, void *W, const void *twx, const void *rtw, const void *twy,
-                              int Nx, int Ny, int Nz, cudaStream_t st)
-{
-    switch (LX) {
-#define X_(n) \
-    case n: return run_xy<R_, n>(src, W, twx, rtw, twy, Nx, Ny, Nz, st);
-        ISOFFT_FUSED_LENGTHS(X_)
-#undef X_
-    default: return cudaErrorInvalidValue;
-    }
-}
-template <typename R_>
-cudaError_t launch_yx_inverse(int LX, void *W, In<R_> *phi, const void *twx, const void *rtw, const void *twy, int Nx,
-                              int Ny, int Nz, cudaStream_t st)
-{
-    switch (LX) {
-#define X_(n) \
-    case n: return run_yx<R_, n>(W, phi, twx, rtw, twy, Nx, Ny, Nz, st);
-        ISOFFT_FUSED_LENGTHS(X_)
-#undef X_
-    default: return cudaErrorInvalidValue;
-    }
-}
-template <typename R_>
-bool xy_fusable(int LX)
-{
-    switch (LX) {
-#define X_(n) \
-    case n: return XYCfg<R_, n>::OK;
-        ISOFFT_FUSED_LENGTHS(X_)
-#undef X_
-    default: return false;
-    }
-}
-template bool xy_fusable<Real>(int);
-template cudaError_t launch_xy_forward<Real>(int, const In<Real> *, void *, const void *, const void *,
-                                             const void *, int, int, int, cudaStream_t);
-template cudaError_t launch_yx_inverse<Real>(int, void *, In<Real> *, const void *, const void *, const void *, int,
-                                             int, int, cudaStream_t);
 #endif
 
 #if ISOFFT_GROUP == 3

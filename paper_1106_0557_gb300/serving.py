@@ -171,9 +171,12 @@ class Server:
                 return "reject"
             self.pool.add(plan, nbytes)
         else:
-            if self.used() + out_bytes > self.budget:
-                self.pool.release(key, plan)
-                return "wait"
+            # room for the output: other idle plans go first (the one taken
+            # is not idle, so it stays)
+            while self.used() + out_bytes > self.budget:
+                if not self.pool.evict_one():
+                    self.pool.release(key, plan)
+                    return "wait"
         req.plan = plan
         req.slot = slot
         req.out = self.backend.alloc_output(req.n, req.dtype)

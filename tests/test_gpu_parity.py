@@ -161,8 +161,7 @@ def test_in_place_host_and_events():
         inplace = d.clone()
         p.solve(inplace, out=inplace)
         torch.cuda.synchronize()
-        # 3 kernels when the x and y passes are fused (Mx == My here), else 5
-        assert native.ipf_launch_count() - before in (3, 5)
+        assert native.ipf_launch_count() - before == 5  # one kernel per pass
         assert torch.equal(inplace, ref)
         times = p.pass_times()
         assert len(times) == 5 and all(t >= 0 for t in times) and times[2] > 0 and sum(times) > times[2]
@@ -188,6 +187,51 @@ def test_batch_matches_single_solves():
         ref = oracle.solve(s.cpu().numpy().astype(np.float64), w.h)
         assert oracle.max_rel_error(o.cpu().numpy(), ref) <= TOL["f32"]
     for p in plans:
+        p.close()
+
+
+def test_ragged_batch_of_64_runs_in_five_launches():
+    """The config-4 batch (64 grids, each axis from {32,48,64,96,128}, FP32):
+    one launch per pass over all grids (a table of work items), results
+    bitwise those of the single solves."""
+    from paper_1106_0557_gb300 import Plan, submit_batch
+    wl = sources.ragged_batch(count=64)
+    plans = [Plan(w.N, w.h, "f32") for w in wl]
+    srcs = [torch.from_numpy(w.source(np.float32)).cuda() for w in wl]
+    outs = [torch.empty_like(s) for s in srcs]
+    submit_batch(plans, srcs, outs)  # builds the work tables
+    torch.cuda.synchronize()
+    before = native.ipf_launch_count()
+    for o in outs:
+        o.zero_()
+    submit_batch(plans, srcs, outs)
+    torch.cuda.synchronize()
+    assert native.ipf_launch_count() - before == 5
+    for p, s, o in zip(plans, srcs, outs):
+        assert torch.equal(o, p.solve(s))
+    for p in plans:
+        p.close()
+
+
+def test_mixed_batch_fused_and_per_grid():
+    """A batch mixing small FP32 grids (one launch per pass), an FP64 grid
+    and an FP32 grid beyond the batched lengths (their own passes on the
+    library's streams): every result bitwise its single solve's, and in
+    place (d_src = d_phi) too."""
+    from paper_1106_0557_gb300 import Plan, submit_batch
+    shapes = [((40, 33, 24), "f32"), ((20, 70, 9), "f32"), ((48, 48, 48), "f64"), ((150, 20, 16), "f32"),
+              ((17, 5, 100), "f32"), ((33, 64, 20), "df64")]
+    plans, srcs, singles = [], [], []
+    for k, (N, dt) in enumerate(shapes):
+        p = Plan(N, (1.0, 0.5, 0.25), dt)
+        s = torch.from_numpy(rand_src(N, 30 + k).astype(NP[dt])).cuda()
+        singles.append(p.solve(s).clone())
+        plans.append(p)
+        srcs.append(s)
+    submit_batch(plans, srcs, srcs)  # in place
+    torch.cuda.synchronize()
+    for p, s, r in zip(plans, srcs, singles):
+        assert torch.equal(s, r)
         p.close()
 
 
@@ -274,30 +318,6 @@ def test_batch_graph_replay_matches_single_solves():
             assert torch.equal(o, p.solve(s))
     for p in plans:
         p.close()
-
-
-@pytest.mark.parametrize("dtype", ["f32", "f64", "df64"])
-@pytest.mark.parametrize("N", [(64, 64, 64), (60, 50, 13), (256, 200, 31), (500, 400, 7)])
-def test_fused_xy_passes_equal_separate_passes(N, dtype, monkeypatch):
-    """Planes with My = Mx run the x and y passes fused in one cluster
-    kernel per direction; the result is bitwise that of the separate
-    passes (the same arithmetic in the same order)."""
-    from paper_1106_0557_gb300 import Plan
-    src = torch.from_numpy(rand_src(N, 3).astype(NP[dtype])).cuda()
-    monkeypatch.setenv("ISOFFT_FUSE_XY", "1")
-    with Plan(N, (1.0, 1.0, 1.0), dtype) as p:
-        assert p.padded_shape[0] == p.padded_shape[1]
-        before = native.ipf_launch_count()
-        fused = p.solve(src)
-        torch.cuda.synchronize()
-        assert native.ipf_launch_count() - before == 3
-    monkeypatch.setenv("ISOFFT_FUSE_XY", "0")
-    with Plan(N, (1.0, 1.0, 1.0), dtype) as p:
-        before = native.ipf_launch_count()
-        sep = p.solve(src)
-        torch.cuda.synchronize()
-        assert native.ipf_launch_count() - before == 5
-    assert torch.equal(fused, sep)
 
 
 def test_df64_is_fp64_class_and_beats_fp32():

@@ -140,3 +140,46 @@ def test_poisson_arrivals_and_stats():
     reqs = srv.run(make_requests(200, seed=5, rate=3000.0), clock=clock)
     st = serving.latency_stats(reqs)
     assert st["count"] == 200 and 0 < st["p50_ms"] <= st["p99_ms"]
+
+
+def test_async_plans_respect_budget_and_complete():
+    """Plans built on the background thread: the budget (with the bytes
+    reserved for plans being built) is never exceeded, every request
+    completes, failed creations are rejected, and plans are reused."""
+    clock = FakeClock()
+    be = FakeBackend(clock, fail={(40, "f64")})
+    budget = 3 * be.plan_bytes(48, "f64")
+    srv = serving.Server(be, budget_bytes=budget, slots=4, async_plans=True, lookahead=16)
+    reqs = make_requests(300, rate=2000.0)
+    reqs.append(serving.Request(300, 40, "f64", 300, 0.05))
+    srv.run(reqs, clock=clock)
+    st = {r.id: r.status for r in reqs}
+    assert st[300] == "error:%d" % native.IPF_OUT_OF_MEMORY
+    assert all(s == serving.OK for i, s in st.items() if not (reqs[i].n == 40 and reqs[i].dtype == "f64"))
+    assert srv.peak_bytes <= budget
+    srv.close()
+    assert be.live == set()
+    # with room for every plan, each shape's plan is built once and reused
+    clock = FakeClock()
+    be = FakeBackend(clock)
+    srv = serving.Server(be, budget_bytes=1e12, slots=4, async_plans=True)
+    reqs = [serving.Request(i, 32 if i % 2 else 24, "f32", i, 0.0) for i in range(60)]
+    srv.run(reqs, clock=clock)
+    assert all(r.status == serving.OK for r in reqs)
+    assert be.created <= 8
+    srv.close()
+
+
+def test_async_lookahead_passes_requests_waiting_for_a_plan():
+    """A request whose plan is being built does not hold back a later request
+    whose plan is ready; with look-ahead off (synchronous plans) admission is
+    in arrival order."""
+    clock = FakeClock()
+    be = FakeBackend(clock)
+    srv = serving.Server(be, budget_bytes=1e12, slots=2, async_plans=True, lookahead=8)
+    srv.run([serving.Request(0, 16, "f32", 0, 0.0)], clock=clock)  # a ready plan of N = 16
+    reqs = [serving.Request(1, 32, "f32", 1, 0.0), serving.Request(2, 16, "f32", 2, 0.0)]
+    srv.run(reqs, clock=clock)
+    assert all(r.status == serving.OK for r in reqs)
+    assert reqs[1].admitted <= reqs[0].admitted
+    srv.close()
