@@ -363,9 +363,11 @@ def run_batch(steps=50, count=64):
         b = pass_bytes(w.N, p.padded_shape, 4)
         nbytes += sum(b[k] for k in PASSES)
     res = {"grids": count, "workload": "ragged batch, each axis from {32,48,64,96,128}, seed = grid index",
-           "how": "one launch per pass over a table of every grid's work items" if
-                  os.environ.get("ISOFFT_BATCH_FUSED", "1") != "0" else "per-grid passes on 8 library streams"}
-    for mode in ("graph", "submit"):
+           "how": {"graph": "per-grid passes on 8 library streams, captured in a CUDA graph",
+                   "submit": "the same without the graph",
+                   "fused": "one launch per pass over a table of every grid's work items (ISOFFT_BATCH_FUSED=1)"}}
+    for mode in ("graph", "submit", "fused"):
+        os.environ["ISOFFT_BATCH_FUSED"] = "1" if mode == "fused" else "0"
         if mode == "graph":
             bg = BatchGraph(plans, srcs, outs)
             run = bg.replay
@@ -389,6 +391,7 @@ def run_batch(steps=50, count=64):
         res[mode] = {"ms_per_batch": round(ms, 4), "solves_per_s": round(count / (ms / 1e3), 1),
                      "hbm_gbs_algorithmic": round(nbytes / (ms / 1e3) / 1e9, 1),
                      "launches_per_batch": None if mode == "graph" else launches}
+    os.environ.pop("ISOFFT_BATCH_FUSED", None)
     for p in plans:
         p.close()
     return res

@@ -223,7 +223,12 @@ int ipf_noalloc_check(void *stream);
 /* Submit `count` independent solves, possibly of different shapes and
  * dtypes; plans[i] solves d_src[i] into d_phi[i].  Not in the paper, which
  * runs one solve at a time per communicator; each solve is the Sec. 2.2.2
- * sequence of ipf_solve.  A plan may appear only
+ * sequence of ipf_solve.  With the environment variable ISOFFT_BATCH_FUSED=1
+ * the FP32 solves whose doubled mesh is at most 256 on every axis run
+ * together in one launch per pass (five launches for all of them, over a
+ * table of their work items, built and uploaded synchronously the first
+ * time a given set of plans and buffers is submitted -- do that before any
+ * capture; the library keeps the tables of the last 64 such sets).  A plan may appear only
  * once per batch (each owns one workspace).  The solves are spread over up to
  * 8 internal streams of the library that fork from and join back into
  * `stream`: the batch starts after the work already enqueued on `stream`, and

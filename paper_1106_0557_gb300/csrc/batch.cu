@@ -164,25 +164,65 @@ k_batch_y(const BatchGrid *__restrict__ grids, const BatchItem *__restrict__ ite
 }
 
 // ---------------------------------------------------------------------
-// K3 on a batch: z tiles of ZCfg (TX columns of the line pair ky, My - ky),
-// staged into shared memory with plain loads (the single-solve kernel's
-// tensor copies need one tensor map per grid), then z_tile.
+// K3 on a batch: z tiles of ZCfg (TX columns of the line pair ky, My - ky).
+// The kernel is persistent over its items; each item's tiles and spectrum
+// blocks are staged into shared memory by cp.async one item ahead (two
+// staging sets), so the copies of the next item overlap the transforms of
+// this one.  (The single-solve kernel's tensor copies would need one tensor
+// map per grid.)
 // ---------------------------------------------------------------------
 template <int L>
 struct BZ {
     using C = ZCfg<float, L>;
     static constexpr int SUB = kBatchColThreads / C::THREADS;
     static_assert(SUB >= 1 && SUB * C::THREADS == kBatchColThreads, "batched z tiles fill the CTA");
-    static constexpr size_t XCH2 = 2 * C::XCH;  // two exchange buffers
-    static constexpr size_t ONE = XCH2 + C::IN_SET + C::G_SET;
-    static constexpr size_t SMEM = (size_t)SUB * ONE;
+    static_assert(C::TX % 2 == 0, "16-byte copies of tile rows");
+    static constexpr size_t XCH2 = 2 * C::XCH;  // two exchange buffers per tile
+    static constexpr size_t STAGE = C::IN_SET + C::G_SET;  // one tile's input and spectrum blocks
+    static constexpr size_t SMEM_X = (size_t)SUB * XCH2, SMEM_S = (size_t)SUB * STAGE;
     static_assert(C::XCH % 16 == 0 && C::IN_SET % 16 == 0 && C::G_SET % 16 == 0, "16-byte aligned regions");
     __host__ __device__ static int64_t tiles(const BatchGrid &g) { return (int64_t)((g.Kx + C::TX - 1) / C::TX) * (g.My / 2); }
     __host__ __device__ static int64_t items(const BatchGrid &g) { return (tiles(g) + SUB - 1) / SUB; }
 };
 
+// Issue the copies of one item's tiles into staging set `S` (this thread's
+// share; every thread then commits one group).  Rows of planes z >= Nz
+// arrive as zeros; the batched classes have Kx a multiple of TX, so no
+// tile column lies past Kx.
 template <int L>
-__device__ __forceinline__ void batch_z(const BatchGrid &g, uint32_t idx, unsigned char *smem)
+__device__ __forceinline__ void batch_z_stage(const BatchGrid &g, uint32_t idx, unsigned char *S)
+{
+    using B = BZ<L>;
+    using C = typename B::C;
+    constexpr int TX = C::TX, Lh = L / 2, CH = TX / 2;  // 16-byte chunks per row
+    const int s = threadIdx.x / C::THREADS, lt = threadIdx.x % C::THREADS;
+    const int ntx = g.Kx / TX;
+    const int64_t tile = (int64_t)idx * B::SUB + s;
+    const bool live = tile < B::tiles(g);
+    const int pr = live ? (int)(tile / ntx) : 0, xt = live ? (int)(tile % ntx) : 0;
+    const int ky1 = pr == 0 ? g.My / 2 : g.My - pr;
+    unsigned char *base = S + (size_t)s * B::STAGE;
+    Cx<float> *s_in = reinterpret_cast<Cx<float> *>(base);
+    float *s_g = reinterpret_cast<float *>(base + C::IN_SET);
+    for (int i = lt; i < 2 * Lh * CH; i += C::THREADS) {
+        const int gi = i / (Lh * CH), r = i % (Lh * CH), z = r / CH, q = r % CH;
+        const bool ok = live && z < g.Nz;
+        const Cx<float> *src = ok ? g.W + ((size_t)z * g.My + (gi == 0 ? pr : ky1)) * g.Kx + xt * TX + 2 * q : g.W;
+        cp_async<16>(s_in + (size_t)(gi * Lh + z) * TX + 2 * q, src, ok);
+    }
+    const ZSpecLayout lay{TX, ntx, Lh + 1, C::GBLK};
+    for (int i = lt; i < 2 * C::GBLK / 4; i += C::THREADS) {
+        const int b = i / (C::GBLK / 4), j = i % (C::GBLK / 4);
+        const bool ok = live && (b == 0 || pr == 0);
+        const float *src = ok ? g.G + lay.block(b == 0 ? pr : g.My / 2, xt) + 4 * j : g.G;
+        cp_async<16>(s_g + (size_t)b * C::GBLK + 4 * j, src, ok);
+    }
+}
+
+// The transforms of one staged item (its SUB tiles side by side).
+template <int L>
+__device__ __forceinline__ void batch_z_compute(const BatchGrid &g, uint32_t idx, const unsigned char *S,
+                                                unsigned char *X)
 {
     using B = BZ<L>;
     using C = typename B::C;
@@ -190,35 +230,19 @@ __device__ __forceinline__ void batch_z(const BatchGrid &g, uint32_t idx, unsign
     using Rad = typename ZShape<float, L>::Rad;
     const int s = threadIdx.x / C::THREADS, lt = threadIdx.x % C::THREADS;
     const int c = lt % TX, grp = (lt / TX) & 1, t = lt / COLS;
-    const int ntx = (g.Kx + TX - 1) / TX;
+    const int ntx = g.Kx / TX;
     const int64_t tile = (int64_t)idx * B::SUB + s;
     const bool live = tile < B::tiles(g);
     const int pr = live ? (int)(tile / ntx) : 0, xt = live ? (int)(tile % ntx) : 0;
-    const int Kx = live ? g.Kx : 0;
-    unsigned char *base = smem + (size_t)s * B::ONE;
-    Cx<float> *xch_buf = reinterpret_cast<Cx<float> *>(base);
-    Cx<float> *s_in = reinterpret_cast<Cx<float> *>(base + B::XCH2);
-    float *s_g = reinterpret_cast<float *>(base + B::XCH2 + C::IN_SET);
-    const ZSpecLayout lay{TX, ntx, Lh + 1, C::GBLK};
-    // stage the tile: planes z < Lh of both line groups (zeros from Nz on and
-    // past Kx), and the spectrum block(s)
-    const int ky1 = pr == 0 ? g.My / 2 : g.My - pr;
-    for (int i = lt; i < 2 * Lh * TX; i += C::THREADS) {
-        const int gi = i / (Lh * TX), r = i % (Lh * TX), z = r / TX, cc = r % TX;
-        const int kx = xt * TX + cc;
-        Cx<float> v = {0.0f, 0.0f};
-        if (z < g.Nz && kx < Kx) v = g.W[((size_t)z * g.My + (gi == 0 ? pr : ky1)) * g.Kx + kx];
-        s_in[i] = v;
-    }
-    for (int i = lt; i < 2 * C::GBLK; i += C::THREADS) {
-        const int b = i / C::GBLK, j = i % C::GBLK;
-        s_g[i] = (live && (b == 0 || pr == 0)) ? g.G[lay.block(b == 0 ? pr : g.My / 2, xt) + j] : 0.0f;
-    }
-    __syncthreads();
+    const int Kx = live ? g.Kx : 0;  // a tile-less sub-group stores nothing
+    const unsigned char *base = S + (size_t)s * B::STAGE;
+    const Cx<float> *s_in = reinterpret_cast<const Cx<float> *>(base);
+    const float *s_g = reinterpret_cast<const float *>(base + C::IN_SET);
     typename ZTwiddles<C::TWR, float, L, E, Rad>::type twr;
     twr.load(g.tw_z, t);
     auto hook = [](int) {};
-    ZXch<float, L, E, COLS, C::SWZ, true, decltype(hook)> xch{xch_buf, grp * TX + c, hook};
+    ZXch<float, L, E, COLS, C::SWZ, true, decltype(hook)> xch{
+        reinterpret_cast<Cx<float> *>(X + (size_t)s * B::XCH2), grp * TX + c, hook};
     const float *sg = s_g + (pr == 0 ? grp : 0) * C::GBLK;
     // every sub-group meets the packed column's barriers (the sub-groups'
     // tiles differ in xt)
@@ -226,19 +250,57 @@ __device__ __forceinline__ void batch_z(const BatchGrid &g, uint32_t idx, unsign
                                twr, g.tw_z, xch, [] { return true; });
 }
 
+template <int... I>
+struct BZMax;
+template <>
+struct BZMax<> {
+    static constexpr size_t X = 0, S = 0;
+};
+template <int I, int... R>
+struct BZMax<I, R...> {
+    static constexpr size_t X = BZ<kBatchCols[I]>::SMEM_X > BZMax<R...>::X ? BZ<kBatchCols[I]>::SMEM_X : BZMax<R...>::X;
+    static constexpr size_t S = BZ<kBatchCols[I]>::SMEM_S > BZMax<R...>::S ? BZ<kBatchCols[I]>::SMEM_S : BZMax<R...>::S;
+};
+using BZAll = BZMax<0, 1, 2, 3, 4, 5, 6>;
+constexpr size_t kBatchZSmem = BZAll::X + 2 * BZAll::S;
+
 __global__ void __launch_bounds__(kBatchColThreads)
-k_batch_z(const BatchGrid *__restrict__ grids, const BatchItem *__restrict__ items)
+k_batch_z(const BatchGrid *__restrict__ grids, const BatchItem *__restrict__ items, int nitems)
 {
     extern __shared__ __align__(16) unsigned char bsm[];
-    const BatchItem it = items[blockIdx.x];
-    const BatchGrid &g = grids[it.grid_cls >> 8];
-    switch (it.grid_cls & 255) {
-#define X_(i) \
-    case i: batch_z<kBatchCols[i]>(g, it.idx, bsm); break;
-        X_(0) X_(1) X_(2) X_(3) X_(4) X_(5) X_(6)
+    unsigned char *X = bsm, *S[2] = {bsm + BZAll::X, bsm + BZAll::X + BZAll::S};
+    auto stage = [&](int i, unsigned char *dst) {
+        const BatchItem it = items[i];
+        const BatchGrid &g = grids[it.grid_cls >> 8];
+        switch (it.grid_cls & 255) {
+#define X_(k) \
+    case k: batch_z_stage<kBatchCols[k]>(g, it.idx, dst); break;
+            X_(0) X_(1) X_(2) X_(3) X_(4) X_(5) X_(6)
 #undef X_
-    default: break;
+        default: break;
+        }
+    };
+    int i = blockIdx.x, buf = 0;
+    if (i < nitems) stage(i, S[0]);
+    cp_async_commit();
+    for (; i < nitems; i += gridDim.x, buf ^= 1) {
+        const int next = i + gridDim.x;
+        if (next < nitems) stage(next, S[buf ^ 1]);  // the other set was last read before the loop's barrier
+        cp_async_commit();
+        cp_async_wait<1>();  // this item's copies (this thread's) have landed
+        __syncthreads();     // ... and every thread's
+        const BatchItem it = items[i];
+        const BatchGrid &g = grids[it.grid_cls >> 8];
+        switch (it.grid_cls & 255) {
+#define X_(k) \
+    case k: batch_z_compute<kBatchCols[k]>(g, it.idx, S[buf], X); break;
+            X_(0) X_(1) X_(2) X_(3) X_(4) X_(5) X_(6)
+#undef X_
+        default: break;
+        }
+        __syncthreads();  // the set is refilled by the next iteration's prefetch
     }
+    cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------------
@@ -291,14 +353,7 @@ static size_t col_smem()
 #undef X_
     return m;
 }
-static size_t z_smem_max()
-{
-    size_t m = 0;
-#define X_(i) m = std::max(m, BZ<kBatchCols[i]>::SMEM);
-    X_(0) X_(1) X_(2) X_(3) X_(4) X_(5) X_(6)
-#undef X_
-    return m;
-}
+static size_t z_smem_max() { return kBatchZSmem; }
 
 // The device tables of one batch: grids, then the five passes' items.
 struct BatchTables {
@@ -426,7 +481,20 @@ cudaError_t batch_enqueue(const BatchGridDesc *descs, int count, cudaStream_t st
         count_launch();
     }
     if (tb.count[2]) {
-        k_batch_z<<<tb.count[2], kBatchColThreads, z_smem_max(), st>>>(tb.grids, tb.items[2]);
+        // persistent: as many CTAs as are resident (one per SM at this size)
+        static std::atomic<int> zgrid{0};
+        int grid = zgrid.load();
+        if (grid == 0) {
+            int sms = 0, per = 0;
+            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_z, kBatchColThreads, z_smem_max());
+            if (e != cudaSuccess) return e;
+            grid = sms * (per > 0 ? per : 1);
+            zgrid.store(grid);
+        }
+        if (grid > tb.count[2]) grid = tb.count[2];
+        k_batch_z<<<grid, kBatchColThreads, z_smem_max(), st>>>(tb.grids, tb.items[2], tb.count[2]);
         count_launch();
     }
     if (tb.count[3]) {

@@ -190,11 +190,12 @@ def test_batch_matches_single_solves():
         p.close()
 
 
-def test_ragged_batch_of_64_runs_in_five_launches():
-    """The config-4 batch (64 grids, each axis from {32,48,64,96,128}, FP32):
-    one launch per pass over all grids (a table of work items), results
-    bitwise those of the single solves."""
+def test_ragged_batch_of_64_runs_in_five_launches(monkeypatch):
+    """The config-4 batch (64 grids, each axis from {32,48,64,96,128}, FP32)
+    with ISOFFT_BATCH_FUSED=1: one launch per pass over all grids (a table
+    of work items), results bitwise those of the single solves."""
     from paper_1106_0557_gb300 import Plan, submit_batch
+    monkeypatch.setenv("ISOFFT_BATCH_FUSED", "1")
     wl = sources.ragged_batch(count=64)
     plans = [Plan(w.N, w.h, "f32") for w in wl]
     srcs = [torch.from_numpy(w.source(np.float32)).cuda() for w in wl]
@@ -213,12 +214,14 @@ def test_ragged_batch_of_64_runs_in_five_launches():
         p.close()
 
 
-def test_mixed_batch_fused_and_per_grid():
-    """A batch mixing small FP32 grids (one launch per pass), an FP64 grid
-    and an FP32 grid beyond the batched lengths (their own passes on the
-    library's streams): every result bitwise its single solve's, and in
-    place (d_src = d_phi) too."""
+@pytest.mark.parametrize("fused", ["0", "1"])
+def test_mixed_batch_fused_and_per_grid(fused, monkeypatch):
+    """A batch mixing small FP32 grids (with ISOFFT_BATCH_FUSED=1 one launch
+    per pass), an FP64 grid and an FP32 grid beyond the batched lengths
+    (their own passes on the library's streams): every result bitwise its
+    single solve's, and in place (d_src = d_phi) too."""
     from paper_1106_0557_gb300 import Plan, submit_batch
+    monkeypatch.setenv("ISOFFT_BATCH_FUSED", fused)
     shapes = [((40, 33, 24), "f32"), ((20, 70, 9), "f32"), ((48, 48, 48), "f64"), ((150, 20, 16), "f32"),
               ((17, 5, 100), "f32"), ((33, 64, 20), "df64")]
     plans, srcs, singles = [], [], []
