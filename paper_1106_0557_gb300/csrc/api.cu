@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <atomic>
 #include <map>
+#include <condition_variable>
 #include <mutex>
 #include <new>
 #include <tuple>
@@ -107,9 +108,11 @@ struct SpecEntry {
     size_t bytes = 0;
     int refs = 0;
     uint64_t last_use = 0;
+    bool ready = false;  // false while a thread builds it (the cache lock is not held then)
 };
 
 static std::mutex g_cache_mu;
+static std::condition_variable g_cache_cv;  // an entry was published or dropped
 static std::map<SpecKey, SpecEntry> g_cache;
 static uint64_t g_clock = 0;
 
@@ -512,15 +515,36 @@ static void spectrum_save(const SpecKey &k, const SpecEntry &e, cudaStream_t st)
     if (fclose(f) != 0 || !ok || rename(tmp, path) != 0) remove(tmp);
 }
 
+// The cache lock is held only to look up, reserve and publish an entry: the
+// allocation, the file read or the build, and the file write of a missing
+// spectrum run outside it (other plans, cache queries and trims go on
+// meanwhile); a plan that needs a spectrum another thread is building waits
+// for it to be published.
 int acquire_spectrum(ipf_plan_s *p, cudaStream_t st)
 {
-    std::lock_guard<std::mutex> lk(g_cache_mu);
-    auto it = g_cache.find(p->key);
-    if (it == g_cache.end()) {
-        SpecEntry e;
-        e.bytes = spectrum_bytes(p->M, p->dtype);
-        cudaError_t ce = dev_alloc(&e.G, e.bytes, "spectrum");
-        if (ce != cudaSuccess) return cuda_status(ce);
+    std::unique_lock<std::mutex> lk(g_cache_mu);
+    for (;;) {
+        auto it = g_cache.find(p->key);
+        if (it == g_cache.end()) break;
+        if (it->second.ready) {
+            it->second.refs += 1;
+            it->second.last_use = ++g_clock;
+            p->spec = &it->second;
+            return IPF_OK;
+        }
+        g_cache_cv.wait(lk);  // being built by another thread
+    }
+    // reserve the entry (a reference keeps trims away from it)
+    SpecEntry e;
+    e.bytes = spectrum_bytes(p->M, p->dtype);
+    e.refs = 1;
+    auto it = g_cache.emplace(p->key, e).first;
+    lk.unlock();
+
+    void *G = nullptr;
+    cudaError_t ce = dev_alloc(&G, e.bytes, "spectrum");
+    if (ce == cudaSuccess) {
+        e.G = G;
         const size_t es = elem_size(p->dtype);
         const size_t Y = p->M[1] / 2 + 1, Z = p->M[2] / 2 + 1;
         e.Gs = (char *)e.G + e.bytes - es * Y * Z;
@@ -537,17 +561,23 @@ int acquire_spectrum(ipf_plan_s *p, cudaStream_t st)
                 ce = build_green_spectrum<double>(p->M, p->key.hn, (double *)e.G, (double *)e.Gs, st);
             else
                 ce = build_green_spectrum<df64>(p->M, p->key.hn, (df64 *)e.G, (df64 *)e.Gs, st);
-            if (ce != cudaSuccess) {
-                free_entry(e);
-                return cuda_status(ce);
-            }
-            spectrum_save(p->key, e, st);
+            if (ce == cudaSuccess) spectrum_save(p->key, e, st);
         }
-        it = g_cache.emplace(p->key, e).first;
     }
-    it->second.refs += 1;
+
+    lk.lock();
+    if (ce != cudaSuccess) {
+        free_entry(e);
+        g_cache.erase(it);
+        g_cache_cv.notify_all();
+        return cuda_status(ce);
+    }
+    it->second.G = e.G;
+    it->second.Gs = e.Gs;
+    it->second.ready = true;
     it->second.last_use = ++g_clock;
     p->spec = &it->second;
+    g_cache_cv.notify_all();
     return IPF_OK;
 }
 
@@ -1078,7 +1108,8 @@ int ipf_greens_cache_trim(size_t budget)
     while (b > budget) {
         auto victim = g_cache.end();
         for (auto it = g_cache.begin(); it != g_cache.end(); ++it)
-            if (it->second.refs == 0 && (victim == g_cache.end() || it->second.last_use < victim->second.last_use))
+            if (it->second.ready && it->second.refs == 0 &&
+                (victim == g_cache.end() || it->second.last_use < victim->second.last_use))
                 victim = it;
         if (victim == g_cache.end()) break;
         b -= victim->second.bytes;
