@@ -532,7 +532,7 @@ def run_isofft(args, ws, rank, local):
     def timed_solves(dtype, steps, warmup, pool=4):
         tdt = torch.float32 if dtype == "f32" else torch.float64  # df64 reads and writes FP64 arrays
         plan = Plan(N, w.h, dtype, flags=native.IPF_FLAG_PASS_EVENTS)
-        forms[dtype] = ["tiles" if v == 0 else "streamed" for v in plan.variants]
+        forms[dtype] = [("tiles", "streamed", "narrow tiles")[v] for v in plan.variants]
         base = torch.from_numpy(src64).to(dev, tdt)
         srcs = [base.clone() for _ in range(pool)]
         outs = [torch.empty_like(base) for _ in range(pool)]

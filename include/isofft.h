@@ -76,8 +76,8 @@ enum {
                                        ipf_plan_pass_times can report them */
     IPF_FLAG_Y_TILES = 1u << 1,     /* run the y passes in their tile form  */
     IPF_FLAG_Y_STREAM = 1u << 2,    /* run the y passes in their streamed form
-                                       (neither flag: the plan times both forms
-                                       and keeps the faster, see
+                                       (no y-form flag: the plan times the
+                                       three forms and keeps the fastest, see
                                        ipf_plan_variants) */
     IPF_FLAG_TEST_WAIT_RUNOUT = 1u << 3, /* test hook: the z pass's first tile
                                        on each CTA expects 16 bytes more than
@@ -86,11 +86,14 @@ enum {
                                        reports IPF_TIMEOUT through
                                        ipf_plan_check; its potential is then
                                        unspecified */
-    IPF_FLAG_TEST_CANARY = 1u << 4  /* test hook: before every solve the
+    IPF_FLAG_TEST_CANARY = 1u << 4, /* test hook: before every solve the
                                        plan's workspace is filled with NaN
                                        bytes, so a pass that read an element
                                        no earlier pass of that solve wrote
                                        would show in the potential */
+    IPF_FLAG_Y_TILES_NARROW = 1u << 5 /* run the y passes in their tile form
+                                       on tiles of half the width (at most one
+                                       of the three y-form flags) */
 };
 /* Two more test hooks are read from the environment:
  *   ISOFFT_TEST_FAIL_ALLOC=workspace|tables|spectrum|staging  the device
@@ -250,13 +253,16 @@ int ipf_plan_pass_times(ipf_plan_t plan, float ms[5]);
 
 /* The form each y pass of the plan runs in, v[0] for the forward and v[1]
  * for the inverse pass: 0 tiles (one CTA per column tile, plain loads), 1
- * streamed (persistent CTAs fed by tensor-map copies).  Both give bitwise
- * the same potential.  Unless a flag forces one, ipf_plan_create times both
- * forms on the plan's own workspace (a few launches of each) and keeps the
- * faster; the choice is remembered per (dtype, mesh, shape, device) for the
- * process, and in the file named by the environment variable
- * ISOFFT_TUNE_FILE if set (read at the first plan, appended as choices are
- * made).  ISOFFT_TUNE=0 skips the timing and takes the built-in rule. */
+ * streamed (persistent CTAs fed by tensor-map copies), 2 tiles of half the
+ * width (twice the CTAs, half the threads and shared memory each).  All give
+ * bitwise the same potential.  Unless a flag forces one, ipf_plan_create
+ * times the three forms on the plan's own workspace (a few launches of each)
+ * and keeps the fastest per pass; the choice is remembered per (dtype, mesh,
+ * shape, device) for the process, and in the file named by the environment
+ * variable ISOFFT_TUNE_FILE if set (read at the first plan, rewritten as
+ * choices are made).  ISOFFT_TUNE=0 skips the timing and takes the built-in
+ * rule (streamed for FP32 lines of 512 to 1024 points, tiles elsewhere).
+ * Not in the paper: the tuning of this implementation's tile shapes. */
 int ipf_plan_variants(const ipf_plan_t plan, int v[2]);
 
 /* Bytes held by the library's cache of Green's spectra, and a trim of

@@ -272,10 +272,11 @@ int read_status(ipf_plan_s *p, cudaStream_t st)
 }
 
 // ---------------------------------------------------------------------
-// y-pass form tuning: both forms run a few times on the plan's workspace and
-// the faster is kept, per (dtype, My, Kx, Ny, Nz, device capability); the
-// choices persist for the process and, with ISOFFT_TUNE_FILE, in a JSON
-// file of entries [dtype, My, Kx, Ny, Nz, sm, forward, inverse].
+// y-pass form tuning: the three forms (tiles, streamed, half-width tiles)
+// run a few times each on the plan's workspace and the fastest is kept per
+// direction, per (dtype, My, Kx, Ny, Nz, device capability); the choices
+// persist for the process and, with ISOFFT_TUNE_FILE, in a JSON file of
+// entries [dtype, My, Kx, Ny, Nz, sm, forward, inverse].
 // ---------------------------------------------------------------------
 struct TuneKey {
     int v[6];
@@ -313,7 +314,7 @@ void tune_file_load()
         TuneKey k;
         for (int j = 0; j < 6; ++j) k.v[j] = (int)nums[i + j];
         const int a = (int)nums[i + 6], b = (int)nums[i + 7];
-        if ((a == kYTile || a == kYStream) && (b == kYTile || b == kYStream)) g_tune[k] = {a, b};
+        if (a >= 0 && a < kYForms && b >= 0 && b < kYForms) g_tune[k] = {a, b};
     }
 }
 
@@ -353,8 +354,10 @@ template <typename T>
 int tune_y(ipf_plan_s *p, cudaStream_t st)
 {
     const int Ny = (int)p->N[1], Nz = (int)p->N[2], My = (int)p->M[1], Lx = (int)(p->M[0] / 2);
-    if (p->flags & (IPF_FLAG_Y_TILES | IPF_FLAG_Y_STREAM)) {
-        p->yvar[0] = p->yvar[1] = (p->flags & IPF_FLAG_Y_STREAM) ? kYStream : kYTile;
+    if (p->flags & (IPF_FLAG_Y_TILES | IPF_FLAG_Y_STREAM | IPF_FLAG_Y_TILES_NARROW)) {
+        p->yvar[0] = p->yvar[1] = (p->flags & IPF_FLAG_Y_STREAM)         ? kYStream
+                                  : (p->flags & IPF_FLAG_Y_TILES_NARROW) ? kYTileNarrow
+                                                                         : kYTile;
         return IPF_OK;
     }
     const char *env = getenv("ISOFFT_TUNE");
@@ -380,8 +383,8 @@ int tune_y(ipf_plan_s *p, cudaStream_t st)
     cudaError_t e = cudaEventCreate(&a);
     if (e == cudaSuccess) e = cudaEventCreate(&b);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->W, 0, p->W_bytes, st);
-    float t[2][2] = {{0, 0}, {0, 0}};
-    for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+    float t[2][kYForms] = {};
+    for (int v = 0; v < kYForms && e == cudaSuccess; ++v) {
         t[0][v] = time_launches([&] { return launch_y_forward<T>(My, p->W, p->tw_y, Ny, Lx, Nz, p->status, v, st); },
                                 st, a, b, &e);
         if (e == cudaSuccess)
@@ -391,10 +394,15 @@ int tune_y(ipf_plan_s *p, cudaStream_t st)
     if (a) cudaEventDestroy(a);
     if (b) cudaEventDestroy(b);
     if (e != cudaSuccess) return cuda_status(e);
-    p->yvar[0] = t[0][kYStream] < t[0][kYTile] ? kYStream : kYTile;
-    p->yvar[1] = t[1][kYStream] < t[1][kYTile] ? kYStream : kYTile;
-    logf(IPF_CONSOLE_INFO_2, p->verbosity, "y forms for mesh %dx%d: forward %.4f/%.4f ms, inverse %.4f/%.4f ms",
-         My, Lx, t[0][0], t[0][1], t[1][0], t[1][1]);
+    for (int d = 0; d < 2; ++d) {
+        int best = kYTile;
+        for (int v = 1; v < kYForms; ++v)
+            if (t[d][v] < t[d][best]) best = v;
+        p->yvar[d] = best;
+    }
+    logf(IPF_CONSOLE_INFO_2, p->verbosity,
+         "y forms for mesh %dx%d (tiles/streamed/narrow tiles): forward %.4f/%.4f/%.4f ms, inverse %.4f/%.4f/%.4f ms",
+         My, Lx, t[0][0], t[0][1], t[0][2], t[1][0], t[1][1], t[1][2]);
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[key] = {p->yvar[0], p->yvar[1]};
     tune_file_save();
@@ -830,9 +838,12 @@ int ipf_plan_create(ipf_plan_t *out, const int64_t n[3], const double h[3], int 
     int rc = validate(n, h, dtype);
     if (rc) return rc;
     if (flags & ~(uint32_t)(IPF_FLAG_PASS_EVENTS | IPF_FLAG_Y_TILES | IPF_FLAG_Y_STREAM | IPF_FLAG_TEST_WAIT_RUNOUT |
-                            IPF_FLAG_TEST_CANARY))
+                            IPF_FLAG_TEST_CANARY | IPF_FLAG_Y_TILES_NARROW))
         return IPF_INVALID_ARG;
-    if ((flags & IPF_FLAG_Y_TILES) && (flags & IPF_FLAG_Y_STREAM)) return IPF_INVALID_ARG;
+    {
+        const uint32_t forms = flags & (IPF_FLAG_Y_TILES | IPF_FLAG_Y_STREAM | IPF_FLAG_Y_TILES_NARROW);
+        if (forms & (forms - 1)) return IPF_INVALID_ARG;  // at most one form forced
+    }
     if (verbosity < IPF_CONSOLE_ERROR || verbosity > IPF_CONSOLE_INFO_2) return IPF_INVALID_ARG;
     const int ev = env_verbosity();
     if (ev >= 0) verbosity = ev;

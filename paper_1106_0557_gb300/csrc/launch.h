@@ -26,11 +26,13 @@ cudaError_t launch_x_forward(int L, const typename IoReal<T>::type *src, void *W
 template <typename T>
 cudaError_t launch_x_inverse(int L, const void *W, typename IoReal<T>::type *phi, const void *tw, const void *rtw,
                              int Nx, int Ny, int My, int64_t nrows, cudaStream_t st);
-// The y passes come in two forms with bitwise the same arithmetic:
-//   kYTile   one CTA per column tile (plain loads; many CTAs per SM),
-//   kYStream persistent CTAs fed by tensor-map copies (see passes.cuh).
-// Plans pick one per pass by timing both (y_default_variant without).
-enum { kYTile = 0, kYStream = 1 };
+// The y passes come in three forms with bitwise the same arithmetic:
+//   kYTile        one CTA per column tile (plain loads; many CTAs per SM),
+//   kYStream      persistent CTAs fed by tensor-map copies (see passes.cuh),
+//   kYTileNarrow  the tile form on tiles of half the width.
+// Plans pick one per pass by timing all three (y_default_variant without).
+enum { kYTile = 0, kYStream = 1, kYTileNarrow = 2 };
+constexpr int kYForms = 3;
 template <typename T>
 cudaError_t launch_y_forward(int L, void *W, const void *tw, int Ny, int Kx, int Nz, unsigned *status, int variant,
                              cudaStream_t st);

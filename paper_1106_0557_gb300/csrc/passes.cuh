@@ -181,14 +181,18 @@ struct RowCfg {
 // most 512 threads, so two or three tiles are resident per SM and one tile's
 // global loads overlap the others' butterflies; rows of at least 32 bytes
 // (one sector) even where that takes more threads (FP32 2304-point lines).
-template <typename T, int L>
+// NARROW: tiles of half that width (at least one column), the third y-pass
+// form the plan's timing chooses from (half the threads and shared memory
+// per CTA, twice the CTAs).
+template <typename T, int L, bool NARROW = false>
 struct ColCfg {
     static constexpr int E = Shape<T, L>::E;
     static constexpr int NT = L / E;
     static constexpr int TX0 = 128 / (int)sizeof(Cx<T>);
     static constexpr int TXS = 32 / (int)sizeof(Cx<T>);  // one 32-byte sector
     static constexpr int TXT = TX0 * NT <= 512 ? TX0 : (512 / NT >= 1 ? 512 / NT : 1);
-    static constexpr int TX = TXT >= TXS || TXS * NT > 1024 ? TXT : TXS;
+    static constexpr int TXW = TXT >= TXS || TXS * NT > 1024 ? TXT : TXS;
+    static constexpr int TX = NARROW ? (TXW > 1 ? TXW / 2 : 1) : TXW;
     static constexpr int THREADS = TX * NT;
     static constexpr size_t SMEM = (size_t)L * TX * sizeof(Cx<T>);
     // FP32 forward: registers low enough for 3 resident CTAs per SM with 8
@@ -641,21 +645,21 @@ k_x_inverse(const Cx<T> *__restrict__ W, In<T> *__restrict__ phi, const Cx<T> *_
 // keep the loads in flight; best where the persistent form (below) would
 // hold fewer warps per SM (small lines, 16-byte points).
 // ---------------------------------------------------------------------
-template <typename T, int L>
-__global__ void __launch_bounds__(ColCfg<T, L>::THREADS, ColCfg<T, L>::MIN_BLOCKS_FWD)
+template <typename T, int L, bool NARROW = false>
+__global__ void __launch_bounds__(ColCfg<T, L, NARROW>::THREADS, ColCfg<T, L, NARROW>::MIN_BLOCKS_FWD)
 k_y_forward(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx)
 {
-    using C = ColCfg<T, L>;
+    using C = ColCfg<T, L, NARROW>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     y_forward_tile<T, L, C::TX>(W, tw, Ny, Kx, blockIdx.y, blockIdx.x * C::TX, reinterpret_cast<Cx<T> *>(smem_raw),
                                 threadIdx.x % C::TX, threadIdx.x / C::TX);
 }
 
-template <typename T, int L>
-__global__ void __launch_bounds__(ColCfg<T, L>::THREADS)
+template <typename T, int L, bool NARROW = false>
+__global__ void __launch_bounds__(ColCfg<T, L, NARROW>::THREADS)
 k_y_inverse(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx)
 {
-    using C = ColCfg<T, L>;
+    using C = ColCfg<T, L, NARROW>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     y_inverse_tile<T, L, C::TX>(W, tw, Ny, Kx, blockIdx.y, blockIdx.x * C::TX, reinterpret_cast<Cx<T> *>(smem_raw),
                                 threadIdx.x % C::TX, threadIdx.x / C::TX);

@@ -150,12 +150,12 @@ template cudaError_t launch_x_inverse<Real>(int, const void *, In<Real> *, const
 #endif
 
 #if ISOFFT_GROUP == 2
-template <typename T, int L, bool FWD>
+template <typename T, int L, bool FWD, bool NARROW>
 static cudaError_t run_y_tile(void *W, const void *tw, int Ny, int Kx, int Nz, cudaStream_t st)
 {
-    using C = ColCfg<T, L>;
+    using C = ColCfg<T, L, NARROW>;
     static std::atomic<uint64_t> done{0};
-    auto *k = FWD ? k_y_forward<T, L> : k_y_inverse<T, L>;
+    auto *k = FWD ? k_y_forward<T, L, NARROW> : k_y_inverse<T, L, NARROW>;
     cudaError_t e = ensure_smem(k, C::SMEM, done);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((Kx + C::TX - 1) / C::TX), (unsigned)Nz);
@@ -199,8 +199,9 @@ template <typename T, int L, bool FWD>
 static cudaError_t run_y(void *W, const void *tw, int Ny, int Kx, int Nz, unsigned *status, int variant,
                          cudaStream_t st)
 {
-    return variant == kYStream ? run_y_stream<T, L, FWD>(W, tw, Ny, Kx, Nz, status, st)
-                               : run_y_tile<T, L, FWD>(W, tw, Ny, Kx, Nz, st);
+    if (variant == kYStream) return run_y_stream<T, L, FWD>(W, tw, Ny, Kx, Nz, status, st);
+    if (variant == kYTileNarrow) return run_y_tile<T, L, FWD, true>(W, tw, Ny, Kx, Nz, st);
+    return run_y_tile<T, L, FWD, false>(W, tw, Ny, Kx, Nz, st);
 }
 template <typename R_>
 cudaError_t launch_y_forward(int L, void *W, const void *tw, int Ny, int Kx, int Nz, unsigned *status, int variant,

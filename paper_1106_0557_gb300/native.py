@@ -35,6 +35,7 @@ IPF_FLAG_Y_TILES = 2
 IPF_FLAG_Y_STREAM = 4
 IPF_FLAG_TEST_WAIT_RUNOUT = 8
 IPF_FLAG_TEST_CANARY = 16
+IPF_FLAG_Y_TILES_NARROW = 32
 
 DTYPES = {"f32": IPF_F32, "f64": IPF_F64, "df64": IPF_DF64, IPF_F32: IPF_F32, IPF_F64: IPF_F64,
           IPF_DF64: IPF_DF64}

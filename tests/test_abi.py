@@ -68,11 +68,13 @@ def test_bad_dtype_and_flags():
     rc = native.lib().ipf_plan_create(ctypes.byref(ctypes.c_void_p()), (ctypes.c_int64 * 3)(4, 4, 4),
                                       (ctypes.c_double * 3)(1, 1, 1), 0, 1 << 9, 0, None)
     assert rc == native.IPF_INVALID_ARG
-    # the two y-pass forms cannot both be forced
-    rc = native.lib().ipf_plan_create(ctypes.byref(ctypes.c_void_p()), (ctypes.c_int64 * 3)(4, 4, 4),
-                                      (ctypes.c_double * 3)(1, 1, 1), 0,
-                                      native.IPF_FLAG_Y_TILES | native.IPF_FLAG_Y_STREAM, 0, None)
-    assert rc == native.IPF_INVALID_ARG
+    # at most one y-pass form can be forced
+    for two in (native.IPF_FLAG_Y_TILES | native.IPF_FLAG_Y_STREAM,
+                native.IPF_FLAG_Y_TILES | native.IPF_FLAG_Y_TILES_NARROW,
+                native.IPF_FLAG_Y_STREAM | native.IPF_FLAG_Y_TILES_NARROW):
+        rc = native.lib().ipf_plan_create(ctypes.byref(ctypes.c_void_p()), (ctypes.c_int64 * 3)(4, 4, 4),
+                                          (ctypes.c_double * 3)(1, 1, 1), 0, two, 0, None)
+        assert rc == native.IPF_INVALID_ARG
     assert native.lib().ipf_plan_create(None, None, None, 0, 0, 0, None) == native.IPF_INVALID_ARG
 
 

@@ -414,21 +414,21 @@ def test_async_host_solves_in_flight_together(dtype):
 @pytest.mark.parametrize("dtype", ["f32", "f64", "df64"])
 @pytest.mark.parametrize("N", [(64, 64, 64), (37, 200, 13), (256, 256, 40), (20, 300, 17), (9, 700, 8), (9, 1100, 8)])
 def test_y_pass_forms_are_bitwise_equal(N, dtype):
-    """The tile and streamed forms of the y passes run the same arithmetic in
-    the same order: forcing either gives bitwise the same potential, and a
-    tuned plan picks one of the two for each pass."""
+    """The three forms of the y passes (tiles, streamed, half-width tiles)
+    run the same arithmetic in the same order: forcing any gives bitwise the
+    same potential, and a tuned plan picks one of the three for each pass."""
     from paper_1106_0557_gb300 import Plan
     src = torch.from_numpy(rand_src(N, 4).astype(NP[dtype])).cuda()
     outs = []
-    for flag in (native.IPF_FLAG_Y_TILES, native.IPF_FLAG_Y_STREAM):
+    for flag, want in ((native.IPF_FLAG_Y_TILES, (0, 0)), (native.IPF_FLAG_Y_STREAM, (1, 1)),
+                       (native.IPF_FLAG_Y_TILES_NARROW, (2, 2))):
         with Plan(N, (1.0, 0.5, 1.0), dtype, flags=flag) as p:
-            want = (1, 1) if flag == native.IPF_FLAG_Y_STREAM else (0, 0)
             assert p.variants == want
             outs.append(p.solve(src))
             p.check()
-    assert torch.equal(outs[0], outs[1])
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
     with Plan(N, (1.0, 0.5, 1.0), dtype) as p:
-        assert set(p.variants) <= {0, 1}
+        assert set(p.variants) <= {0, 1, 2}
         assert torch.equal(p.solve(src), outs[0])
 
 
