@@ -167,12 +167,20 @@ struct ipf_plan_s {
     cudaEvent_t ev[kSlots][6] = {};
     bool have_events = false;
     int yvar[2] = {kYTile, kYTile};  // form of the y forward / inverse pass
+    int zsh = 0;  // the workspace's z planes in blocks of 2^zsh (plan_zsh)
     uint64_t solves = 0, folded = 0;
     double pass_sum[5] = {0, 0, 0, 0, 0};
     uint64_t pass_n = 0;
 };
 
 namespace {
+
+// z blocking of the workspace (w_row): on 2304-point z lines, blocks of
+// 2^kZBlockShift planes, where the plane count allows.
+int plan_zsh(int64_t Mz, int64_t Nz)
+{
+    return Mz == 2304 && Nz % (1 << kZBlockShift) == 0 ? kZBlockShift : 0;
+}
 
 int64_t choose_mesh(int64_t n)
 {
@@ -385,11 +393,13 @@ int tune_y(ipf_plan_s *p, cudaStream_t st)
     if (e == cudaSuccess) e = cudaMemsetAsync(p->W, 0, p->W_bytes, st);
     float t[2][kYForms] = {};
     for (int v = 0; v < kYForms && e == cudaSuccess; ++v) {
-        t[0][v] = time_launches([&] { return launch_y_forward<T>(My, p->W, p->tw_y, Ny, Lx, Nz, p->status, v, st); },
-                                st, a, b, &e);
+        t[0][v] = time_launches(
+            [&] { return launch_y_forward<T>(My, p->W, p->tw_y, Ny, Lx, Nz, p->zsh, p->status, v, st); }, st, a, b,
+            &e);
         if (e == cudaSuccess)
             t[1][v] = time_launches(
-                [&] { return launch_y_inverse<T>(My, p->W, p->tw_y, Ny, Lx, Nz, p->status, v, st); }, st, a, b, &e);
+                [&] { return launch_y_inverse<T>(My, p->W, p->tw_y, Ny, Lx, Nz, p->zsh, p->status, v, st); }, st,
+                a, b, &e);
     }
     if (a) cudaEventDestroy(a);
     if (b) cudaEventDestroy(b);
@@ -642,32 +652,32 @@ cudaError_t enqueue_solve(ipf_plan_s *p, const void *src, void *phi, cudaStream_
     if (ev_on) cudaEventRecord(ev[0], st);
     {
         PassRange r(p->nvtx, "isofft K1 x forward");
-        e = launch_x_forward<T>(Lx, (const IoT *)src, p->W, p->tw_x, p->rtw, Nx, Ny, My, nrows, st);
+        e = launch_x_forward<T>(Lx, (const IoT *)src, p->W, p->tw_x, p->rtw, Nx, Ny, My, nrows, p->zsh, st);
         if (e != cudaSuccess) return e;
     }
     if (ev_on) cudaEventRecord(ev[1], st);
     {
         PassRange r(p->nvtx, "isofft K2 y forward");
-        e = launch_y_forward<T>(My, p->W, p->tw_y, Ny, Lx, Nz, p->status, p->yvar[0], st);
+        e = launch_y_forward<T>(My, p->W, p->tw_y, Ny, Lx, Nz, p->zsh, p->status, p->yvar[0], st);
         if (e != cudaSuccess) return e;
     }
     if (ev_on) cudaEventRecord(ev[2], st);
     {
         PassRange r(p->nvtx, "isofft K3 z convolve");
         e = launch_z_convolve<T>(Mz, p->W, p->tw_z, (const T *)p->spec->G, (const T *)p->spec->Gs,
-                                 (T)p->gscale, Nz, My, Lx, p->status, runout_bytes(p), st);
+                                 (T)p->gscale, Nz, My, Lx, p->zsh, p->status, runout_bytes(p), st);
         if (e != cudaSuccess) return e;
     }
     if (ev_on) cudaEventRecord(ev[3], st);
     {
         PassRange r(p->nvtx, "isofft K4 y inverse");
-        e = launch_y_inverse<T>(My, p->W, p->tw_y, Ny, Lx, Nz, p->status, p->yvar[1], st);
+        e = launch_y_inverse<T>(My, p->W, p->tw_y, Ny, Lx, Nz, p->zsh, p->status, p->yvar[1], st);
         if (e != cudaSuccess) return e;
     }
     if (ev_on) cudaEventRecord(ev[4], st);
     {
         PassRange r(p->nvtx, "isofft K5 x inverse");
-        e = launch_x_inverse<T>(Lx, p->W, (IoT *)phi, p->tw_x, p->rtw, Nx, Ny, My, nrows, st);
+        e = launch_x_inverse<T>(Lx, p->W, (IoT *)phi, p->tw_x, p->rtw, Nx, Ny, My, nrows, p->zsh, st);
         if (e != cudaSuccess) return e;
     }
     if (ev_on) cudaEventRecord(ev[5], st);
@@ -696,7 +706,9 @@ cudaError_t enqueue_solve_host(ipf_plan_s *p, const void *h_src, void *h_phi, in
     const int Lx = (int)(p->M[0] / 2), My = (int)p->M[1], Mz = (int)p->M[2];
     const size_t plane = (size_t)Nx * Ny, wplane = (size_t)My * Lx;
     const int chunks = Nz < max_chunks ? Nz : max_chunks;
-    const int per = (Nz + chunks - 1) / chunks;
+    // chunks of whole z blocks (the workspace's blocks start every 2^zsh planes)
+    const int zb = 1 << p->zsh;
+    const int per = ((Nz + chunks - 1) / chunks + zb - 1) / zb * zb;
     const int s = p->stage_set;
     p->stage_set = (s + 1) % ipf_plan_s::kSets;
     IoT *stage = (IoT *)p->stage[s];
@@ -717,20 +729,21 @@ cudaError_t enqueue_solve_host(ipf_plan_s *p, const void *h_src, void *h_phi, in
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, p->ev_in[s][k], 0);
         if (e == cudaSuccess)
             e = launch_x_forward<T>(Lx, stage + z0 * plane, W + z0 * wplane * cs, p->tw_x, p->rtw, Nx, Ny, My,
-                                    (int64_t)nz * Ny, st);
+                                    (int64_t)nz * Ny, p->zsh, st);
         if (e == cudaSuccess)
-            e = launch_y_forward<T>(My, W + z0 * wplane * cs, p->tw_y, Ny, Lx, nz, p->status, p->yvar[0], st);
+            e = launch_y_forward<T>(My, W + z0 * wplane * cs, p->tw_y, Ny, Lx, nz, p->zsh, p->status, p->yvar[0],
+                                    st);
     }
     if (e == cudaSuccess)
         e = launch_z_convolve<T>(Mz, p->W, p->tw_z, (const T *)p->spec->G, (const T *)p->spec->Gs, (T)p->gscale, Nz,
-                                 My, Lx, p->status, runout_bytes(p), st);
+                                 My, Lx, p->zsh, p->status, runout_bytes(p), st);
     for (int k = 0; k < chunks && e == cudaSuccess; ++k) {
         const int z0 = k * per, nz = z0 + per <= Nz ? per : Nz - z0;
         if (nz <= 0) break;
-        e = launch_y_inverse<T>(My, W + z0 * wplane * cs, p->tw_y, Ny, Lx, nz, p->status, p->yvar[1], st);
+        e = launch_y_inverse<T>(My, W + z0 * wplane * cs, p->tw_y, Ny, Lx, nz, p->zsh, p->status, p->yvar[1], st);
         if (e == cudaSuccess)
             e = launch_x_inverse<T>(Lx, W + z0 * wplane * cs, stage + z0 * plane, p->tw_x, p->rtw, Nx, Ny, My,
-                                    (int64_t)nz * Ny, st);
+                                    (int64_t)nz * Ny, p->zsh, st);
         if (e == cudaSuccess) e = cudaEventRecord(p->ev_out[s][k], st);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(p->d2h_st, p->ev_out[s][k], 0);
         if (e == cudaSuccess)
@@ -874,6 +887,7 @@ int ipf_plan_create(ipf_plan_t *out, const int64_t n[3], const double h[3], int 
     p->key.device = p->device;
     p->key.dtype = dtype;
     for (int a = 0; a < 3; ++a) p->key.M[a] = p->M[a];
+    p->zsh = plan_zsh(p->M[2], p->N[2]);
 
     p->W_bytes = 2 * elem_size(dtype) * (size_t)p->N[2] * (size_t)p->M[1] * (size_t)(p->M[0] / 2);
     ce = dev_alloc(&p->W, p->W_bytes, "workspace");

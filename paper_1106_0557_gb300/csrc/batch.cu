@@ -89,9 +89,9 @@ __device__ __forceinline__ void batch_row(const BatchGrid &g, uint32_t idx, unsi
     const int64_t row = (int64_t)idx * C::NL + l;
     const bool active = row < nrows;
     if constexpr (FWD)
-        x_forward_row<float, L>(g.src, g.W, g.tw_x, g.rtw, g.Nx, g.Ny, g.My, active ? row : 0, active, line, t);
+        x_forward_row<float, L>(g.src, g.W, g.tw_x, g.rtw, g.Nx, g.Ny, g.My, active ? row : 0, active, line, t, 0);
     else
-        x_inverse_row<float, L>(g.W, g.phi, g.tw_x, g.rtw, g.Nx, g.Ny, g.My, active ? row : 0, active, line, t);
+        x_inverse_row<float, L>(g.W, g.phi, g.tw_x, g.rtw, g.Nx, g.Ny, g.My, active ? row : 0, active, line, t, 0);
 }
 
 template <bool FWD>
@@ -246,7 +246,7 @@ __device__ __forceinline__ void batch_z_compute(const BatchGrid &g, uint32_t idx
     const float *sg = s_g + (pr == 0 ? grp : 0) * C::GBLK;
     // every sub-group meets the packed column's barriers (the sub-groups'
     // tiles differ in xt)
-    z_tile<float, L, TX, true>(s_in + grp * Lh * TX, sg, pr, xt, g.W, g.Gs, g.gscale, g.Nz, g.My, Kx, c, grp, t,
+    z_tile<float, L, TX, true>(s_in + grp * Lh * TX, sg, pr, xt, g.W, g.Gs, g.gscale, g.Nz, g.My, Kx, 0, c, grp, t,
                                twr, g.tw_z, xch, [] { return true; });
 }
 

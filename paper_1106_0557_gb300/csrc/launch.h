@@ -20,12 +20,23 @@ void count_launch();
 // All pointers are device pointers of the current device; complex buffers
 // are interleaved (re, im) of the arithmetic type T; source and potential
 // arrays hold IoReal<T>::type (double for df64).
+// `zsh`: the workspace's z planes are grouped in blocks of 2^zsh (w_row in
+// passes.cuh; 0 = plain [Nz][My][Kx]).  Every launch must cover whole blocks
+// (cudaErrorInvalidValue otherwise); plans block the workspace only where the
+// z lines have 2304 points (the paired z pass).
+// Planes per z block of a blocked workspace, as a shift: 16.  The z pass
+// then reads each line group in runs of 16 rows one Kx row (9 KB at 1152^3)
+// apart instead of rows a whole plane (21 MB) apart: 32-byte strided reads
+// measured 3.5 TB/s against 1.5 TB/s, while the y passes' rows move from Kx
+// to 16 Kx apart (4.7 -> 3.2 TB/s on the same read test, on passes that are
+// bound elsewhere).
+constexpr int kZBlockShift = 4;
 template <typename T>
 cudaError_t launch_x_forward(int L, const typename IoReal<T>::type *src, void *W, const void *tw, const void *rtw,
-                             int Nx, int Ny, int My, int64_t nrows, cudaStream_t st);
+                             int Nx, int Ny, int My, int64_t nrows, int zsh, cudaStream_t st);
 template <typename T>
 cudaError_t launch_x_inverse(int L, const void *W, typename IoReal<T>::type *phi, const void *tw, const void *rtw,
-                             int Nx, int Ny, int My, int64_t nrows, cudaStream_t st);
+                             int Nx, int Ny, int My, int64_t nrows, int zsh, cudaStream_t st);
 // The y passes come in three forms with bitwise the same arithmetic:
 //   kYTile        one CTA per column tile (plain loads; many CTAs per SM),
 //   kYStream      persistent CTAs fed by tensor-map copies (see passes.cuh),
@@ -34,11 +45,11 @@ cudaError_t launch_x_inverse(int L, const void *W, typename IoReal<T>::type *phi
 enum { kYTile = 0, kYStream = 1, kYTileNarrow = 2 };
 constexpr int kYForms = 3;
 template <typename T>
-cudaError_t launch_y_forward(int L, void *W, const void *tw, int Ny, int Kx, int Nz, unsigned *status, int variant,
-                             cudaStream_t st);
+cudaError_t launch_y_forward(int L, void *W, const void *tw, int Ny, int Kx, int Nz, int zsh, unsigned *status,
+                             int variant, cudaStream_t st);
 template <typename T>
-cudaError_t launch_y_inverse(int L, void *W, const void *tw, int Ny, int Kx, int Nz, unsigned *status, int variant,
-                             cudaStream_t st);
+cudaError_t launch_y_inverse(int L, void *W, const void *tw, int Ny, int Kx, int Nz, int zsh, unsigned *status,
+                             int variant, cudaStream_t st);
 // The form used without timing: streamed for 8-byte points on lines of 512
 // to 1024 points (where it measured faster), tiles elsewhere.
 inline int y_default_variant(int L, size_t real_bytes)
@@ -51,7 +62,7 @@ inline int y_default_variant(int L, size_t real_bytes)
 // run-out test hook: bytes each CTA's first tile expects beyond its copies.
 template <typename T>
 cudaError_t launch_z_convolve(int L, void *W, const void *tw, const T *G, const T *Gs, T gscale, int Nz,
-                              int My, int Kx, unsigned *status, unsigned test_extra_tx, cudaStream_t st);
+                              int My, int Kx, int zsh, unsigned *status, unsigned test_extra_tx, cudaStream_t st);
 
 // Width (kx columns per tile) of the z pass for line length L; the cached
 // Green's spectrum is stored in tiles of this width (0: unsupported L).

@@ -130,11 +130,11 @@ int solve_noalloc(const int64_t N[3], const int64_t M[3], const double hn[3], do
     double *ct = oct + green_octant_elems(M);
     e = enqueue_green_spectrum<T>(M, hn, G, Gs, oct, ct, st);
     if (e == cudaSuccess)
-        e = launch_x_forward<T>(Lx, (const T *)src, W, tw_x, rtw, Nx, Ny, My, (int64_t)Ny * Nz, st);
-    if (e == cudaSuccess) e = launch_y_forward<T>(My, W, tw_y, Ny, Lx, Nz, (unsigned *)b, y_default_variant(My, sizeof(T)), st);
-    if (e == cudaSuccess) e = launch_z_convolve<T>(Mz, W, tw_z, G, Gs, (T)gscale, Nz, My, Lx, (unsigned *)b, 0u, st);
-    if (e == cudaSuccess) e = launch_y_inverse<T>(My, W, tw_y, Ny, Lx, Nz, (unsigned *)b, y_default_variant(My, sizeof(T)), st);
-    if (e == cudaSuccess) e = launch_x_inverse<T>(Lx, W, (T *)phi, tw_x, rtw, Nx, Ny, My, (int64_t)Ny * Nz, st);
+        e = launch_x_forward<T>(Lx, (const T *)src, W, tw_x, rtw, Nx, Ny, My, (int64_t)Ny * Nz, 0, st);
+    if (e == cudaSuccess) e = launch_y_forward<T>(My, W, tw_y, Ny, Lx, Nz, 0, (unsigned *)b, y_default_variant(My, sizeof(T)), st);
+    if (e == cudaSuccess) e = launch_z_convolve<T>(Mz, W, tw_z, G, Gs, (T)gscale, Nz, My, Lx, 0, (unsigned *)b, 0u, st);
+    if (e == cudaSuccess) e = launch_y_inverse<T>(My, W, tw_y, Ny, Lx, Nz, 0, (unsigned *)b, y_default_variant(My, sizeof(T)), st);
+    if (e == cudaSuccess) e = launch_x_inverse<T>(Lx, W, (T *)phi, tw_x, rtw, Nx, Ny, My, (int64_t)Ny * Nz, 0, st);
     return e == cudaSuccess ? IPF_OK : IPF_CUDA_ERROR;
 }
 

@@ -4,7 +4,8 @@
 //
 // Buffers (C order, x fastest):
 //   src, phi : real [Nz][Ny][Nx]
-//   W        : complex [Nz][My][Kx], Kx = Mx / 2, the plan's workspace.  The
+//   W        : complex [Nz][My][Kx], Kx = Mx / 2, the plan's workspace (on
+//              2304-point z lines in blocks of 16 planes, w_row below).  The
 //              z padding is never stored: the z pass reads z < Nz, treats the
 //              rest of its line as zero, and writes back only z < Nz.
 //   G        : real, the transform of the Eq. 9 table on the even octant (it
@@ -40,6 +41,19 @@
 #include "tma.cuh"
 
 namespace isofft {
+
+// Row (z, y) of the workspace W, in complex elements / Kx.  With zsh > 0 the
+// planes are grouped in blocks of 2^zsh: [z >> zsh][My][z & (2^zsh - 1)][Kx],
+// so that the z lines of one (kx, ky) lie 2^zsh rows apart within a block
+// (the z pass reads them in long runs of nearby rows); zsh = 0 is the plain
+// [Nz][My][Kx].  Every pass addresses W through this map.
+__host__ __device__ __forceinline__ size_t w_row(int64_t z, int64_t y, int64_t My, int zsh)
+{
+    return (size_t)((((z >> zsh) * My + y) << zsh) + (z & ((int64_t(1) << zsh) - 1)));
+}
+// A launch on nz planes of a z-blocked workspace covers whole blocks only
+// (the map above leaves the allocation otherwise).
+inline bool w_blocks_ok(int64_t nz, int zsh) { return zsh >= 0 && zsh <= 6 && (nz & ((int64_t(1) << zsh) - 1)) == 0; }
 
 // Asynchronous global -> shared copies (cp.async): BYTES = 4, 8 or 16;
 // when `valid` is false nothing is read and the slot is zero-filled.
@@ -445,11 +459,11 @@ template <typename T, int L, bool TWR = false, typename SH = XShape<T, L>>
 __device__ __forceinline__ void x_forward_row(const In<T> *__restrict__ src, Cx<T> *__restrict__ W,
                                               const Cx<T> *__restrict__ tw, const Cx<T> *__restrict__ rtw, int Nx,
                                               int Ny, int My, int64_t rr, bool active, Cx<T> *line, int t,
-                                              const RowTwiddles<TWR, T, L, SH> &twr = {})
+                                              int zsh, const RowTwiddles<TWR, T, L, SH> &twr = {})
 {
     const int y = (int)(rr % Ny);
     const int64_t z = rr / Ny;
-    x_forward_row_at<T, L, TWR, SH>(src + rr * Nx, W + ((size_t)z * My + y) * L, tw, rtw, Nx, active, line, t,
+    x_forward_row_at<T, L, TWR, SH>(src + rr * Nx, W + w_row(z, y, My, zsh) * L, tw, rtw, Nx, active, line, t,
                                     twr);
 }
 
@@ -513,11 +527,12 @@ template <typename T, int L, bool CG = false, bool TWR = false>
 __device__ __forceinline__ void x_inverse_row(const Cx<T> *__restrict__ W, In<T> *__restrict__ phi,
                                               const Cx<T> *__restrict__ tw, const Cx<T> *__restrict__ rtw, int Nx,
                                               int Ny, int My, int64_t rr, bool active, Cx<T> *line, int t,
-                                              const RowTwiddles<TWR, T, L> &twr = {})
+                                              int zsh, const RowTwiddles<TWR, T, L> &twr = {})
 {
     const int y = (int)(rr % Ny);
     const int64_t z = rr / Ny;
-    x_inverse_row_at<T, L, CG, TWR>(W + ((size_t)z * My + y) * L, phi + rr * Nx, tw, rtw, Nx, active, line, t, twr);
+    x_inverse_row_at<T, L, CG, TWR>(W + w_row(z, y, My, zsh) * L, phi + rr * Nx, tw, rtw, Nx, active, line, t,
+                                    twr);
 }
 
 // K2 body: y forward of columns kx0 .. kx0 + TX - 1 of plane z.  Rows
@@ -525,12 +540,13 @@ __device__ __forceinline__ void x_inverse_row(const Cx<T> *__restrict__ W, In<T>
 template <typename T, int L, int TX, bool CG = false>
 __device__ __forceinline__ void y_forward_tile(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx,
                                                int z, int kx0, Cx<T> *smem, int c, int t,
-                                               const Cx<T> *staged = nullptr)
+                                               const Cx<T> *staged = nullptr, int zsh = 0)
 {
     constexpr int E = Shape<T, L>::E, NT = L / E;
     const int kx = kx0 + c;
     const bool active = kx < Kx;
-    Cx<T> *base = W + (size_t)z * L * Kx + (active ? kx : 0);
+    Cx<T> *base = W + w_row(z, 0, L, zsh) * Kx + (active ? kx : 0);
+    const size_t ys = (size_t)Kx << zsh;  // row stride
     Cx<T> v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) {
@@ -539,13 +555,13 @@ __device__ __forceinline__ void y_forward_tile(Cx<T> *__restrict__ W, const Cx<T
         if (staged)
             v[m] = ok ? staged[y * TX + c] : Cx<T>{(T)0, (T)0};
         else
-            v[m] = ok ? ld_cx<CG>(base + (size_t)y * Kx) : Cx<T>{(T)0, (T)0};
+            v[m] = ok ? ld_cx<CG>(base + (size_t)y * ys) : Cx<T>{(T)0, (T)0};
     }
     ColXch<T, L, E, TX> xch{smem, c};
     run_stages<T, L, E, true>(v, t, tw, xch, typename Shape<T, L>::Rad{});
     if (active) {
 #pragma unroll
-        for (int m = 0; m < E; ++m) base[(size_t)(t + m * NT) * Kx] = v[m];
+        for (int m = 0; m < E; ++m) base[(size_t)(t + m * NT) * ys] = v[m];
     }
 }
 
@@ -553,12 +569,13 @@ __device__ __forceinline__ void y_forward_tile(Cx<T> *__restrict__ W, const Cx<T
 template <typename T, int L, int TX>
 __device__ __forceinline__ void y_inverse_tile(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx,
                                                int z, int kx0, Cx<T> *smem, int c, int t,
-                                               const Cx<T> *staged = nullptr)
+                                               const Cx<T> *staged = nullptr, int zsh = 0)
 {
     constexpr int E = Shape<T, L>::E, NT = L / E;
     const int kx = kx0 + c;
     const bool active = kx < Kx;
-    Cx<T> *base = W + (size_t)z * L * Kx + (active ? kx : 0);
+    Cx<T> *base = W + w_row(z, 0, L, zsh) * Kx + (active ? kx : 0);
+    const size_t ys = (size_t)Kx << zsh;  // row stride
     Cx<T> v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) {
@@ -566,7 +583,7 @@ __device__ __forceinline__ void y_inverse_tile(Cx<T> *__restrict__ W, const Cx<T
         if (staged)
             v[m] = active ? cswap(staged[y * TX + c]) : Cx<T>{(T)0, (T)0};
         else
-            v[m] = active ? cswap(base[(size_t)y * Kx]) : Cx<T>{(T)0, (T)0};
+            v[m] = active ? cswap(base[(size_t)y * ys]) : Cx<T>{(T)0, (T)0};
     }
     ColXch<T, L, E, TX> xch{smem, c};
     run_stages<T, L, E, false>(v, t, tw, xch, typename Shape<T, L>::Rad{});
@@ -574,7 +591,7 @@ __device__ __forceinline__ void y_inverse_tile(Cx<T> *__restrict__ W, const Cx<T
 #pragma unroll
         for (int m = 0; m < E / 2; ++m) {
             const int y = t + m * NT;
-            if (y < Ny) base[(size_t)y * Kx] = cswap(v[m]);
+            if (y < Ny) base[(size_t)y * ys] = cswap(v[m]);
         }
     }
 }
@@ -588,7 +605,7 @@ __device__ __forceinline__ void y_inverse_tile(Cx<T> *__restrict__ W, const Cx<T
 template <typename T, int L>
 __global__ void __launch_bounds__(RowCfg<T, L, XShapeF<T, L>>::THREADS)
 k_x_forward(const In<T> *__restrict__ src, Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw,
-            const Cx<T> *__restrict__ rtw, int Nx, int Ny, int My, int64_t nrows)
+            const Cx<T> *__restrict__ rtw, int Nx, int Ny, int My, int64_t nrows, int zsh)
 {
     using SH = XShapeF<T, L>;
     using C = RowCfg<T, L, SH>;
@@ -601,7 +618,7 @@ k_x_forward(const In<T> *__restrict__ src, Cx<T> *__restrict__ W, const Cx<T> *_
         for (int64_t r0 = (int64_t)blockIdx.x * C::NL; r0 < nrows; r0 += (int64_t)gridDim.x * C::NL) {
             const int64_t row = r0 + l;  // row = z * Ny + y
             const bool active = row < nrows;
-            x_forward_row<T, L, true, SH>(src, W, tw, rtw, Nx, Ny, My, active ? row : 0, active, line, t, twr);
+            x_forward_row<T, L, true, SH>(src, W, tw, rtw, Nx, Ny, My, active ? row : 0, active, line, t, zsh, twr);
             // rows wider than a warp read their mirror points from `line`
             // last: the next row's first exchange must wait for those reads
             if constexpr (!(C::NT <= 32 && 32 % C::NT == 0)) {
@@ -611,14 +628,14 @@ k_x_forward(const In<T> *__restrict__ src, Cx<T> *__restrict__ W, const Cx<T> *_
     } else {
         const int64_t row = (int64_t)blockIdx.x * C::NL + l;
         const bool active = row < nrows;
-        x_forward_row<T, L, false, SH>(src, W, tw, rtw, Nx, Ny, My, active ? row : 0, active, line, t);
+        x_forward_row<T, L, false, SH>(src, W, tw, rtw, Nx, Ny, My, active ? row : 0, active, line, t, zsh);
     }
 }
 
 template <typename T, int L>
 __global__ void __launch_bounds__(RowCfg<T, L>::THREADS)
 k_x_inverse(const Cx<T> *__restrict__ W, In<T> *__restrict__ phi, const Cx<T> *__restrict__ tw,
-            const Cx<T> *__restrict__ rtw, int Nx, int Ny, int My, int64_t nrows)
+            const Cx<T> *__restrict__ rtw, int Nx, int Ny, int My, int64_t nrows, int zsh)
 {
     using C = RowCfg<T, L>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -630,12 +647,13 @@ k_x_inverse(const Cx<T> *__restrict__ W, In<T> *__restrict__ phi, const Cx<T> *_
         for (int64_t r0 = (int64_t)blockIdx.x * C::NL; r0 < nrows; r0 += (int64_t)gridDim.x * C::NL) {
             const int64_t row = r0 + l;
             const bool active = row < nrows;
-            x_inverse_row<T, L, false, true>(W, phi, tw, rtw, Nx, Ny, My, active ? row : 0, active, line, t, twr);
+            x_inverse_row<T, L, false, true>(W, phi, tw, rtw, Nx, Ny, My, active ? row : 0, active, line, t, zsh,
+                                             twr);
         }
     } else {
         const int64_t row = (int64_t)blockIdx.x * C::NL + l;
         const bool active = row < nrows;
-        x_inverse_row<T, L>(W, phi, tw, rtw, Nx, Ny, My, active ? row : 0, active, line, t);
+        x_inverse_row<T, L>(W, phi, tw, rtw, Nx, Ny, My, active ? row : 0, active, line, t, zsh);
     }
 }
 
@@ -647,22 +665,22 @@ k_x_inverse(const Cx<T> *__restrict__ W, In<T> *__restrict__ phi, const Cx<T> *_
 // ---------------------------------------------------------------------
 template <typename T, int L, bool NARROW = false>
 __global__ void __launch_bounds__(ColCfg<T, L, NARROW>::THREADS, ColCfg<T, L, NARROW>::MIN_BLOCKS_FWD)
-k_y_forward(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx)
+k_y_forward(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx, int zsh)
 {
     using C = ColCfg<T, L, NARROW>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     y_forward_tile<T, L, C::TX>(W, tw, Ny, Kx, blockIdx.y, blockIdx.x * C::TX, reinterpret_cast<Cx<T> *>(smem_raw),
-                                threadIdx.x % C::TX, threadIdx.x / C::TX);
+                                threadIdx.x % C::TX, threadIdx.x / C::TX, nullptr, zsh);
 }
 
 template <typename T, int L, bool NARROW = false>
 __global__ void __launch_bounds__(ColCfg<T, L, NARROW>::THREADS)
-k_y_inverse(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx)
+k_y_inverse(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx, int zsh)
 {
     using C = ColCfg<T, L, NARROW>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     y_inverse_tile<T, L, C::TX>(W, tw, Ny, Kx, blockIdx.y, blockIdx.x * C::TX, reinterpret_cast<Cx<T> *>(smem_raw),
-                                threadIdx.x % C::TX, threadIdx.x / C::TX);
+                                threadIdx.x % C::TX, threadIdx.x / C::TX, nullptr, zsh);
 }
 
 // z-pass exchanger.  With DB (two buffers, used in turn) an exchange needs a
@@ -757,7 +775,7 @@ struct YCfg {
 template <typename T, int L, bool FWD>
 __global__ void __launch_bounds__(YCfg<T, L>::THREADS, YCfg<T, L>::MIN_BLOCKS)
 k_y_pass(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny,
-         int Kx, int ntiles, unsigned *__restrict__ status)
+         int Kx, int ntiles, unsigned *__restrict__ status, int zsh)
 {
     using C = YCfg<T, L>;
     constexpr int E = C::E, NT = C::NT, TX = C::TX;
@@ -785,9 +803,13 @@ k_y_pass(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, const C
         const int z = tile / ntx, xt = tile - z * ntx;
         mbar_arrive_expect_tx(&bar[set], (uint32_t)IN);
 #pragma unroll
-        for (int b = 0; b < NB; ++b)
-            tma_load_3d(s_in + set * IN + (size_t)b * BOX * TX * sizeof(Cx<T>), &tmW, xt * TX * C::EPC, b * BOX, z,
-                        &bar[set]);
+        for (int b = 0; b < NB; ++b) {
+            void *dst = s_in + set * IN + (size_t)b * BOX * TX * sizeof(Cx<T>);
+            if (zsh == 0)
+                tma_load_3d(dst, &tmW, xt * TX * C::EPC, b * BOX, z, &bar[set]);
+            else  // tmW dims {Kx EPC, 2^zsh, rows, Nz >> zsh}
+                tma_load_4d(dst, &tmW, xt * TX * C::EPC, z & ((1 << zsh) - 1), b * BOX, z >> zsh, &bar[set]);
+        }
     };
     auto no_hook = [](int) {};
     using Rad = typename Shape<T, L>::Rad;
@@ -819,15 +841,16 @@ k_y_pass(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, const C
         }
         z_fft<C::TW_REGS, FWD, T, L, E>(v, t, twr, tw, xch, Rad{});
         if (kx < Kx) {
-            Cx<T> *base = W + (size_t)z * L * Kx + kx;
+            Cx<T> *base = W + w_row(z, 0, L, zsh) * Kx + kx;
+            const size_t ys = (size_t)Kx << zsh;  // row stride
             if constexpr (FWD) {
 #pragma unroll
-                for (int m = 0; m < E; ++m) base[(size_t)(t + m * NT) * Kx] = v[m];
+                for (int m = 0; m < E; ++m) base[(size_t)(t + m * NT) * ys] = v[m];
             } else {
 #pragma unroll
                 for (int m = 0; m < E / 2; ++m) {
                     const int y = t + m * NT;
-                    if (y < Ny) base[(size_t)y * Kx] = cswap(v[m]);
+                    if (y < Ny) base[(size_t)y * ys] = cswap(v[m]);
                 }
             }
         }
@@ -850,8 +873,8 @@ k_y_pass(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, const C
 // returns false (the same on every thread) to abandon the tile.
 template <typename T, int L, int IS, bool SYNC_ALL = false, typename TWR, typename Xch, typename BeforeG>
 __device__ __forceinline__ bool z_tile(const Cx<T> *sin, const T *sg, int pr, int xt, Cx<T> *__restrict__ W,
-                                       const T *__restrict__ Gs, T gscale, int Nz, int My, int Kx, int c, int g,
-                                       int t, const TWR &twr, const Cx<T> *twz, Xch &xch, BeforeG before_g)
+                                       const T *__restrict__ Gs, T gscale, int Nz, int My, int Kx, int zsh, int c,
+                                       int g, int t, const TWR &twr, const Cx<T> *twz, Xch &xch, BeforeG before_g)
 {
     using C = ZCfg<T, L>;
     using Rad = typename ZShape<T, L>::Rad;
@@ -909,13 +932,22 @@ __device__ __forceinline__ bool z_tile(const Cx<T> *sin, const T *sg, int pr, in
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = cswap(v[m]);
     z_fft<C::TWR, false, T, L, E>(v, t, twr, twz, xch, Rad{});
-    if (active) {
+    if (active && zsh == 0) {
         Cx<T> *base = W + (size_t)ky * Kx + kx;
         const size_t zstride = (size_t)My * Kx;
 #pragma unroll
         for (int m = 0; m < E / 2; ++m) {
             const int z = t + m * NT;
             if (z < Nz) base[(size_t)z * zstride] = cswap(v[m]);
+        }
+    } else if (active) {
+        Cx<T> *base = W + ((size_t)ky << zsh) * Kx + kx;
+#pragma unroll
+        for (int m = 0; m < E / 2; ++m) {
+            const int z = t + m * NT;
+            // w_row(z, ky) - w_row(0, ky): (z >> zsh) blocks, row z & (2^zsh - 1)
+            const size_t zr = (((size_t)(z >> zsh) * My) << zsh) + (z & ((1 << zsh) - 1));
+            if (z < Nz) base[zr * Kx] = cswap(v[m]);
         }
     }
     return true;
@@ -1022,7 +1054,7 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
         const int pr = tile / ntx, xt = tile - pr * ntx;
         const Cx<T> *sin = reinterpret_cast<const Cx<T> *>(s_in + g * C::IN_GROUP);
         const T *sg = s_g + ((size_t)set * 2 + (pr == 0 ? g : 0)) * C::GBLK;
-        z_tile<T, L, TX>(sin, sg, pr, xt, W, Gs, gscale, Nz, My, Kx, c, g, t, twr, twz, xch, [] { return true; });
+        z_tile<T, L, TX>(sin, sg, pr, xt, W, Gs, gscale, Nz, My, Kx, 0, c, g, t, twr, twz, xch, [] { return true; });
     }
     if (!ok && tid == 0) {
         // a wait gave up: flag it, then let this tile's copies land (bounded
@@ -1043,13 +1075,14 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
 // the barrier of the second tile's first inverse exchange: by then every
 // thread has read the current pair's input, and its spectrum, respectively.
 // When ntx is odd the last pair of a line pair has one tile.
-template <typename T, int L>
+template <typename T, int L, int ZSH = 0>
 __global__ void __launch_bounds__(ZCfg<T, L>::THREADS, ZCfg<T, L>::MIN_BLOCKS)
 k_z_convolve_pairs(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw,
                    const T *__restrict__ G, const T *__restrict__ Gs, T gscale, int Nz, int My, int Kx,
                    int npairs, unsigned *__restrict__ status, unsigned test_extra_tx)
 {
     using C = ZCfg<T, L>;
+    constexpr int zsh = ZSH;  // workspace z blocks of 2^ZSH planes (w_row)
     static_assert(!C::DBX, "lines with room for two exchange buffers take k_z_convolve");
     constexpr int E = C::E, TX = C::TX, COLS = C::COLS, PTX = C::PTX;
     constexpr int Lh = L / 2;
@@ -1095,8 +1128,14 @@ k_z_convolve_pairs(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ 
 #pragma unroll
         for (int zb = 0; zb < C::NZB; ++zb) {
             const size_t off = (size_t)zb * C::BOXZ * PTX * sizeof(Cx<T>);
-            tma_load_3d(s_in + off, &tmW, xt0 * TX * C::EPC, pr, zb * C::BOXZ, &bar[0]);
-            tma_load_3d(s_in + C::PIN_GROUP + off, &tmW, xt0 * TX * C::EPC, ky1, zb * C::BOXZ, &bar[0]);
+            if constexpr (zsh == 0) {
+                tma_load_3d(s_in + off, &tmW, xt0 * TX * C::EPC, pr, zb * C::BOXZ, &bar[0]);
+                tma_load_3d(s_in + C::PIN_GROUP + off, &tmW, xt0 * TX * C::EPC, ky1, zb * C::BOXZ, &bar[0]);
+            } else {  // tmW dims {Kx EPC, 2^zsh, My, Nz >> zsh}, box {2 TX EPC, 2^zsh, 1, BOXZ >> zsh}
+                tma_load_4d(s_in + off, &tmW, xt0 * TX * C::EPC, 0, pr, (zb * C::BOXZ) >> zsh, &bar[0]);
+                tma_load_4d(s_in + C::PIN_GROUP + off, &tmW, xt0 * TX * C::EPC, 0, ky1, (zb * C::BOXZ) >> zsh,
+                            &bar[0]);
+            }
         }
         ++n_in;
     };
@@ -1140,7 +1179,7 @@ k_z_convolve_pairs(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ 
             };
             const Cx<T> *sin = reinterpret_cast<const Cx<T> *>(s_in + g * C::PIN_GROUP) + s * TX;
             const T *sg = s_g + ((size_t)(pr == 0 ? g : 0) * 2 + s) * C::GBLK;
-            if (!z_tile<T, L, PTX>(sin, sg, pr, xt0 + s, W, Gs, gscale, Nz, My, Kx, c, g, t, twr, twz, xch,
+            if (!z_tile<T, L, PTX>(sin, sg, pr, xt0 + s, W, Gs, gscale, Nz, My, Kx, zsh, c, g, t, twr, twz, xch,
                                    spectrum_landed)) {
                 ok = false;
                 break;

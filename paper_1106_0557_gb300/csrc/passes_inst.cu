@@ -88,44 +88,46 @@ static unsigned row_grid(int64_t nrows, int nl, int resident)
 }
 template <typename T, int L>
 static cudaError_t run_x_forward(const In<T> *src, void *W, const void *tw, const void *rtw, int Nx, int Ny,
-                                 int My, int64_t nrows, cudaStream_t st)
+                                 int My, int64_t nrows, int zsh, cudaStream_t st)
 {
     using C = RowCfg<T, L, XShapeF<T, L>>;
     static std::atomic<uint64_t> done{0};
     static std::atomic<int> resident{0};
+    if (Ny <= 0 || nrows % Ny || !w_blocks_ok(nrows / Ny, zsh)) return cudaErrorInvalidValue;
     cudaError_t e = ensure_smem(k_x_forward<T, L>, C::SMEM, done);
     if (e != cudaSuccess) return e;
     const unsigned grid =
         row_grid(nrows, C::NL, C::TWR_F ? resident_ctas(k_x_forward<T, L>, C::THREADS, C::SMEM, resident) : 0);
     k_x_forward<T, L><<<grid, C::THREADS, C::SMEM, st>>>(src, (Cx<T> *)W, (const Cx<T> *)tw,
-                                                        (const Cx<T> *)rtw, Nx, Ny, My, nrows);
+                                                        (const Cx<T> *)rtw, Nx, Ny, My, nrows, zsh);
     count_launch();
     return cudaGetLastError();
 }
 template <typename T, int L>
 static cudaError_t run_x_inverse(const void *W, In<T> *phi, const void *tw, const void *rtw, int Nx, int Ny,
-                                 int My, int64_t nrows, cudaStream_t st)
+                                 int My, int64_t nrows, int zsh, cudaStream_t st)
 {
     using C = RowCfg<T, L>;
     static std::atomic<uint64_t> done{0};
     static std::atomic<int> resident{0};
+    if (Ny <= 0 || nrows % Ny || !w_blocks_ok(nrows / Ny, zsh)) return cudaErrorInvalidValue;
     cudaError_t e = ensure_smem(k_x_inverse<T, L>, C::SMEM, done);
     if (e != cudaSuccess) return e;
     const unsigned grid =
         row_grid(nrows, C::NL, C::TWR_I ? resident_ctas(k_x_inverse<T, L>, C::THREADS, C::SMEM, resident) : 0);
     k_x_inverse<T, L><<<grid, C::THREADS, C::SMEM, st>>>((const Cx<T> *)W, phi, (const Cx<T> *)tw,
-                                                        (const Cx<T> *)rtw, Nx, Ny, My, nrows);
+                                                        (const Cx<T> *)rtw, Nx, Ny, My, nrows, zsh);
     count_launch();
     return cudaGetLastError();
 }
 
 template <typename R_>
 cudaError_t launch_x_forward(int L, const In<R_> *src, void *W, const void *tw, const void *rtw, int Nx,
-                                 int Ny, int My, int64_t nrows, cudaStream_t st)
+                                 int Ny, int My, int64_t nrows, int zsh, cudaStream_t st)
 {
     switch (L) {
 #define X_(n) \
-    case n: return run_x_forward<R_, n>(src, W, tw, rtw, Nx, Ny, My, nrows, st);
+    case n: return run_x_forward<R_, n>(src, W, tw, rtw, Nx, Ny, My, nrows, zsh, st);
         ISOFFT_ROW_LENGTHS(X_)
 #undef X_
     default: return cudaErrorInvalidValue;
@@ -133,38 +135,40 @@ cudaError_t launch_x_forward(int L, const In<R_> *src, void *W, const void *tw, 
 }
 template <typename R_>
 cudaError_t launch_x_inverse(int L, const void *W, In<R_> *phi, const void *tw, const void *rtw, int Nx,
-                                 int Ny, int My, int64_t nrows, cudaStream_t st)
+                                 int Ny, int My, int64_t nrows, int zsh, cudaStream_t st)
 {
     switch (L) {
 #define X_(n) \
-    case n: return run_x_inverse<R_, n>(W, phi, tw, rtw, Nx, Ny, My, nrows, st);
+    case n: return run_x_inverse<R_, n>(W, phi, tw, rtw, Nx, Ny, My, nrows, zsh, st);
         ISOFFT_ROW_LENGTHS(X_)
 #undef X_
     default: return cudaErrorInvalidValue;
     }
 }
 template cudaError_t launch_x_forward<Real>(int, const In<Real> *, void *, const void *, const void *, int, int,
-                                            int, int64_t, cudaStream_t);
+                                            int, int64_t, int, cudaStream_t);
 template cudaError_t launch_x_inverse<Real>(int, const void *, In<Real> *, const void *, const void *, int, int,
-                                            int, int64_t, cudaStream_t);
+                                            int, int64_t, int, cudaStream_t);
 #endif
 
 #if ISOFFT_GROUP == 2
 template <typename T, int L, bool FWD, bool NARROW>
-static cudaError_t run_y_tile(void *W, const void *tw, int Ny, int Kx, int Nz, cudaStream_t st)
+static cudaError_t run_y_tile(void *W, const void *tw, int Ny, int Kx, int Nz, int zsh, cudaStream_t st)
 {
     using C = ColCfg<T, L, NARROW>;
     static std::atomic<uint64_t> done{0};
     auto *k = FWD ? k_y_forward<T, L, NARROW> : k_y_inverse<T, L, NARROW>;
+    if (!w_blocks_ok(Nz, zsh)) return cudaErrorInvalidValue;
     cudaError_t e = ensure_smem(k, C::SMEM, done);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((Kx + C::TX - 1) / C::TX), (unsigned)Nz);
-    k<<<grid, C::THREADS, C::SMEM, st>>>((Cx<T> *)W, (const Cx<T> *)tw, Ny, Kx);
+    k<<<grid, C::THREADS, C::SMEM, st>>>((Cx<T> *)W, (const Cx<T> *)tw, Ny, Kx, zsh);
     count_launch();
     return cudaGetLastError();
 }
 template <typename T, int L, bool FWD>
-static cudaError_t run_y_stream(void *W, const void *tw, int Ny, int Kx, int Nz, unsigned *status, cudaStream_t st)
+static cudaError_t run_y_stream(void *W, const void *tw, int Ny, int Kx, int Nz, int zsh, unsigned *status,
+                                cudaStream_t st)
 {
     using C = YCfg<T, L>;
     constexpr size_t SMEM = FWD ? C::SMEM_F : C::SMEM_I;
@@ -179,56 +183,65 @@ static cudaError_t run_y_stream(void *W, const void *tw, int Ny, int Kx, int Nz,
     int grid = resident_ctas(k, C::THREADS, SMEM, slots);
     if (grid <= 0) return cudaErrorInvalidConfiguration;
     if (grid > ntiles) grid = ntiles;
-    // W as 8-byte elements [Nz][My][Kx * EPC]; K2 sees only rows y < Ny
+    // W as 8-byte elements [Nz][My][Kx * EPC] (z-blocked: [Nz >> zsh][My][2^zsh][Kx * EPC], mapped as
+    // {Kx EPC, 2^zsh, rows, Nz >> zsh}); K2 sees only rows y < Ny
     EncodeTiledFn encode = encode_tiled();
     if (!encode) return cudaErrorNotSupported;
+    if (!w_blocks_ok(Nz, zsh)) return cudaErrorInvalidValue;
     CUtensorMap map;
-    const cuuint64_t dims[3] = {(cuuint64_t)Kx * C::EPC, (cuuint64_t)(FWD ? Ny : L), (cuuint64_t)Nz};
-    const cuuint64_t strides[2] = {(cuuint64_t)Kx * sizeof(Cx<T>), (cuuint64_t)L * Kx * sizeof(Cx<T>)};
-    const cuuint32_t box[3] = {(cuuint32_t)(C::TX * C::EPC), (cuuint32_t)(FWD ? C::BOX_F : C::BOX_I), 1u};
-    const cuuint32_t estr[3] = {1u, 1u, 1u};
-    if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, W, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    const cuuint64_t rows = (cuuint64_t)(FWD ? Ny : L), cb = sizeof(Cx<T>);
+    const cuuint64_t dims3[3] = {(cuuint64_t)Kx * C::EPC, rows, (cuuint64_t)Nz};
+    const cuuint64_t strides3[2] = {(cuuint64_t)Kx * cb, (cuuint64_t)L * Kx * cb};
+    const cuuint32_t box3[3] = {(cuuint32_t)(C::TX * C::EPC), (cuuint32_t)(FWD ? C::BOX_F : C::BOX_I), 1u};
+    const cuuint64_t dims4[4] = {(cuuint64_t)Kx * C::EPC, (cuuint64_t)1 << zsh, rows, (cuuint64_t)(Nz >> zsh)};
+    const cuuint64_t strides4[3] = {(cuuint64_t)Kx * cb, ((cuuint64_t)Kx * cb) << zsh,
+                                    ((cuuint64_t)L * Kx * cb) << zsh};
+    const cuuint32_t box4[4] = {(cuuint32_t)(C::TX * C::EPC), 1u, (cuuint32_t)(FWD ? C::BOX_F : C::BOX_I), 1u};
+    const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+    if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT64, zsh ? 4 : 3, W, zsh ? dims4 : dims3, zsh ? strides4 : strides3,
+               zsh ? box4 : box3, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
-    k<<<grid, C::THREADS, SMEM, st>>>(map, (Cx<T> *)W, (const Cx<T> *)tw, Ny, Kx, ntiles, status);
+    k<<<grid, C::THREADS, SMEM, st>>>(map, (Cx<T> *)W, (const Cx<T> *)tw, Ny, Kx, ntiles, status, zsh);
     count_launch();
     return cudaGetLastError();
 }
 template <typename T, int L, bool FWD>
-static cudaError_t run_y(void *W, const void *tw, int Ny, int Kx, int Nz, unsigned *status, int variant,
+static cudaError_t run_y(void *W, const void *tw, int Ny, int Kx, int Nz, int zsh, unsigned *status, int variant,
                          cudaStream_t st)
 {
-    if (variant == kYStream) return run_y_stream<T, L, FWD>(W, tw, Ny, Kx, Nz, status, st);
-    if (variant == kYTileNarrow) return run_y_tile<T, L, FWD, true>(W, tw, Ny, Kx, Nz, st);
-    return run_y_tile<T, L, FWD, false>(W, tw, Ny, Kx, Nz, st);
+    if (variant == kYStream) return run_y_stream<T, L, FWD>(W, tw, Ny, Kx, Nz, zsh, status, st);
+    if (variant == kYTileNarrow) return run_y_tile<T, L, FWD, true>(W, tw, Ny, Kx, Nz, zsh, st);
+    return run_y_tile<T, L, FWD, false>(W, tw, Ny, Kx, Nz, zsh, st);
 }
 template <typename R_>
-cudaError_t launch_y_forward(int L, void *W, const void *tw, int Ny, int Kx, int Nz, unsigned *status, int variant,
-                             cudaStream_t st)
+cudaError_t launch_y_forward(int L, void *W, const void *tw, int Ny, int Kx, int Nz, int zsh, unsigned *status,
+                             int variant, cudaStream_t st)
 {
     switch (L) {
 #define X_(n) \
-    case n: return run_y<R_, n, true>(W, tw, Ny, Kx, Nz, status, variant, st);
+    case n: return run_y<R_, n, true>(W, tw, Ny, Kx, Nz, zsh, status, variant, st);
         ISOFFT_COL_LENGTHS(X_)
 #undef X_
     default: return cudaErrorInvalidValue;
     }
 }
 template <typename R_>
-cudaError_t launch_y_inverse(int L, void *W, const void *tw, int Ny, int Kx, int Nz, unsigned *status, int variant,
-                             cudaStream_t st)
+cudaError_t launch_y_inverse(int L, void *W, const void *tw, int Ny, int Kx, int Nz, int zsh, unsigned *status,
+                             int variant, cudaStream_t st)
 {
     switch (L) {
 #define X_(n) \
-    case n: return run_y<R_, n, false>(W, tw, Ny, Kx, Nz, status, variant, st);
+    case n: return run_y<R_, n, false>(W, tw, Ny, Kx, Nz, zsh, status, variant, st);
         ISOFFT_COL_LENGTHS(X_)
 #undef X_
     default: return cudaErrorInvalidValue;
     }
 }
-template cudaError_t launch_y_forward<Real>(int, void *, const void *, int, int, int, unsigned *, int, cudaStream_t);
-template cudaError_t launch_y_inverse<Real>(int, void *, const void *, int, int, int, unsigned *, int, cudaStream_t);
+template cudaError_t launch_y_forward<Real>(int, void *, const void *, int, int, int, int, unsigned *, int,
+                                            cudaStream_t);
+template cudaError_t launch_y_inverse<Real>(int, void *, const void *, int, int, int, int, unsigned *, int,
+                                            cudaStream_t);
 #endif
 
 #if ISOFFT_GROUP == 3
@@ -237,38 +250,58 @@ template cudaError_t launch_y_inverse<Real>(int, void *, const void *, int, int,
 // room for two exchange buffers.
 template <typename T, int L>
 static cudaError_t run_z(void *W, const void *tw, const T *G, const T *Gs, T gscale, int Nz, int My, int Kx,
-                         unsigned *status, unsigned test_extra_tx, cudaStream_t st)
+                         int zsh, unsigned *status, unsigned test_extra_tx, cudaStream_t st)
 {
     using C = ZCfg<T, L>;
-    constexpr auto kernel = []() {
+    // the paired form comes in a plain and a z-blocked instance
+    constexpr auto kernel0 = []() {
         if constexpr (C::DBX)
             return k_z_convolve<T, L>;
         else
-            return k_z_convolve_pairs<T, L>;
+            return k_z_convolve_pairs<T, L, 0>;
     }();
-    static std::atomic<uint64_t> done{0};
-    static std::atomic<int> slots{0};
+    constexpr auto kernelb = []() {
+        if constexpr (C::DBX)
+            return k_z_convolve<T, L>;
+        else
+            return k_z_convolve_pairs<T, L, kZBlockShift>;
+    }();
+    static std::atomic<uint64_t> done0{0}, doneb{0};
+    static std::atomic<int> slots0{0}, slotsb{0};
     if (((uintptr_t)W & 15) || ((uintptr_t)G & 15)) return cudaErrorMisalignedAddress;
-    cudaError_t e = ensure_smem(kernel, C::SMEM, done);
+    // the z-blocked workspace is read by the paired form only, in boxes of
+    // whole blocks
+    if (!w_blocks_ok(Nz, zsh) || (zsh && (C::DBX || zsh != kZBlockShift || C::BOXZ % (1 << zsh))))
+        return cudaErrorInvalidValue;
+    const auto kernel = zsh ? kernelb : kernel0;
+    cudaError_t e = ensure_smem(kernel, C::SMEM, zsh ? doneb : done0);
     if (e != cudaSuccess) return e;
     const int ntx = (Kx + C::TX - 1) / C::TX;
     // work units: tiles, or tile pairs
     const int units = (C::DBX ? ntx : (ntx + 1) / 2) * (My / 2);
-    int grid = resident_ctas(kernel, C::THREADS, C::SMEM, slots);
+    int grid = resident_ctas(kernel, C::THREADS, C::SMEM, zsh ? slotsb : slots0);
     if (grid <= 0) return cudaErrorInvalidConfiguration;
     if (grid > units) grid = units;
     // W as 8-byte elements [Nz][My][Kx * EPC]; one box = TX (pairs: 2 TX)
-    // columns of one line for BOXZ planes
+    // columns of one line for BOXZ planes.  z-blocked: [Nz >> zsh][My][2^zsh][Kx * EPC],
+    // mapped as {Kx EPC, 2^zsh, My, Nz >> zsh}; one box = BOXZ >> zsh blocks
     EncodeTiledFn encode = encode_tiled();
     if (!encode) return cudaErrorNotSupported;
     CUtensorMap map;
-    const cuuint64_t dims[3] = {(cuuint64_t)Kx * C::EPC, (cuuint64_t)My, (cuuint64_t)Nz};
-    const cuuint64_t strides[2] = {(cuuint64_t)Kx * sizeof(Cx<T>), (cuuint64_t)My * Kx * sizeof(Cx<T>)};
-    const cuuint32_t box[3] = {(cuuint32_t)((C::DBX ? C::TX : C::PTX) * C::EPC), 1u, (cuuint32_t)C::BOXZ};
-    const cuuint32_t estr[3] = {1u, 1u, 1u};
-    if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, W, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    const cuuint64_t cb = sizeof(Cx<T>);
+    const cuuint32_t bx = (cuuint32_t)((C::DBX ? C::TX : C::PTX) * C::EPC);
+    const cuuint64_t dims3[3] = {(cuuint64_t)Kx * C::EPC, (cuuint64_t)My, (cuuint64_t)Nz};
+    const cuuint64_t strides3[2] = {(cuuint64_t)Kx * cb, (cuuint64_t)My * Kx * cb};
+    const cuuint32_t box3[3] = {bx, 1u, (cuuint32_t)C::BOXZ};
+    const cuuint64_t dims4[4] = {(cuuint64_t)Kx * C::EPC, (cuuint64_t)1 << zsh, (cuuint64_t)My,
+                                 (cuuint64_t)(Nz >> zsh)};
+    const cuuint64_t strides4[3] = {(cuuint64_t)Kx * cb, ((cuuint64_t)Kx * cb) << zsh,
+                                    ((cuuint64_t)My * Kx * cb) << zsh};
+    const cuuint32_t box4[4] = {bx, 1u << zsh, 1u, (cuuint32_t)(C::BOXZ >> zsh)};
+    const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+    if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT64, zsh ? 4 : 3, W, zsh ? dims4 : dims3, zsh ? strides4 : strides3,
+               zsh ? box4 : box3, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
     kernel<<<grid, C::THREADS, C::SMEM, st>>>(map, (Cx<T> *)W, (const Cx<T> *)tw, G, Gs, gscale, Nz, My, Kx, units,
                                              status, test_extra_tx);
@@ -277,11 +310,12 @@ static cudaError_t run_z(void *W, const void *tw, const T *G, const T *Gs, T gsc
 }
 template <typename R_>
 cudaError_t launch_z_convolve(int L, void *W, const void *tw, const R_ *G, const R_ *Gs, R_ gscale,
-                                  int Nz, int My, int Kx, unsigned *status, unsigned test_extra_tx, cudaStream_t st)
+                                  int Nz, int My, int Kx, int zsh, unsigned *status, unsigned test_extra_tx,
+                                  cudaStream_t st)
 {
     switch (L) {
 #define X_(n) \
-    case n: return run_z<R_, n>(W, tw, G, Gs, gscale, Nz, My, Kx, status, test_extra_tx, st);
+    case n: return run_z<R_, n>(W, tw, G, Gs, gscale, Nz, My, Kx, zsh, status, test_extra_tx, st);
         ISOFFT_COL_LENGTHS(X_)
 #undef X_
     default: return cudaErrorInvalidValue;
@@ -299,7 +333,7 @@ int z_tile_for(int L)
     }
 }
 template cudaError_t launch_z_convolve<Real>(int, void *, const void *, const Real *, const Real *, Real, int,
-                                             int, int, unsigned *, unsigned, cudaStream_t);
+                                             int, int, int, unsigned *, unsigned, cudaStream_t);
 template int z_tile_for<Real>(int);
 #endif
 

@@ -271,6 +271,7 @@ LONG_SHAPES = [
     ((9, 1100, 8), (1.0, 2.0, 1.0)),     # My = 2304
     ((8, 9, 1152), (1.0, 1.0, 0.5)),     # Mz = 2304, the largest N
     ((60, 30, 1100), (1.0, 1.0, 1.0)),   # Mz = 2304, several tile pairs per CTA
+    ((40, 30, 1136), (1.0, 2.0, 1.0)),   # Mz = 2304, z-blocked workspace, last box past Nz
     ((5, 3, 2), (1.0, 1.0, 1.0)),        # every axis padded up to 32
 ]
 
@@ -377,11 +378,12 @@ def test_binary_spheroid_convergence_at_least_first_order():
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f64", "df64"])
-@pytest.mark.parametrize("N", [(37, 20, 13), (64, 64, 64), (33, 17, 5), (9, 11, 1)])
+@pytest.mark.parametrize("N", [(37, 20, 13), (64, 64, 64), (33, 17, 5), (9, 11, 1), (12, 10, 1136)])
 def test_host_buffer_solve_equals_device_solve(N, dtype):
     """ipf_solve_host copies and solves in chunks of z planes (ragged last
-    chunk, odd row lengths, fewer planes than chunks); its potential is
-    bitwise the device solve's."""
+    chunk, odd row lengths, fewer planes than chunks; on 2304-point z lines
+    chunks of whole z blocks of the workspace); its potential is bitwise the
+    device solve's."""
     from paper_1106_0557_gb300 import Plan
     src = rand_src(N, 17).astype(NP[dtype])
     with Plan(N, (1.0, 0.5, 2.0), dtype) as p:
