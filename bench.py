@@ -397,7 +397,7 @@ def run_batch(steps=50, count=64):
     return res
 
 
-def run_serving(n_requests, slots, fp64_class="df64"):
+def run_serving(n_requests, slots, fp64_class="df64", express_slots=2, plan_workers=4):
     """Config 5: cubic N log-uniform in [32, 384], 70 % FP32 (tolerance
     1e-5) / 30 % FP64 class (tolerance 1e-12, served with the `fp64_class`
     dtype), HBM budget 120 GB, continuous batching over `slots` streams with
@@ -406,7 +406,11 @@ def run_serving(n_requests, slots, fp64_class="df64"):
     * Poisson arrivals at 0.5, 0.8 and 0.95 x that rate (0.8 headlined), each
       load point from a cold start: a fresh server and an empty spectrum
       cache, so every shape's first request waits for its plan and Green's
-      spectrum to be built (their latency counts).
+      spectrum to be built (their latency counts).  Two admission policies:
+      first come first served on every slot ("fcfs"), and `express_slots`
+      slots, on high-priority streams, kept for requests no costlier than
+      an FP32 128^3 solve ("express", the headline).  Plans are built by
+      `plan_workers` background threads.
     * The FP32 class served vs the same shapes solved one at a time in plain
       FP64 (plan set-up excluded)."""
     import torch
@@ -418,36 +422,47 @@ def run_serving(n_requests, slots, fp64_class="df64"):
     be = serving.TorchBackend(slots=slots)
     reqs = mk(np.zeros(len(spec)))
     be.prepare(reqs)
-    srv = serving.Server(be, budget_bytes=120e9, slots=slots, async_plans=True)
+    srv = serving.Server(be, budget_bytes=120e9, slots=slots, async_plans=True, plan_workers=plan_workers)
     serving.saturated_throughput(srv, be, reqs)  # warm-up pass: plans and spectra
     sat = serving.saturated_throughput(srv, be, reqs)
     peak = srv.peak_bytes
     srv.close()
-    sweep = []
-    cold = {}
-    for load in (0.5, 0.8, 0.95):
-        r = load * sat["solves_per_s"]
-        native.ipf_greens_cache_trim(0)
-        srv = serving.Server(be, budget_bytes=120e9, slots=slots, async_plans=True)
-        rq = mk(serving.poisson_arrivals(len(spec), r, seed=1))
-        srv.run(rq)
-        peak = max(peak, srv.peak_bytes)
-        srv.close()
-        st = serving.latency_stats(rq)
-        # requests that found no plan of their shape: the first of each shape
-        seen, first = set(), []
-        for q in sorted(rq, key=lambda q: q.arrival):
-            if (q.n, q.dtype) not in seen:
-                seen.add((q.n, q.dtype))
-                first.append(q.latency)
-        sweep.append({"load": load, "rate": round(r, 1), "p50_ms": round(st["p50_ms"], 3),
-                      "p99_ms": round(st["p99_ms"], 3), "solves_per_s": round(st["solves_per_s"], 1),
-                      "cold_shapes": len(first), "cold_p50_ms": round(float(np.percentile(first, 50)) * 1e3, 3)})
-        if load == 0.8:
-            rate, lat = r, st
+    policies = {"fcfs": 0, "express": express_slots}
+    sweeps = {}
+    for pol, nexp in policies.items():
+        sweep = []
+        be.set_express(nexp)
+        for load in (0.5, 0.8, 0.95):
+            r = load * sat["solves_per_s"]
+            native.ipf_greens_cache_trim(0)
+            srv = serving.Server(be, budget_bytes=120e9, slots=slots, async_plans=True, express_slots=nexp,
+                                 plan_workers=plan_workers)
+            rq = mk(serving.poisson_arrivals(len(spec), r, seed=1))
+            srv.run(rq)
+            peak = max(peak, srv.peak_bytes)
+            st = serving.latency_stats(rq)
+            cheap = serving.Server(be, slots=slots, express_slots=1).small
+            st_s = serving.latency_stats([q for q in rq if cheap(q)])
+            st_l = serving.latency_stats([q for q in rq if not cheap(q)])
+            srv.close()
+            # requests that found no plan of their shape: the first of each shape
+            seen, first = set(), []
+            for q in sorted(rq, key=lambda q: q.arrival):
+                if (q.n, q.dtype) not in seen:
+                    seen.add((q.n, q.dtype))
+                    first.append(q.latency)
+            sweep.append({"load": load, "rate": round(r, 1), "p50_ms": round(st["p50_ms"], 3),
+                          "p99_ms": round(st["p99_ms"], 3), "solves_per_s": round(st["solves_per_s"], 1),
+                          "small_p50_p99_ms": [round(st_s["p50_ms"], 3), round(st_s["p99_ms"], 3)],
+                          "large_p50_p99_ms": [round(st_l["p50_ms"], 3), round(st_l["p99_ms"], 3)],
+                          "cold_shapes": len(first), "cold_p50_ms": round(float(np.percentile(first, 50)) * 1e3, 3)})
+            if load == 0.8 and pol == "express":
+                rate, lat = r, st
+        sweeps[pol] = sweep
+    be.set_express(0)
     # FP32 class served (saturated, warm) vs plain unbatched FP64 on the same shapes
     sub = [q for q in reqs if q.dtype == "f32"][:300]
-    srv = serving.Server(be, budget_bytes=120e9, slots=slots, async_plans=True)
+    srv = serving.Server(be, budget_bytes=120e9, slots=slots, async_plans=True, plan_workers=plan_workers)
     serving.saturated_throughput(srv, be, sub)
     served32 = serving.saturated_throughput(srv, be, sub)
     srv.close()
@@ -468,12 +483,17 @@ def run_serving(n_requests, slots, fp64_class="df64"):
     plain64 = len(shapes) / plain_s
     return {"requests": len(spec), "slots": slots, "budget_gb": 120,
             "mix": "cubic N log-uniform [32,384], 70%% f32 / 30%% FP64-class served as %s" % fp64_class,
-            "plans": "created on a background thread; admission looks ahead past requests whose plan is "
+            "plans": "created on background threads; admission looks ahead past requests whose plan is "
                      "being built",
             "saturated_solves_per_s": round(sat["solves_per_s"], 1),
+            "policy": "express: %d of %d slots, on high-priority streams, kept for requests no costlier than "
+                      "an FP32 128^3 solve (small = %s); large requests first come first served on the others; "
+                      "plans built by %d background threads" % (
+                          express_slots, slots, "FP32 N <= 128, df64 N <= 72", plan_workers),
             "poisson_rate": round(rate, 1), "p50_ms": round(lat["p50_ms"], 3), "p99_ms": round(lat["p99_ms"], 3),
             "solves_per_s": round(lat["solves_per_s"], 1),
-            "load_sweep": sweep, "load_sweep_start": "cold: fresh server, empty spectrum cache",
+            "load_sweep": sweeps["express"], "load_sweep_fcfs": sweeps["fcfs"],
+            "load_sweep_start": "cold: fresh server, empty spectrum cache",
             "f32_served_solves_per_s": round(served32["solves_per_s"], 1),
             "f64_plain_unbatched_solves_per_s": round(plain64, 1),
             "f32_served_over_f64_plain": round(served32["solves_per_s"] / plain64, 2),

@@ -21,6 +21,12 @@ thread, and stays queued while requests behind it whose plans are ready are
 admitted (within a look-ahead window).  Its latency then includes the plan's
 creation: misses are served cold, not hidden by a warm-up.
 
+Size-aware admission (``express_slots``): the last few slots take only
+cheap requests (estimated device time at most ``express_cost``, see
+``request_cost``), so a burst of large solves cannot hold every slot while
+small requests queue behind it; large requests keep their arrival order on
+the other slots.
+
 The device side is behind a small backend interface (``TorchBackend`` here;
 tests substitute a fake one), so the admission and pooling logic is plain
 host code.
@@ -28,6 +34,7 @@ host code.
 import collections
 import concurrent.futures as cf
 import math
+import threading
 import time
 
 import numpy as np
@@ -58,6 +65,16 @@ class Request:
     @property
     def latency(self):
         return None if self.finished is None else self.finished - self.arrival
+
+
+# device time of a solve relative to FP32 at the same N: FP64 runs on the
+# FP64 units (25.8x FP32 at 256^3), float pairs on the FP32 units (5.4x)
+DTYPE_COST = {"f32": 1.0, "df64": 5.4, "f64": 25.8}
+
+
+def request_cost(n, dtype):
+    """Relative device time of one solve of a cubic mesh of n cells."""
+    return DTYPE_COST.get(dtype, 1.0) * float(n) ** 3
 
 
 class PlanPool:
@@ -101,12 +118,17 @@ class Server:
 
     on_finish: called with each completed request before its output is
     dropped (unless keep_outputs), e.g. to check or copy it.
-    async_plans: create missing plans on a background thread; admission then
-    looks at up to `lookahead` queued requests for one whose plan is ready.
+    async_plans: create missing plans on background threads (`plan_workers`
+    of them); admission then looks at up to `lookahead` queued requests for
+    one whose plan is ready.
+    express_slots: slots kept for requests of request_cost <= express_cost
+    (default: an FP32 solve of 128^3); such requests take an express slot
+    first, then any slot; admission then also looks past large requests
+    that wait for a slot (which keep their order among themselves).
     """
 
     def __init__(self, backend, budget_bytes=120e9, slots=8, keep_outputs=False, on_finish=None,
-                 async_plans=False, lookahead=64):
+                 async_plans=False, lookahead=64, express_slots=0, express_cost=None, plan_workers=1):
         self.backend = backend
         self.budget = float(budget_bytes)
         self.slots = int(slots)
@@ -116,10 +138,31 @@ class Server:
         self.inflight_bytes = 0
         self.peak_bytes = 0
         self.async_plans = async_plans
-        self.lookahead = int(lookahead) if async_plans else 1
+        if not 0 <= int(express_slots) < int(slots):
+            raise ValueError("express_slots must leave at least one slot for every request")
+        self.express_slots = int(express_slots)
+        self.express_cost = request_cost(128, "f32") if express_cost is None else float(express_cost)
+        self.lookahead = int(lookahead) if (async_plans or self.express_slots) else 1
         self.pending = {}          # key -> (future, reserved bytes)
         self.pending_bytes = 0
-        self.factory = cf.ThreadPoolExecutor(max_workers=1) if async_plans else None
+        # background plan creation: `plan_workers` threads (the backend gives
+        # each its own set-up stream)
+        self.factory = cf.ThreadPoolExecutor(max_workers=max(1, int(plan_workers))) if async_plans else None
+
+    def small(self, req):
+        return self.express_slots > 0 and request_cost(req.n, req.dtype) <= self.express_cost
+
+    def _pick_slot(self, free, small):
+        """A free slot for a request: small ones take an express slot first,
+        large ones only the others; None if there is none."""
+        if not self.express_slots:
+            return free[-1]
+        first_express = self.slots - self.express_slots
+        normal = [s for s in free if s < first_express]
+        if small:
+            express = [s for s in free if s >= first_express]
+            return (express or normal)[-1]
+        return normal[-1] if normal else None
 
     def used(self):
         return self.pool.bytes + self.backend.spectrum_bytes() + self.inflight_bytes + self.pending_bytes
@@ -226,11 +269,18 @@ class Server:
             # admission: the first `lookahead` queued requests in arrival
             # order; one waiting for memory stops the scan (nothing behind
             # it may take the memory it waits for), one whose plan is being
-            # built is passed over
+            # built is passed over, and so is a large request with no slot
+            # of its kind free (and every large request behind it)
             j = 0
+            large_blocked = False
             while j < len(queue) and j < self.lookahead and free:
                 req = queue[j]
-                slot = free[-1]
+                small = self.small(req)
+                slot = None if (large_blocked and not small) else self._pick_slot(free, small)
+                if slot is None:
+                    large_blocked = True
+                    j += 1
+                    continue
                 verdict = self._admit(req, slot)
                 if verdict == "wait" and not inflight and not self.pending:
                     # nothing will complete to make room: drop the cached
@@ -251,7 +301,7 @@ class Server:
                     done += 1
                 else:
                     req.admitted = clock() - t0
-                    free.pop()
+                    free.remove(slot)
                     inflight[slot] = req
                 progressed = True
             if not progressed:
@@ -297,13 +347,31 @@ class TorchBackend:
     slot, a completion event per request, and a bank of client sources (one
     seeded multi-sphere source per (N, dtype), made before serving starts)."""
 
-    def __init__(self, slots, device=0):
+    def __init__(self, slots, device=0, express_slots=0):
         import torch
         self.torch = torch
         self.dev = torch.device("cuda", device)
-        self.streams = [torch.cuda.Stream(device=self.dev) for _ in range(slots)]
-        self.setup_stream = torch.cuda.Stream(device=self.dev)
+        # the express slots (the last ones) run on high-priority streams: the
+        # block scheduler gives their pending blocks the SMs that free up
+        # before those of the other streams' queued kernels
+        self.slots = slots
+        self.set_express(express_slots)
+        self._tls = threading.local()  # one set-up stream per plan-creating thread
         self.bank = {}
+
+    def set_express(self, express_slots):
+        """Give the last `express_slots` slots high-priority streams (the
+        others normal ones)."""
+        torch = self.torch
+        self.streams = [torch.cuda.Stream(device=self.dev, priority=-1 if s >= self.slots - express_slots else 0)
+                        for s in range(self.slots)]
+
+    @property
+    def setup_stream(self):
+        st = getattr(self._tls, "stream", None)
+        if st is None:
+            st = self._tls.stream = self.torch.cuda.Stream(device=self.dev)
+        return st
 
     def source(self, n, dtype):
         key = (n, dtype)

@@ -5,9 +5,12 @@ and match the oracle.
   streams give bitwise the potentials of one-at-a-time solves, with the
   FP64 class served in FP64 and as float pairs (df64), as the benchmark
   serves it.
+* Plans created on four threads at once (shared and distinct spectra) solve
+  bitwise like plans created one at a time.
 * The whole 10 000-request serving mix (cubic N log-uniform in [32, 384],
   70 % FP32 / 30 % FP64 class as df64), served cold (plans and spectra built
-  on the server's background thread while it serves): every request with
+  on the server's four background threads while it serves, two express
+  slots on high-priority streams, as the benchmark serves it): every request with
   N <= 64 against the full-grid FP64 oracle, and a seeded 1 % sample of the
   rest at sampled cells against the direct sum.
 """
@@ -32,9 +35,10 @@ def _gpu():
 
 def _alone_equals_mix(reqs, slots, budget):
     from paper_1106_0557_gb300 import Plan
-    be = serving.TorchBackend(slots=slots)
+    be = serving.TorchBackend(slots=slots, express_slots=2)
     be.prepare(reqs)
-    srv = serving.Server(be, budget_bytes=budget, slots=slots, keep_outputs=True, async_plans=True)
+    srv = serving.Server(be, budget_bytes=budget, slots=slots, keep_outputs=True, async_plans=True,
+                         plan_workers=4, express_slots=2)
     srv.run(reqs)
     torch.cuda.synchronize()
     assert all(r.status == serving.OK for r in reqs)
@@ -88,10 +92,11 @@ def test_served_mix_matches_oracle():
             cells[r.id] = c
             kept[r.id] = r.out.double().reshape(-1)[torch.from_numpy(c).to(r.out.device)].cpu().numpy()
 
-    be = serving.TorchBackend(slots=8)
+    be = serving.TorchBackend(slots=8, express_slots=2)
     be.prepare(reqs)
     native.ipf_greens_cache_trim(0)
-    srv = serving.Server(be, budget_bytes=120e9, slots=8, on_finish=on_finish, async_plans=True)
+    srv = serving.Server(be, budget_bytes=120e9, slots=8, on_finish=on_finish, async_plans=True, plan_workers=4,
+                         express_slots=2)
     srv.run(reqs)
     torch.cuda.synchronize()
     srv.close()
@@ -115,3 +120,32 @@ def test_served_mix_matches_oracle():
         ref = oracle.direct_points(s64, (1.0 / r.n,) * 3, cells[r.id])
         scale = np.abs(ref).max()
         assert np.abs(kept[r.id] - ref).max() / scale <= TOL[r.dtype], (r.id, r.n, r.dtype)
+
+
+def test_plans_created_concurrently_solve_like_plans_created_alone():
+    """Four threads create plans at once (several share a doubled mesh and
+    so a cached spectrum, built by one of them while the others wait); each
+    plan's solve is bitwise that of a plan created alone afterwards."""
+    import concurrent.futures as cf
+    from paper_1106_0557_gb300 import Plan
+    shapes = [(40, "f32"), (48, "f32"), (40, "df64"), (70, "f32"), (100, "df64"), (36, "f32"), (64, "f64"),
+              (90, "f32")]
+    native.ipf_greens_cache_trim(0)
+    be = serving.TorchBackend(slots=1)
+
+    def make(shape):
+        n, dtype = shape
+        return be.create_plan(n, dtype)[0]
+
+    with cf.ThreadPoolExecutor(max_workers=4) as ex:
+        plans = list(ex.map(make, shapes))
+    torch.cuda.synchronize()
+    for (n, dtype), p in zip(shapes, plans):
+        src = be.source(n, dtype)
+        out = torch.empty_like(src)
+        native.ipf_solve(p, src.data_ptr(), out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        with Plan((n,) * 3, (1.0 / n,) * 3, dtype) as q:
+            alone = q.solve(src)
+        torch.cuda.synchronize()
+        assert torch.equal(out, alone), (n, dtype)
+        native.ipf_plan_destroy(p)

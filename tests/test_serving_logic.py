@@ -183,3 +183,47 @@ def test_async_lookahead_passes_requests_waiting_for_a_plan():
     assert all(r.status == serving.OK for r in reqs)
     assert reqs[1].admitted <= reqs[0].admitted
     srv.close()
+
+
+def test_express_slot_serves_small_requests_past_a_burst_of_large_ones():
+    """With one of four slots kept for cheap requests, small requests that
+    arrive behind a burst of large ones run at once on that slot; the large
+    ones never take it and keep their arrival order."""
+    clock = FakeClock()
+    be = FakeBackend(clock)
+    srv = serving.Server(be, budget_bytes=1e12, slots=4, express_slots=1)
+    big = [serving.Request(i, 48, "f64", i, 0.0) for i in range(8)]
+    small = [serving.Request(100 + i, 16, "f32", i, 1e-4) for i in range(4)]
+    assert not any(srv.small(r) for r in big) and all(srv.small(r) for r in small)
+    srv.run(big + small, clock=clock)
+    assert all(r.status == serving.OK for r in big + small)
+    assert all(r.slot < 3 for r in big)
+    assert max(r.finished for r in small) < max(r.admitted for r in big)
+    adm = [r.admitted for r in big]
+    assert adm == sorted(adm)
+    # without the express slot the small requests wait for the large ones
+    clock = FakeClock()
+    srv = serving.Server(FakeBackend(clock), budget_bytes=1e12, slots=4)
+    big = [serving.Request(i, 48, "f64", i, 0.0) for i in range(8)]
+    small = [serving.Request(100 + i, 16, "f32", i, 1e-4) for i in range(4)]
+    srv.run(big + small, clock=clock)
+    assert min(r.admitted for r in small) > max(r.admitted for r in big)
+
+
+def test_express_slots_keep_the_budget_and_complete_a_mix():
+    clock = FakeClock()
+    be = FakeBackend(clock, fail={(40, "f64")})
+    budget = 3 * be.plan_bytes(48, "f64")
+    srv = serving.Server(be, budget_bytes=budget, slots=4, express_slots=1, async_plans=True, lookahead=16,
+                         express_cost=serving.request_cost(24, "f32"))
+    reqs = make_requests(300, rate=2000.0)
+    srv.run(reqs, clock=clock)
+    st = [r.status for r in reqs]
+    assert all(s == serving.OK or (r.n == 40 and r.dtype == "f64") for s, r in zip(st, reqs))
+    assert srv.peak_bytes <= budget
+    big = sorted((r for r in reqs if r.status == serving.OK and not srv.small(r)), key=lambda r: r.arrival)
+    assert all(r.slot < 3 for r in big)
+    srv.close()
+    assert be.live == set()
+    with pytest.raises(ValueError):
+        serving.Server(be, slots=2, express_slots=2)
