@@ -49,6 +49,7 @@ namespace isofft {
 // [Nz][My][Kx].  Every pass addresses W through this map.
 __host__ __device__ __forceinline__ size_t w_row(int64_t z, int64_t y, int64_t My, int zsh)
 {
+    if (zsh == 0) return (size_t)(z * My + y);  // (a uniform branch: the plain layout's arithmetic)
     return (size_t)((((z >> zsh) * My + y) << zsh) + (z & ((int64_t(1) << zsh) - 1)));
 }
 // A launch on nz planes of a z-blocked workspace covers whole blocks only
@@ -537,7 +538,9 @@ __device__ __forceinline__ void x_inverse_row(const Cx<T> *__restrict__ W, In<T>
 
 // K2 body: y forward of columns kx0 .. kx0 + TX - 1 of plane z.  Rows
 // y >= Ny are zero padding and are not read.
-template <typename T, int L, int TX, bool CG = false>
+// BLK: the workspace is z-blocked (w_row with shift zsh); otherwise plain
+// and zsh is ignored.
+template <typename T, int L, int TX, bool CG = false, bool BLK = false>
 __device__ __forceinline__ void y_forward_tile(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx,
                                                int z, int kx0, Cx<T> *smem, int c, int t,
                                                const Cx<T> *staged = nullptr, int zsh = 0)
@@ -545,8 +548,8 @@ __device__ __forceinline__ void y_forward_tile(Cx<T> *__restrict__ W, const Cx<T
     constexpr int E = Shape<T, L>::E, NT = L / E;
     const int kx = kx0 + c;
     const bool active = kx < Kx;
-    Cx<T> *base = W + w_row(z, 0, L, zsh) * Kx + (active ? kx : 0);
-    const size_t ys = (size_t)Kx << zsh;  // row stride
+    Cx<T> *base = W + (BLK ? w_row(z, 0, L, zsh) : (size_t)z * L) * Kx + (active ? kx : 0);
+    const int ys = BLK ? Kx << zsh : Kx;  // row stride
     Cx<T> v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) {
@@ -566,7 +569,7 @@ __device__ __forceinline__ void y_forward_tile(Cx<T> *__restrict__ W, const Cx<T
 }
 
 // K4 body: y inverse of a column tile of plane z, keeping rows y < Ny.
-template <typename T, int L, int TX>
+template <typename T, int L, int TX, bool BLK = false>
 __device__ __forceinline__ void y_inverse_tile(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx,
                                                int z, int kx0, Cx<T> *smem, int c, int t,
                                                const Cx<T> *staged = nullptr, int zsh = 0)
@@ -574,8 +577,8 @@ __device__ __forceinline__ void y_inverse_tile(Cx<T> *__restrict__ W, const Cx<T
     constexpr int E = Shape<T, L>::E, NT = L / E;
     const int kx = kx0 + c;
     const bool active = kx < Kx;
-    Cx<T> *base = W + w_row(z, 0, L, zsh) * Kx + (active ? kx : 0);
-    const size_t ys = (size_t)Kx << zsh;  // row stride
+    Cx<T> *base = W + (BLK ? w_row(z, 0, L, zsh) : (size_t)z * L) * Kx + (active ? kx : 0);
+    const int ys = BLK ? Kx << zsh : Kx;  // row stride
     Cx<T> v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) {
@@ -663,24 +666,26 @@ k_x_inverse(const Cx<T> *__restrict__ W, In<T> *__restrict__ phi, const Cx<T> *_
 // keep the loads in flight; best where the persistent form (below) would
 // hold fewer warps per SM (small lines, 16-byte points).
 // ---------------------------------------------------------------------
-template <typename T, int L, bool NARROW = false>
+template <typename T, int L, bool NARROW = false, bool BLK = false>
 __global__ void __launch_bounds__(ColCfg<T, L, NARROW>::THREADS, ColCfg<T, L, NARROW>::MIN_BLOCKS_FWD)
 k_y_forward(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx, int zsh)
 {
     using C = ColCfg<T, L, NARROW>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    y_forward_tile<T, L, C::TX>(W, tw, Ny, Kx, blockIdx.y, blockIdx.x * C::TX, reinterpret_cast<Cx<T> *>(smem_raw),
-                                threadIdx.x % C::TX, threadIdx.x / C::TX, nullptr, zsh);
+    y_forward_tile<T, L, C::TX, false, BLK>(W, tw, Ny, Kx, blockIdx.y, blockIdx.x * C::TX,
+                                            reinterpret_cast<Cx<T> *>(smem_raw), threadIdx.x % C::TX,
+                                            threadIdx.x / C::TX, nullptr, zsh);
 }
 
-template <typename T, int L, bool NARROW = false>
+template <typename T, int L, bool NARROW = false, bool BLK = false>
 __global__ void __launch_bounds__(ColCfg<T, L, NARROW>::THREADS)
 k_y_inverse(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx, int zsh)
 {
     using C = ColCfg<T, L, NARROW>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    y_inverse_tile<T, L, C::TX>(W, tw, Ny, Kx, blockIdx.y, blockIdx.x * C::TX, reinterpret_cast<Cx<T> *>(smem_raw),
-                                threadIdx.x % C::TX, threadIdx.x / C::TX, nullptr, zsh);
+    y_inverse_tile<T, L, C::TX, BLK>(W, tw, Ny, Kx, blockIdx.y, blockIdx.x * C::TX,
+                                     reinterpret_cast<Cx<T> *>(smem_raw), threadIdx.x % C::TX, threadIdx.x / C::TX,
+                                     nullptr, zsh);
 }
 
 // z-pass exchanger.  With DB (two buffers, used in turn) an exchange needs a
@@ -772,7 +777,7 @@ struct YCfg {
                   "tensor copy destinations must stay 128-byte aligned");
 };
 
-template <typename T, int L, bool FWD>
+template <typename T, int L, bool FWD, bool BLK = false>
 __global__ void __launch_bounds__(YCfg<T, L>::THREADS, YCfg<T, L>::MIN_BLOCKS)
 k_y_pass(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny,
          int Kx, int ntiles, unsigned *__restrict__ status, int zsh)
@@ -805,7 +810,7 @@ k_y_pass(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, const C
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             void *dst = s_in + set * IN + (size_t)b * BOX * TX * sizeof(Cx<T>);
-            if (zsh == 0)
+            if constexpr (!BLK)
                 tma_load_3d(dst, &tmW, xt * TX * C::EPC, b * BOX, z, &bar[set]);
             else  // tmW dims {Kx EPC, 2^zsh, rows, Nz >> zsh}
                 tma_load_4d(dst, &tmW, xt * TX * C::EPC, z & ((1 << zsh) - 1), b * BOX, z >> zsh, &bar[set]);
@@ -841,8 +846,8 @@ k_y_pass(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, const C
         }
         z_fft<C::TW_REGS, FWD, T, L, E>(v, t, twr, tw, xch, Rad{});
         if (kx < Kx) {
-            Cx<T> *base = W + w_row(z, 0, L, zsh) * Kx + kx;
-            const size_t ys = (size_t)Kx << zsh;  // row stride
+            Cx<T> *base = W + (BLK ? w_row(z, 0, L, zsh) : (size_t)z * L) * Kx + kx;
+            const int ys = BLK ? Kx << zsh : Kx;  // row stride
             if constexpr (FWD) {
 #pragma unroll
                 for (int m = 0; m < E; ++m) base[(size_t)(t + m * NT) * ys] = v[m];

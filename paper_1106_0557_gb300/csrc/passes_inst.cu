@@ -156,10 +156,12 @@ template <typename T, int L, bool FWD, bool NARROW>
 static cudaError_t run_y_tile(void *W, const void *tw, int Ny, int Kx, int Nz, int zsh, cudaStream_t st)
 {
     using C = ColCfg<T, L, NARROW>;
-    static std::atomic<uint64_t> done{0};
-    auto *k = FWD ? k_y_forward<T, L, NARROW> : k_y_inverse<T, L, NARROW>;
+    static std::atomic<uint64_t> done0{0}, doneb{0};
+    // plain and z-blocked workspace instances
+    auto *k = zsh ? (FWD ? k_y_forward<T, L, NARROW, true> : k_y_inverse<T, L, NARROW, true>)
+                  : (FWD ? k_y_forward<T, L, NARROW, false> : k_y_inverse<T, L, NARROW, false>);
     if (!w_blocks_ok(Nz, zsh)) return cudaErrorInvalidValue;
-    cudaError_t e = ensure_smem(k, C::SMEM, done);
+    cudaError_t e = ensure_smem(k, C::SMEM, zsh ? doneb : done0);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((Kx + C::TX - 1) / C::TX), (unsigned)Nz);
     k<<<grid, C::THREADS, C::SMEM, st>>>((Cx<T> *)W, (const Cx<T> *)tw, Ny, Kx, zsh);
@@ -172,15 +174,16 @@ static cudaError_t run_y_stream(void *W, const void *tw, int Ny, int Kx, int Nz,
 {
     using C = YCfg<T, L>;
     constexpr size_t SMEM = FWD ? C::SMEM_F : C::SMEM_I;
-    static std::atomic<uint64_t> done{0};
-    static std::atomic<int> slots{0};
+    static std::atomic<uint64_t> done0{0}, doneb{0};
+    static std::atomic<int> slots0{0}, slotsb{0};
     if ((uintptr_t)W & 15) return cudaErrorMisalignedAddress;
-    auto *k = k_y_pass<T, L, FWD>;
-    cudaError_t e = ensure_smem(k, SMEM, done);
+    // plain and z-blocked workspace instances
+    auto *k = zsh ? k_y_pass<T, L, FWD, true> : k_y_pass<T, L, FWD, false>;
+    cudaError_t e = ensure_smem(k, SMEM, zsh ? doneb : done0);
     if (e != cudaSuccess) return e;
     const int ntx = (Kx + C::TX - 1) / C::TX;
     const int ntiles = ntx * Nz;
-    int grid = resident_ctas(k, C::THREADS, SMEM, slots);
+    int grid = resident_ctas(k, C::THREADS, SMEM, zsh ? slotsb : slots0);
     if (grid <= 0) return cudaErrorInvalidConfiguration;
     if (grid > ntiles) grid = ntiles;
     // W as 8-byte elements [Nz][My][Kx * EPC] (z-blocked: [Nz >> zsh][My][2^zsh][Kx * EPC], mapped as
