@@ -200,9 +200,44 @@ struct DftCT {
     }
 };
 
+// Radix 8 as 2 x 4 (the DftCT order: even bins from the sums, odd bins from
+// the differences twiddled by W_8^n), with the two 1/sqrt(2) roots of the odd
+// half factored out: W_8 m1 + W_8^3 m3 = r (c1 + c3) with r = 1/sqrt(2) and
+// c1, c3 sums and differences of the components, so that r multiplies
+// inside the last level's additions (one fused multiply-add each) instead of
+// four separate products.  Odd bins: the 4-point DFT of
+// (m0, W_8 m1, -i m2, W_8^3 m3).
+template <typename T>
+ISOFFT_HD void dft4_w8_odd(Cx<T> m0, Cx<T> m1, Cx<T> m2, Cx<T> m3, Cx<T> &o0, Cx<T> &o1, Cx<T> &o2, Cx<T> &o3)
+{
+    constexpr T r = (T)0.7071067811865476;
+    const Cx<T> c1 = {m1.x + m1.y, m1.y - m1.x};    // W_8 m1 / r
+    const Cx<T> c3 = {m3.y - m3.x, -(m3.x + m3.y)};  // W_8^3 m3 / r
+    const Cx<T> S = cadd(c1, c3), D = csub(c1, c3);
+    const Cx<T> s02 = {m0.x + m2.y, m0.y - m2.x}, d02 = {m0.x - m2.y, m0.y + m2.x};  // m0 +- (-i m2)
+    o0 = {s02.x + r * S.x, s02.y + r * S.y};
+    o2 = {s02.x - r * S.x, s02.y - r * S.y};
+    o1 = {d02.x + r * D.y, d02.y - r * D.x};  // d02 - i r D
+    o3 = {d02.x - r * D.y, d02.y + r * D.x};
+}
+
 template <typename T>
 struct Dft<T, 8> {
-    static ISOFFT_HD void run(Cx<T> (&a)[8]) { DftCT<T, 2, 4>::run(a); }
+    static ISOFFT_HD void run(Cx<T> (&a)[8])
+    {
+        Cx<T> p[4], m[4];
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+            p[n] = cadd(a[n], a[n + 4]);
+            m[n] = csub(a[n], a[n + 4]);
+        }
+        Dft<T, 4>::run(p);
+        a[0] = p[0];
+        a[2] = p[1];
+        a[4] = p[2];
+        a[6] = p[3];
+        dft4_w8_odd(m[0], m[1], m[2], m[3], a[1], a[3], a[5], a[7]);
+    }
 };
 template <typename T>
 struct Dft<T, 6> {
@@ -245,6 +280,21 @@ struct DftHalf {
             a[2 * k] = e[k];
             a[2 * k + 1] = o[k];
         }
+    }
+};
+// Radix 8 with a[4..8) zero: even bins the 4-point DFT of a[0..4), odd
+// bins as in Dft<T, 8> with m = a.
+template <typename T>
+struct DftHalf<T, 8> {
+    static ISOFFT_HD void run(Cx<T> (&a)[8])
+    {
+        Cx<T> e[4] = {a[0], a[1], a[2], a[3]};
+        dft4_w8_odd(a[0], a[1], a[2], a[3], a[1], a[3], a[5], a[7]);
+        Dft<T, 4>::run(e);
+        a[0] = e[0];
+        a[2] = e[1];
+        a[4] = e[2];
+        a[6] = e[3];
     }
 };
 template <typename T>
