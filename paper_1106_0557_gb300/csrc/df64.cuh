@@ -43,6 +43,24 @@ __host__ __device__ __forceinline__ df64 operator+(df64 a, df64 b)
     return df64_fast_two_sum(s, e);
 }
 
+// The sum without its closing renormalisation: hi = fl(a.hi + b.hi) and lo
+// its exact error plus a.lo + b.lo.  hi + lo is the same sloppy sum, but lo
+// may exceed half an ulp of hi (by a few ulps along a chain of such sums,
+// and more where hi cancels).  The FFT engine's butterflies chain these and
+// renormalise (df64_renorm) before any product, whose error term drops
+// lo x lo and so needs |lo| << |hi|.
+__host__ __device__ __forceinline__ df64 df64_add_lazy(df64 a, df64 b)
+{
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb);
+    return {s, e + (a.lo + b.lo)};
+}
+__host__ __device__ __forceinline__ df64 df64_renorm(df64 a)
+{
+    return df64_fast_two_sum(a.hi, a.lo);
+}
+
 __host__ __device__ __forceinline__ df64 operator-(df64 a) { return {-a.hi, -a.lo}; }
 __host__ __device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
 

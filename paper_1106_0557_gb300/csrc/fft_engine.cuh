@@ -30,17 +30,35 @@ struct alignas(2 * sizeof(T)) Cx {
     T x, y;
 };
 
+// Sums inside the butterflies: plain for float and double; for float pairs
+// without the closing renormalisation (df64_add_lazy), which every product
+// below restores on its data operand first (crenorm; a no-op elsewhere).
 template <typename T>
-ISOFFT_HD Cx<T> cadd(Cx<T> a, Cx<T> b) { return {a.x + b.x, a.y + b.y}; }
+ISOFFT_HD T radd(T a, T b) { return a + b; }
 template <typename T>
-ISOFFT_HD Cx<T> csub(Cx<T> a, Cx<T> b) { return {a.x - b.x, a.y - b.y}; }
+ISOFFT_HD T rsub(T a, T b) { return a - b; }
+ISOFFT_HD df64 radd(df64 a, df64 b) { return df64_add_lazy(a, b); }
+ISOFFT_HD df64 rsub(df64 a, df64 b) { return df64_add_lazy(a, -b); }
+template <typename T>
+ISOFFT_HD Cx<T> crenorm(Cx<T> a) { return a; }
+ISOFFT_HD Cx<df64> crenorm(Cx<df64> a) { return {df64_renorm(a.x), df64_renorm(a.y)}; }
+
+template <typename T>
+ISOFFT_HD Cx<T> cadd(Cx<T> a, Cx<T> b) { return {radd(a.x, b.x), radd(a.y, b.y)}; }
+template <typename T>
+ISOFFT_HD Cx<T> csub(Cx<T> a, Cx<T> b) { return {rsub(a.x, b.x), rsub(a.y, b.y)}; }
 template <typename T>
 ISOFFT_HD Cx<T> cmul(Cx<T> a, Cx<T> b)
 {
-    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+    a = crenorm(a);
+    return {rsub(a.x * b.x, a.y * b.y), radd(a.x * b.y, a.y * b.x)};
 }
 template <typename T>
-ISOFFT_HD Cx<T> cscale(Cx<T> a, T s) { return {a.x * s, a.y * s}; }
+ISOFFT_HD Cx<T> cscale(Cx<T> a, T s)
+{
+    a = crenorm(a);
+    return {a.x * s, a.y * s};
+}
 template <typename T>
 ISOFFT_HD Cx<T> cconj(Cx<T> a) { return {a.x, -a.y}; }
 // multiply by -i
@@ -75,6 +93,7 @@ ISOFFT_HD Cx<T> mul_root(Cx<T> a)
 {
     constexpr int ee = ((e % R) + R) % R;
     constexpr int j = ee * (48 / R);  // angle in units of 2 pi / 48
+    if constexpr (j != 0 && j % 12 != 0) a = crenorm(a);  // a product follows
     if constexpr (j == 0) {
         return a;
     } else if constexpr (j == 12) {
@@ -89,11 +108,11 @@ ISOFFT_HD Cx<T> mul_root(Cx<T> a)
         constexpr bool cp = cos48(j) > 0, sp = sin48(j) > 0;
         const T cx = cp ? a.x : -a.x, cy = cp ? a.y : -a.y;  // c a / |c|
         const T sx = sp ? a.x : -a.x, sy = sp ? a.y : -a.y;  // s a / |s|
-        return {(cx + sy) * r, (cy - sx) * r};
+        return {(cx + sy) * r, (cy - sx) * r};  // normalised sums: products follow
     } else {
         constexpr T c = (T)cos48(j);
         constexpr T s = (T)sin48(j);
-        return {a.x * c + a.y * s, a.y * c - a.x * s};
+        return {radd(a.x * c, a.y * s), rsub(a.y * c, a.x * s)};
     }
 }
 
@@ -118,8 +137,8 @@ struct Dft<T, 3> {
     static ISOFFT_HD void run(Cx<T> (&a)[3])
     {
         constexpr T s3 = (T)0.8660254037844387;  // sin(2 pi / 3)
-        Cx<T> sum = cadd(a[1], a[2]);
-        Cx<T> dif = csub(a[1], a[2]);
+        Cx<T> sum = crenorm(cadd(a[1], a[2]));  // both enter products
+        Cx<T> dif = crenorm(csub(a[1], a[2]));
         Cx<T> t = {a[0].x - (T)0.5 * sum.x, a[0].y - (T)0.5 * sum.y};
         Cx<T> u = {dif.y * s3, -dif.x * s3};  // -i s3 (a1 - a2)
         a[0] = cadd(a[0], sum);
@@ -147,8 +166,8 @@ struct Dft<T, 5> {
     {
         constexpr T c1 = (T)0.30901699437494745, c2 = (T)-0.8090169943749473;
         constexpr T s1 = (T)0.9510565162951535, s2 = (T)0.5877852522924732;
-        Cx<T> b1 = cadd(a[1], a[4]), b2 = cadd(a[2], a[3]);
-        Cx<T> d1 = csub(a[1], a[4]), d2 = csub(a[2], a[3]);
+        Cx<T> b1 = crenorm(cadd(a[1], a[4])), b2 = crenorm(cadd(a[2], a[3]));  // all enter products
+        Cx<T> d1 = crenorm(csub(a[1], a[4])), d2 = crenorm(csub(a[2], a[3]));
         Cx<T> t1 = {a[0].x + c1 * b1.x + c2 * b2.x, a[0].y + c1 * b1.y + c2 * b2.y};
         Cx<T> t2 = {a[0].x + c2 * b1.x + c1 * b2.x, a[0].y + c2 * b1.y + c1 * b2.y};
         Cx<T> u1 = {s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y};
@@ -211,14 +230,14 @@ template <typename T>
 ISOFFT_HD void dft4_w8_odd(Cx<T> m0, Cx<T> m1, Cx<T> m2, Cx<T> m3, Cx<T> &o0, Cx<T> &o1, Cx<T> &o2, Cx<T> &o3)
 {
     constexpr T r = (T)0.7071067811865476;
-    const Cx<T> c1 = {m1.x + m1.y, m1.y - m1.x};    // W_8 m1 / r
-    const Cx<T> c3 = {m3.y - m3.x, -(m3.x + m3.y)};  // W_8^3 m3 / r
-    const Cx<T> S = cadd(c1, c3), D = csub(c1, c3);
-    const Cx<T> s02 = {m0.x + m2.y, m0.y - m2.x}, d02 = {m0.x - m2.y, m0.y + m2.x};  // m0 +- (-i m2)
-    o0 = {s02.x + r * S.x, s02.y + r * S.y};
-    o2 = {s02.x - r * S.x, s02.y - r * S.y};
-    o1 = {d02.x + r * D.y, d02.y - r * D.x};  // d02 - i r D
-    o3 = {d02.x - r * D.y, d02.y + r * D.x};
+    const Cx<T> c1 = {radd(m1.x, m1.y), rsub(m1.y, m1.x)};    // W_8 m1 / r
+    const Cx<T> c3 = {rsub(m3.y, m3.x), -radd(m3.x, m3.y)};  // W_8^3 m3 / r
+    const Cx<T> S = crenorm(cadd(c1, c3)), D = crenorm(csub(c1, c3));  // enter the products
+    const Cx<T> s02 = {radd(m0.x, m2.y), rsub(m0.y, m2.x)}, d02 = {rsub(m0.x, m2.y), radd(m0.y, m2.x)};
+    o0 = {radd(s02.x, r * S.x), radd(s02.y, r * S.y)};
+    o2 = {rsub(s02.x, r * S.x), rsub(s02.y, r * S.y)};
+    o1 = {radd(d02.x, r * D.y), rsub(d02.y, r * D.x)};  // d02 - i r D
+    o3 = {rsub(d02.x, r * D.y), radd(d02.y, r * D.x)};
 }
 
 template <typename T>
@@ -376,6 +395,8 @@ ISOFFT_HD void run_stages(Cx<T> (&v)[E], int t, const Cx<T> *__restrict__ tw, Xc
                                            Radices<Rs...>)
 {
     run_stages_impl<T, L, E, 1, HALF, Xch, Rs...>(v, t, tw, xch);
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = crenorm(v[m]);  // the transform's results leave normalised
 }
 
 // ---------------------------------------------------------------------
@@ -454,6 +475,8 @@ template <typename T, int L, int E, bool HALF, typename Xch, typename TWR, int..
 ISOFFT_HD void run_stages_reg(Cx<T> (&v)[E], int t, const TWR &twr, Xch &xch, Radices<Rs...>)
 {
     run_stages_reg_impl<T, L, E, 1, HALF, Xch, TWR, Rs...>(v, t, twr, xch);
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = crenorm(v[m]);  // the transform's results leave normalised
 }
 
 template <typename T, int L, int E, typename Rad>
