@@ -56,6 +56,17 @@ __host__ __device__ __forceinline__ df64 df64_add_lazy(df64 a, df64 b)
     const float e = (a.hi - (s - bb)) + (b.hi - bb);
     return {s, e + (a.lo + b.lo)};
 }
+// The product without its closing renormalisation (its lo is the exact
+// error of hi plus the cross terms, within a few ulps of hi): for products
+// that only enter sums.  Both operands must be normalised.
+__host__ __device__ __forceinline__ df64 df64_mul_lazy(df64 a, df64 b)
+{
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return {p, e};
+}
 __host__ __device__ __forceinline__ df64 df64_renorm(df64 a)
 {
     return df64_fast_two_sum(a.hi, a.lo);

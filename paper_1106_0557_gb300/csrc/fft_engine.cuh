@@ -37,7 +37,10 @@ template <typename T>
 ISOFFT_HD T radd(T a, T b) { return a + b; }
 template <typename T>
 ISOFFT_HD T rsub(T a, T b) { return a - b; }
+template <typename T>
+ISOFFT_HD T rmul(T a, T b) { return a * b; }  // a product that only enters sums
 ISOFFT_HD df64 radd(df64 a, df64 b) { return df64_add_lazy(a, b); }
+ISOFFT_HD df64 rmul(df64 a, df64 b) { return df64_mul_lazy(a, b); }
 ISOFFT_HD df64 rsub(df64 a, df64 b) { return df64_add_lazy(a, -b); }
 template <typename T>
 ISOFFT_HD Cx<T> crenorm(Cx<T> a) { return a; }
@@ -51,7 +54,7 @@ template <typename T>
 ISOFFT_HD Cx<T> cmul(Cx<T> a, Cx<T> b)
 {
     a = crenorm(a);
-    return {rsub(a.x * b.x, a.y * b.y), radd(a.x * b.y, a.y * b.x)};
+    return {rsub(rmul(a.x, b.x), rmul(a.y, b.y)), radd(rmul(a.x, b.y), rmul(a.y, b.x))};
 }
 template <typename T>
 ISOFFT_HD Cx<T> cscale(Cx<T> a, T s)
@@ -112,7 +115,7 @@ ISOFFT_HD Cx<T> mul_root(Cx<T> a)
     } else {
         constexpr T c = (T)cos48(j);
         constexpr T s = (T)sin48(j);
-        return {radd(a.x * c, a.y * s), rsub(a.y * c, a.x * s)};
+        return {radd(rmul(a.x, c), rmul(a.y, s)), rsub(rmul(a.y, c), rmul(a.x, s))};
     }
 }
 
@@ -234,10 +237,10 @@ ISOFFT_HD void dft4_w8_odd(Cx<T> m0, Cx<T> m1, Cx<T> m2, Cx<T> m3, Cx<T> &o0, Cx
     const Cx<T> c3 = {rsub(m3.y, m3.x), -radd(m3.x, m3.y)};  // W_8^3 m3 / r
     const Cx<T> S = crenorm(cadd(c1, c3)), D = crenorm(csub(c1, c3));  // enter the products
     const Cx<T> s02 = {radd(m0.x, m2.y), rsub(m0.y, m2.x)}, d02 = {rsub(m0.x, m2.y), radd(m0.y, m2.x)};
-    o0 = {radd(s02.x, r * S.x), radd(s02.y, r * S.y)};
-    o2 = {rsub(s02.x, r * S.x), rsub(s02.y, r * S.y)};
-    o1 = {radd(d02.x, r * D.y), rsub(d02.y, r * D.x)};  // d02 - i r D
-    o3 = {rsub(d02.x, r * D.y), radd(d02.y, r * D.x)};
+    o0 = {radd(s02.x, rmul(r, S.x)), radd(s02.y, rmul(r, S.y))};
+    o2 = {rsub(s02.x, rmul(r, S.x)), rsub(s02.y, rmul(r, S.y))};
+    o1 = {radd(d02.x, rmul(r, D.y)), rsub(d02.y, rmul(r, D.x))};  // d02 - i r D
+    o3 = {rsub(d02.x, rmul(r, D.y)), radd(d02.y, rmul(r, D.x))};
 }
 
 template <typename T>
