@@ -118,7 +118,8 @@ enum {
  *   dtype      IPF_F32, IPF_F64 or IPF_DF64.  The Green's spectrum is always
  *              built in FP64 and rounded to the plan's dtype.
  *   flags      a bitwise OR of IPF_FLAG_*.
- *   verbosity  an IPF_CONSOLE_* level.
+ *   verbosity  an IPF_CONSOLE_* level; the environment variable
+ *              ISOFFT_VERBOSITY (0-3), if set, overrides it.
  *   stream     stream used for the one-off set-up work (Green's spectrum
  *              build, table uploads); the call synchronises on it before
  *              returning.
