@@ -26,6 +26,9 @@
  *   - Every call returns an int status (ipf_status below); nothing throws
  *     across the ABI.  ipf_status_string() names a status.
  *   - A plan is used by one stream at a time (it owns one workspace).
+ *   - Plans may be created and destroyed from several host threads at once:
+ *     the spectrum cache and the y-pass timing table are locked, and a
+ *     spectrum that one thread is building is waited for, not built twice.
  *   - The caller owns its buffers.  A plan owns its workspace; the library
  *     owns the cache of Green's spectra, shared by plans of equal doubled
  *     mesh, width ratios and dtype.
