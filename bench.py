@@ -263,17 +263,19 @@ def time_oracle(n, steps, budget_s, warmup=0, keep=False):
 
 
 def potential_errors(potentials, refs):
-    """Normwise max|phi - ref| / max|ref| and pointwise max |phi - ref| / |ref|
+    """Normwise max|phi - ref| / max|ref|, pointwise max |phi - ref| / |ref|
     (well defined: the potential of a non-negative source is negative
-    everywhere) of each dtype's GPU potential against the FP64 oracle on the
-    same input; FP64 and df64 solve the FP64 source, FP32 its FP32 rounding."""
+    everywhere) and the L1 norm of Eq. 11, sum |phi - ref| / sum |ref|, of
+    each dtype's GPU potential against the FP64 oracle on the same input;
+    FP64 and df64 solve the FP64 source, FP32 its FP32 rounding."""
     tol = {"f32": 1e-5, "f64": 1e-12, "df64": 1e-12}
     out = {}
     for dt, phi in potentials.items():
         ref = refs["f32" if dt == "f32" else "f64"]
         d = np.abs(phi - ref)
         out[dt] = {"normwise": float(d.max() / np.abs(ref).max()), "pointwise": float((d / np.abs(ref)).max()),
-                   "tol": tol[dt], "cells": int(ref.size), "ref": "full-grid FP64 oracle solve"}
+                   "l1": float(d.sum() / np.abs(ref).sum()), "tol": tol[dt], "cells": int(ref.size),
+                   "ref": "full-grid FP64 oracle solve"}
     return out
 
 
