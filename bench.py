@@ -367,9 +367,11 @@ def run_batch(steps=50, count=64):
     res = {"grids": count, "workload": "ragged batch, each axis from {32,48,64,96,128}, seed = grid index",
            "how": {"graph": "per-grid passes on 8 library streams, captured in a CUDA graph",
                    "submit": "the same without the graph",
-                   "fused": "one launch per pass over a table of every grid's work items (ISOFFT_BATCH_FUSED=1)"}}
-    for mode in ("graph", "submit", "fused"):
-        os.environ["ISOFFT_BATCH_FUSED"] = "1" if mode == "fused" else "0"
+                   "fused": "one launch per pass over a table of every grid's work items (ISOFFT_BATCH_FUSED=1)",
+                   "one": "one persistent launch for all five passes, per-(grid, pass) completion counters "
+                          "(ISOFFT_BATCH_FUSED=2)"}}
+    for mode in ("graph", "submit", "fused", "one"):
+        os.environ["ISOFFT_BATCH_FUSED"] = {"fused": "1", "one": "2"}.get(mode, "0")
         if mode == "graph":
             bg = BatchGraph(plans, srcs, outs)
             run = bg.replay

@@ -235,7 +235,11 @@ int ipf_noalloc_check(void *stream);
  * together in one launch per pass (five launches for all of them, over a
  * table of their work items, built and uploaded synchronously the first
  * time a given set of plans and buffers is submitted -- do that before any
- * capture; the library keeps the tables of the last 64 such sets).  A plan may appear only
+ * capture; the library keeps the tables of the last 64 such sets); with
+ * ISOFFT_BATCH_FUSED=2 they run in one persistent launch for all five
+ * passes, an item waiting (bounded, 2 s) until its grid's previous pass is
+ * complete; a wait that runs out sets the status word of the first such
+ * plan (ipf_plan_check reports IPF_TIMEOUT).  A plan may appear only
  * once per batch (each owns one workspace).  The solves are spread over up to
  * 8 internal streams of the library that fork from and join back into
  * `stream`: the batch starts after the work already enqueued on `stream`, and

@@ -811,10 +811,12 @@ BatchLanes *g_lanes[64] = {};
 // grid's workspace through HBM between passes, while the per-grid passes
 // keep a grid's workspace in L2 from one pass to the next and measured
 // faster (config 4: 0.94 vs 1.38 ms per batch of 64).  Read at every call.
-bool batch_fused_enabled()
+// ISOFFT_BATCH_FUSED: 1 = one launch per pass, 2 = one launch for the
+// batch, anything else = per-grid passes on the library's streams
+int batch_fused_mode()
 {
     const char *v = getenv("ISOFFT_BATCH_FUSED");
-    return v && v[0] == '1';
+    return v && (v[0] == '1' || v[0] == '2') && v[1] == 0 ? v[0] - '0' : 0;
 }
 
 int batch_lanes(BatchLanes **out)
@@ -1043,10 +1045,13 @@ int ipf_submit_batch(const ipf_plan_t *plans, int count, const void *const *d_sr
     // small FP32 grids: one launch per pass over all of them (batch.cu)
     std::vector<BatchGridDesc> fused;
     std::vector<int> rest;
+    const int mode = batch_fused_mode();
+    unsigned *bstatus = nullptr;  // the first batched plan's status word
     for (int i = 0; i < count; ++i) {
         const ipf_plan_s *p = plans[i];
         const bool plain = !(p->flags & (IPF_FLAG_PASS_EVENTS | IPF_FLAG_TEST_WAIT_RUNOUT | IPF_FLAG_TEST_CANARY));
-        if (batch_fused_enabled() && plain && batch_fits(p->dtype == IPF_F32, p->M)) {
+        if (mode && plain && batch_fits(p->dtype == IPF_F32, p->M)) {
+            if (!bstatus) bstatus = p->status;
             fused.push_back({d_src[i], d_phi[i], p->W, p->tw_x, p->rtw, p->tw_y, p->tw_z, p->spec->G, p->spec->Gs,
                              p->gscale, (int)p->N[0], (int)p->N[1], (int)p->N[2], (int)p->M[0], (int)p->M[1],
                              (int)p->M[2]});
@@ -1059,7 +1064,7 @@ int ipf_submit_batch(const ipf_plan_t *plans, int count, const void *const *d_sr
             if (std::find(rest.begin(), rest.end(), i) == rest.end()) rest.push_back(i);
         fused.clear();
     }
-    if (rest.empty()) return cuda_status(batch_enqueue(fused.data(), (int)fused.size(), st));
+    if (rest.empty()) return cuda_status(batch_enqueue(fused.data(), (int)fused.size(), mode, bstatus, st));
     BatchLanes *bl = nullptr;
     int rc = batch_lanes(&bl);
     if (rc) return rc;
@@ -1074,7 +1079,7 @@ int ipf_submit_batch(const ipf_plan_t *plans, int count, const void *const *d_sr
         if (e != cudaSuccess) return cuda_status(e);
     }
     if (!fused.empty()) {
-        e = batch_enqueue(fused.data(), (int)fused.size(), st);
+        e = batch_enqueue(fused.data(), (int)fused.size(), mode, bstatus, st);
         if (e != cudaSuccess) return cuda_status(e);
     }
     // the other solves longest first, each to the least-loaded lane

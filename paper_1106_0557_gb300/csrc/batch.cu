@@ -10,7 +10,8 @@
 // threads than the launch has, the CTA runs several of its items side by
 // side (sub-groups with their own shared memory).  Each pass waits for the
 // previous one by stream order, so a batch costs five launches whatever its
-// size, instead of five per grid.
+// size, instead of five per grid.  k_batch_all (below) runs all five passes
+// in one persistent launch instead.
 //
 // Classes: FP32 grids whose doubled mesh is at most 256 on every axis
 // (row lengths Mx/2 of 16 to 128, column lengths 32 to 256).  Other grids
@@ -304,6 +305,160 @@ k_batch_z(const BatchGrid *__restrict__ grids, const BatchItem *__restrict__ ite
 }
 
 // ---------------------------------------------------------------------
+// The whole batch in one launch (k_batch_all): a persistent kernel walks one
+// table holding every grid's items of all five passes.  An item of pass p
+// of grid g may start only when every item of pass p - 1 of g has finished:
+// per (grid, pass) completion counters, raised by each item's CTA after its
+// stores (thread 0: barrier, device-scope fence, atomic add) and awaited by
+// thread 0 of a dependent item (acquire load, bounded wait, fence, barrier).
+// Items are taken in table order from one atomic queue head, so an item
+// only ever waits for items taken before it by running CTAs: no deadlock,
+// whatever the number of resident CTAs.  The table is ordered along
+// diagonals of (grid, pass): (0,K1), (0,K2), (1,K1), (0,K3), (1,K2), (2,K1),
+// ..., so each grid's passes follow each other closely and only about five
+// grids' workspaces are live at a time (L2-sized for these grids), while a
+// wait for the tail of one pass overlaps other grids' items.
+//
+// A wait that runs out (2 s) sets bit 0 of the status word and an abort
+// flag that every CTA checks, so the launch ends promptly with the error.
+// Loads of data written in the launch bypass L1 (L2-only loads, cp.async.cg).
+// ---------------------------------------------------------------------
+constexpr int kMegaThreads = kBatchColThreads;
+// Grids per window of the table order.  Measured on the 64-grid batch:
+// 2.53 ms per batch with windows of 1 grid, 2.57-2.67 ms with 4 to 64 (64:
+// plain pass order); the waits are not what costs.  What does is occupancy:
+// the z body's 128 registers at 512 threads leave one CTA per SM, where the
+// x and y bodies run 3-4 CTAs per SM in their own launches (five launches:
+// 1.40 ms; per-grid passes on the library's streams: 0.94 ms).
+constexpr int kMegaWindow = 1;
+constexpr uint32_t kPassShift = 28;  // BatchItem::grid_cls bits 28..30: the pass
+
+// x items cover two row groups (512 threads)
+template <int L>
+__host__ __device__ int64_t mega_row_items(const BatchGrid &g)
+{
+    return (BRow<L>::items(g) + 1) / 2;
+}
+
+template <int L, bool FWD>
+__device__ __forceinline__ void mega_row(const BatchGrid &g, uint32_t idx, unsigned char *smem)
+{
+    using C = RowCfg<float, L>;
+    const int t = threadIdx.x % C::NT, l = threadIdx.x / C::NT;  // l < 2 NL
+    Cx<float> *line = reinterpret_cast<Cx<float> *>(smem) + l * RowPad<float, L>::LP;
+    const int64_t nrows = (int64_t)g.Ny * g.Nz;
+    const int64_t row = (int64_t)idx * 2 * C::NL + l;
+    const bool active = row < nrows;
+    if constexpr (FWD)
+        x_forward_row<float, L>(g.src, g.W, g.tw_x, g.rtw, g.Nx, g.Ny, g.My, active ? row : 0, active, line, t, 0);
+    else
+        x_inverse_row<float, L, true>(g.W, g.phi, g.tw_x, g.rtw, g.Nx, g.Ny, g.My, active ? row : 0, active, line,
+                                      t, 0);
+}
+
+template <int L, bool FWD>
+__device__ __forceinline__ void mega_col(const BatchGrid &g, uint32_t idx, unsigned char *smem)
+{
+    using B = BCol<L>;
+    using C = typename B::C;
+    const int s = threadIdx.x / C::THREADS, lt = threadIdx.x % C::THREADS;
+    const int ntx = (g.Kx + C::TX - 1) / C::TX;
+    const int64_t tile = (int64_t)idx * B::SUB + s;
+    const bool live = tile < B::tiles(g);
+    const int z = live ? (int)(tile / ntx) : 0, xt = live ? (int)(tile % ntx) : 0;
+    const int Kx = live ? g.Kx : 0;
+    Cx<float> *sm = reinterpret_cast<Cx<float> *>(smem + (size_t)s * C::SMEM);
+    if constexpr (FWD)
+        y_forward_tile<float, L, C::TX, true>(g.W, g.tw_y, g.Ny, Kx, z, xt * C::TX, sm, lt % C::TX, lt / C::TX);
+    else
+        y_inverse_tile<float, L, C::TX, false, true>(g.W, g.tw_y, g.Ny, Kx, z, xt * C::TX, sm, lt % C::TX,
+                                                     lt / C::TX);
+}
+
+template <int L>
+__device__ __forceinline__ void mega_z(const BatchGrid &g, uint32_t idx, unsigned char *smem)
+{
+    unsigned char *X = smem, *S = smem + BZAll::X;
+    batch_z_stage<L>(g, idx, S);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    batch_z_compute<L>(g, idx, S, X);
+}
+
+constexpr size_t kMegaSmem = BZAll::X + BZAll::S;
+
+// Thread 0: wait until *cnt reaches `need` (acquire), giving up after the
+// copy-wait limit or when another CTA has aborted.
+__device__ __forceinline__ bool mega_wait(const uint32_t *cnt, uint32_t need, const uint32_t *abort_flag)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(cnt) : "memory");
+    if (v >= need) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 1; i < (1u << 26); ++i) {
+        __nanosleep(64);
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(cnt) : "memory");
+        if (v >= need) return true;
+        if ((i & 31) == 0) {
+            uint32_t a;
+            asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];\n" : "=r"(a) : "l"(abort_flag) : "memory");
+            if (a || global_ns() - t0 > kCopyWaitNs) return false;
+        }
+    }
+    return false;
+}
+
+// state: [0] queue head, [1] abort flag, [2 + 5 g + p] items of pass p of
+// grid g finished; need[5 g + p]: items of pass p of grid g.
+__global__ void __launch_bounds__(kMegaThreads)
+k_batch_all(const BatchGrid *__restrict__ grids, const BatchItem *__restrict__ items, int nitems,
+            const uint32_t *__restrict__ need, uint32_t *state, unsigned *status)
+{
+    extern __shared__ __align__(16) unsigned char bsm[];
+    __shared__ int s_item, s_ok;
+    uint32_t *done = state + 2;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(&state[0], 1u);
+        __syncthreads();
+        const int i = s_item;
+        if (i >= nitems) break;
+        const BatchItem it = items[i];
+        const int pass = (int)(it.grid_cls >> kPassShift), grid = (int)((it.grid_cls >> 8) & 0xFFFFFu);
+        const int cls = (int)(it.grid_cls & 255u);
+        if (threadIdx.x == 0) {
+            bool ok = true;
+            if (pass > 0) ok = mega_wait(&done[5 * grid + pass - 1], need[5 * grid + pass - 1], &state[1]);
+            __threadfence();
+            if (!ok) {
+                if (status) atomicOr(status, 1u);
+                atomicExch(&state[1], 1u);
+            }
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        const BatchGrid &g = grids[grid];
+        switch (pass * 8 + cls) {
+#define X_(c)                                                            \
+    case 0 * 8 + c: mega_row<kBatchRows[c], true>(g, it.idx, bsm); break;  \
+    case 1 * 8 + c: mega_col<kBatchCols[c], true>(g, it.idx, bsm); break;  \
+    case 2 * 8 + c: mega_z<kBatchCols[c]>(g, it.idx, bsm); break;          \
+    case 3 * 8 + c: mega_col<kBatchCols[c], false>(g, it.idx, bsm); break; \
+    case 4 * 8 + c: mega_row<kBatchRows[c], false>(g, it.idx, bsm); break;
+            X_(0) X_(1) X_(2) X_(3) X_(4) X_(5) X_(6)
+#undef X_
+        default: break;
+        }
+        __syncthreads();  // every store of the item precedes the release
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(&done[5 * grid + pass], 1u);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------
 static int64_t row_items(int cls, const BatchGrid &g)
@@ -354,14 +509,36 @@ static size_t col_smem()
     return m;
 }
 static size_t z_smem_max() { return kBatchZSmem; }
+static size_t mega_smem() { return std::max(std::max(2 * row_smem(), col_smem()), kMegaSmem); }
+static int64_t mega_items(int pass, const BatchGrid &g)
+{
+    if (pass == 0 || pass == 4) {
+        switch (batch_row_class(g.Kx)) {
+#define X_(i) \
+    case i: return mega_row_items<kBatchRows[i]>(g);
+            X_(0) X_(1) X_(2) X_(3) X_(4) X_(5) X_(6)
+#undef X_
+        default: return 0;
+        }
+    }
+    if (pass == 2) return z_items(batch_col_class(g.Mz), g);
+    return col_items(batch_col_class(g.My), g);
+}
 
-// The device tables of one batch: grids, then the five passes' items.
+// The device tables of one batch: grids, the five passes' items, and for
+// the one-launch form its item table, the items per (grid, pass) and its
+// counters (zeroed before every launch).
 struct BatchTables {
     void *dev = nullptr;
     size_t bytes = 0;
     const BatchGrid *grids = nullptr;
     const BatchItem *items[5] = {};
     int count[5] = {};
+    const BatchItem *all = nullptr;
+    int nall = 0;
+    const uint32_t *need = nullptr;
+    uint32_t *state = nullptr;
+    size_t state_bytes = 0;
 };
 
 namespace {
@@ -384,7 +561,7 @@ bool batch_fits(int dtype_is_f32, const int64_t M[3])
            batch_col_class((int)M[2]) >= 0;
 }
 
-cudaError_t batch_enqueue(const BatchGridDesc *descs, int count, cudaStream_t st)
+cudaError_t batch_enqueue(const BatchGridDesc *descs, int count, int mode, unsigned *status, cudaStream_t st)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -400,6 +577,8 @@ cudaError_t batch_enqueue(const BatchGridDesc *descs, int count, cudaStream_t st
             e = cudaFuncSetAttribute(k_batch_y<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem());
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_batch_z, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)z_smem_max());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_batch_all, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mega_smem());
         if (e != cudaSuccess) return e;
         g_batch_attr.fetch_or(bit);
     }
@@ -448,6 +627,29 @@ cudaError_t batch_enqueue(const BatchGridDesc *descs, int count, cudaStream_t st
                 }
             }
         }
+        // the one-launch table: windows of kMegaWindow grids; (window, pass)
+        // pairs along the diagonals window + pass = d, later passes (older
+        // windows) first on a diagonal
+        std::vector<BatchItem> all;
+        std::vector<uint32_t> need((size_t)count * 5, 0);
+        const int win = kMegaWindow;
+        const int nwin = (count + win - 1) / win;
+        for (int d = 0; d < nwin + 4; ++d) {
+            for (int pass = 4; pass >= 0; --pass) {
+                const int w = d - pass;
+                if (w < 0 || w >= nwin) continue;
+                for (int i = w * win; i < count && i < (w + 1) * win; ++i) {
+                    const BatchGrid &g = grids[i];
+                    const int cls = pass == 0 || pass == 4 ? batch_row_class(g.Kx)
+                                                           : batch_col_class(pass == 2 ? g.Mz : g.My);
+                    const int64_t n = mega_items(pass, g);
+                    need[(size_t)5 * i + pass] = (uint32_t)n;
+                    for (int64_t k = 0; k < n; ++k)
+                        all.push_back(
+                            {((uint32_t)pass << kPassShift) | ((uint32_t)i << 8) | (uint32_t)cls, (uint32_t)k});
+                }
+            }
+        }
         BatchTables tb;
         tb.bytes = count * sizeof(BatchGrid);
         size_t off[5];
@@ -456,22 +658,58 @@ cudaError_t batch_enqueue(const BatchGridDesc *descs, int count, cudaStream_t st
             tb.bytes += items[p].size() * sizeof(BatchItem);
             tb.count[p] = (int)items[p].size();
         }
-        std::vector<unsigned char> host(tb.bytes);
+        const size_t off_all = tb.bytes;
+        tb.bytes += all.size() * sizeof(BatchItem);
+        tb.nall = (int)all.size();
+        const size_t off_need = tb.bytes;
+        tb.bytes += need.size() * sizeof(uint32_t);
+        const size_t off_state = (tb.bytes + 15) / 16 * 16;
+        tb.state_bytes = (2 + need.size()) * sizeof(uint32_t);
+        tb.bytes = off_state + tb.state_bytes;
+        std::vector<unsigned char> host(off_state, 0);
         memcpy(host.data(), grids.data(), count * sizeof(BatchGrid));
         for (int p = 0; p < 5; ++p) memcpy(host.data() + off[p], items[p].data(), items[p].size() * sizeof(BatchItem));
+        memcpy(host.data() + off_all, all.data(), all.size() * sizeof(BatchItem));
+        memcpy(host.data() + off_need, need.data(), need.size() * sizeof(uint32_t));
         e = cudaMalloc(&tb.dev, tb.bytes);
         if (e != cudaSuccess) return e;
-        e = cudaMemcpy(tb.dev, host.data(), tb.bytes, cudaMemcpyHostToDevice);
+        e = cudaMemcpy(tb.dev, host.data(), off_state, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             cudaFree(tb.dev);
             return e;
         }
         tb.grids = (const BatchGrid *)tb.dev;
         for (int p = 0; p < 5; ++p) tb.items[p] = (const BatchItem *)((unsigned char *)tb.dev + off[p]);
+        tb.all = (const BatchItem *)((unsigned char *)tb.dev + off_all);
+        tb.need = (const uint32_t *)((unsigned char *)tb.dev + off_need);
+        tb.state = (uint32_t *)((unsigned char *)tb.dev + off_state);
         it = g_batch_tables.emplace(key, BatchCacheEntry{tb, 0}).first;
     }
     it->second.last_use = ++g_batch_clock;
     const BatchTables &tb = it->second.tables;
+    if (mode == 2) {
+        // one persistent launch: as many CTAs as are resident
+        static std::atomic<int> mgrid{0};
+        int grid = mgrid.load();
+        if (grid == 0) {
+            int sms = 0, per = 0;
+            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_all, kMegaThreads, mega_smem());
+            if (e != cudaSuccess) return e;
+            grid = sms * (per > 0 ? per : 1);
+            mgrid.store(grid);
+        }
+        if (grid > tb.nall) grid = tb.nall;
+        e = cudaMemsetAsync(tb.state, 0, tb.state_bytes, st);
+        if (e != cudaSuccess) return e;
+        if (tb.nall) {
+            k_batch_all<<<grid, kMegaThreads, mega_smem(), st>>>(tb.grids, tb.all, tb.nall, tb.need, tb.state,
+                                                                  status);
+            count_launch();
+        }
+        return cudaGetLastError();
+    }
     if (tb.count[0]) {
         k_batch_x<true><<<tb.count[0], kBatchXThreads, row_smem(), st>>>(tb.grids, tb.items[0]);
         count_launch();

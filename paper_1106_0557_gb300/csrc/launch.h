@@ -116,10 +116,12 @@ struct BatchGridDesc {
 // Whether a grid of this dtype and doubled mesh can join a batched launch
 // (FP32, every doubled length at most 256).
 bool batch_fits(int dtype_is_f32, const int64_t M[3]);
-// The five passes of `count` such grids, one launch each, on `st`.  The
-// first call for a given set of grids builds and uploads its work tables
-// (synchronously); later calls only launch.
-cudaError_t batch_enqueue(const BatchGridDesc *grids, int count, cudaStream_t st);
+// The five passes of `count` such grids on `st`: mode 1, one launch per
+// pass; mode 2, one persistent launch for all five (per-(grid, pass)
+// completion counters; a wait that runs out sets bit 0 of *status, which
+// may be null).  The first call for a given set of grids builds and uploads
+// its work tables (synchronously); later calls only launch.
+cudaError_t batch_enqueue(const BatchGridDesc *grids, int count, int mode, unsigned *status, cudaStream_t st);
 
 // e^{-2 pi i k / n} for 0 <= k < count, by exact reduction to the first
 // octant (host, libm in double).

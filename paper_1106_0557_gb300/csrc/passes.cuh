@@ -325,8 +325,8 @@ struct ZSpecLayout {
 // ---------------------------------------------------------------------
 // Pass bodies.  Each works on one row (x passes) or one column tile (y
 // passes) and contains CTA-wide barriers, so every thread of the CTA calls it
-// the same number of times.  CG selects L2-only global loads, for data that
-// other SMs of a cluster wrote moments earlier.
+// the same number of times.  CG selects L2-only global loads (FP32 and FP64
+// points), for data that other CTAs of the same launch wrote moments earlier.
 // ---------------------------------------------------------------------
 template <bool CG, typename T>
 __device__ __forceinline__ Cx<T> ld_cx(const Cx<T> *p)
@@ -569,7 +569,7 @@ __device__ __forceinline__ void y_forward_tile(Cx<T> *__restrict__ W, const Cx<T
 }
 
 // K4 body: y inverse of a column tile of plane z, keeping rows y < Ny.
-template <typename T, int L, int TX, bool BLK = false>
+template <typename T, int L, int TX, bool BLK = false, bool CG = false>
 __device__ __forceinline__ void y_inverse_tile(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx,
                                                int z, int kx0, Cx<T> *smem, int c, int t,
                                                const Cx<T> *staged = nullptr, int zsh = 0)
@@ -586,7 +586,7 @@ __device__ __forceinline__ void y_inverse_tile(Cx<T> *__restrict__ W, const Cx<T
         if (staged)
             v[m] = active ? cswap(staged[y * TX + c]) : Cx<T>{(T)0, (T)0};
         else
-            v[m] = active ? cswap(base[(size_t)y * ys]) : Cx<T>{(T)0, (T)0};
+            v[m] = active ? cswap(ld_cx<CG>(base + (size_t)y * ys)) : Cx<T>{(T)0, (T)0};
     }
     ColXch<T, L, E, TX> xch{smem, c};
     run_stages<T, L, E, false>(v, t, tw, xch, typename Shape<T, L>::Rad{});

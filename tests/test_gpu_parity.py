@@ -190,12 +190,15 @@ def test_batch_matches_single_solves():
         p.close()
 
 
-def test_ragged_batch_of_64_runs_in_five_launches(monkeypatch):
+@pytest.mark.parametrize("mode,launches", [("1", 5), ("2", 1)])
+def test_ragged_batch_of_64_runs_in_five_launches_or_one(mode, launches, monkeypatch):
     """The config-4 batch (64 grids, each axis from {32,48,64,96,128}, FP32)
     with ISOFFT_BATCH_FUSED=1: one launch per pass over all grids (a table
-    of work items), results bitwise those of the single solves."""
+    of work items); with ISOFFT_BATCH_FUSED=2: one persistent launch for all
+    five passes (per-(grid, pass) completion counters).  Results bitwise
+    those of the single solves, and no wait ran out."""
     from paper_1106_0557_gb300 import Plan, submit_batch
-    monkeypatch.setenv("ISOFFT_BATCH_FUSED", "1")
+    monkeypatch.setenv("ISOFFT_BATCH_FUSED", mode)
     wl = sources.ragged_batch(count=64)
     plans = [Plan(w.N, w.h, "f32") for w in wl]
     srcs = [torch.from_numpy(w.source(np.float32)).cuda() for w in wl]
@@ -207,17 +210,25 @@ def test_ragged_batch_of_64_runs_in_five_launches(monkeypatch):
         o.zero_()
     submit_batch(plans, srcs, outs)
     torch.cuda.synchronize()
-    assert native.ipf_launch_count() - before == 5
+    assert native.ipf_launch_count() - before == launches
+    for p, s, o in zip(plans, srcs, outs):
+        p.check()
+        assert torch.equal(o, p.solve(s))
+    # again, after other work: the counters restart from zero every launch
+    for o in outs:
+        o.zero_()
+    submit_batch(plans, srcs, outs)
+    torch.cuda.synchronize()
     for p, s, o in zip(plans, srcs, outs):
         assert torch.equal(o, p.solve(s))
     for p in plans:
         p.close()
 
 
-@pytest.mark.parametrize("fused", ["0", "1"])
+@pytest.mark.parametrize("fused", ["0", "1", "2"])
 def test_mixed_batch_fused_and_per_grid(fused, monkeypatch):
     """A batch mixing small FP32 grids (with ISOFFT_BATCH_FUSED=1 one launch
-    per pass), an FP64 grid and an FP32 grid beyond the batched lengths
+    per pass, with 2 one launch in all), an FP64 grid and an FP32 grid beyond the batched lengths
     (their own passes on the library's streams): every result bitwise its
     single solve's, and in place (d_src = d_phi) too."""
     from paper_1106_0557_gb300 import Plan, submit_batch
