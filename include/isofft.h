@@ -88,7 +88,11 @@ enum {
                                        runs out (about 4 s) and the solve
                                        reports IPF_TIMEOUT through
                                        ipf_plan_check; its potential is then
-                                       unspecified */
+                                       unspecified.  In a batch run in one
+                                       launch (ISOFFT_BATCH_FUSED=2) the
+                                       wait of the plan's z items for its y
+                                       pass runs out instead (2 s), and the
+                                       batch's first plan reports it */
     IPF_FLAG_TEST_CANARY = 1u << 4, /* test hook: before every solve the
                                        plan's workspace is filled with NaN
                                        bytes, so a pass that read an element

@@ -1049,12 +1049,15 @@ int ipf_submit_batch(const ipf_plan_t *plans, int count, const void *const *d_sr
     unsigned *bstatus = nullptr;  // the first batched plan's status word
     for (int i = 0; i < count; ++i) {
         const ipf_plan_s *p = plans[i];
-        const bool plain = !(p->flags & (IPF_FLAG_PASS_EVENTS | IPF_FLAG_TEST_WAIT_RUNOUT | IPF_FLAG_TEST_CANARY));
+        // the run-out test hook joins a one-launch batch (its dependency
+        // wait runs out there); other hooked plans keep their own passes
+        const uint32_t hooks = IPF_FLAG_PASS_EVENTS | IPF_FLAG_TEST_CANARY | (mode == 2 ? 0u : IPF_FLAG_TEST_WAIT_RUNOUT);
+        const bool plain = !(p->flags & hooks);
         if (mode && plain && batch_fits(p->dtype == IPF_F32, p->M)) {
             if (!bstatus) bstatus = p->status;
             fused.push_back({d_src[i], d_phi[i], p->W, p->tw_x, p->rtw, p->tw_y, p->tw_z, p->spec->G, p->spec->Gs,
                              p->gscale, (int)p->N[0], (int)p->N[1], (int)p->N[2], (int)p->M[0], (int)p->M[1],
-                             (int)p->M[2]});
+                             (int)p->M[2], (p->flags & IPF_FLAG_TEST_WAIT_RUNOUT) ? 1 : 0});
         } else {
             rest.push_back(i);
         }

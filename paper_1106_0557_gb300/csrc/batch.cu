@@ -427,13 +427,17 @@ k_batch_all(const BatchGrid *__restrict__ grids, const BatchItem *__restrict__ i
         const int pass = (int)(it.grid_cls >> kPassShift), grid = (int)((it.grid_cls >> 8) & 0xFFFFFu);
         const int cls = (int)(it.grid_cls & 255u);
         if (threadIdx.x == 0) {
-            bool ok = true;
-            if (pass > 0) ok = mega_wait(&done[5 * grid + pass - 1], need[5 * grid + pass - 1], &state[1]);
-            __threadfence();
-            if (!ok) {
-                if (status) atomicOr(status, 1u);
-                atomicExch(&state[1], 1u);
+            uint32_t aborted;
+            asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];\n" : "=r"(aborted) : "l"(&state[1]) : "memory");
+            bool ok = !aborted;
+            if (ok && pass > 0) {
+                ok = mega_wait(&done[5 * grid + pass - 1], need[5 * grid + pass - 1], &state[1]);
+                if (!ok) {  // ran out (or another CTA did): flag it, stop every CTA
+                    if (status) atomicOr(status, 1u);
+                    atomicExch(&state[1], 1u);
+                }
             }
+            __threadfence();
             s_ok = ok;
         }
         __syncthreads();
@@ -643,7 +647,9 @@ cudaError_t batch_enqueue(const BatchGridDesc *descs, int count, int mode, unsig
                     const int cls = pass == 0 || pass == 4 ? batch_row_class(g.Kx)
                                                            : batch_col_class(pass == 2 ? g.Mz : g.My);
                     const int64_t n = mega_items(pass, g);
-                    need[(size_t)5 * i + pass] = (uint32_t)n;
+                    // test hook: one more y-forward item than exist, so the
+                    // grid's z items wait for it until the wait runs out
+                    need[(size_t)5 * i + pass] = (uint32_t)n + (pass == 1 && descs[i].runout ? 1u : 0u);
                     for (int64_t k = 0; k < n; ++k)
                         all.push_back(
                             {((uint32_t)pass << kPassShift) | ((uint32_t)i << 8) | (uint32_t)cls, (uint32_t)k});

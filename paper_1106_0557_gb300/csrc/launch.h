@@ -112,6 +112,7 @@ struct BatchGridDesc {
     const void *G, *Gs;
     double gscale;
     int Nx, Ny, Nz, Mx, My, Mz;
+    int runout;  // test hook (IPF_FLAG_TEST_WAIT_RUNOUT): in one launch, the z items' wait runs out
 };
 // Whether a grid of this dtype and doubled mesh can join a batched launch
 // (FP32, every doubled length at most 256).

@@ -225,6 +225,38 @@ def test_ragged_batch_of_64_runs_in_five_launches_or_one(mode, launches, monkeyp
         p.close()
 
 
+def test_one_launch_batch_wait_runs_out_and_the_gpu_stays_usable(monkeypatch):
+    """A batch in one launch whose first plan carries the run-out hook: that
+    grid's z items wait for one y-forward item more than exist, the wait
+    gives up after its limit, the launch ends (the abort flag stops every
+    CTA) and the first plan reports IPF_TIMEOUT once.  The same plans
+    without the hook then solve bitwise like single solves."""
+    from paper_1106_0557_gb300 import Plan, submit_batch
+    monkeypatch.setenv("ISOFFT_BATCH_FUSED", "2")
+    shapes = [(20, 18, 12), (16, 16, 16), (24, 10, 30), (33, 20, 8)]
+    h = (1.0, 1.0, 1.0)
+    srcs = [torch.from_numpy(rand_src(N, 60 + k).astype(np.float32)).cuda() for k, N in enumerate(shapes)]
+    outs = [torch.empty_like(x) for x in srcs]
+    plans = [Plan(shapes[0], h, "f32", flags=native.IPF_FLAG_TEST_WAIT_RUNOUT)] + [Plan(N, h, "f32")
+                                                                                   for N in shapes[1:]]
+    before = native.ipf_launch_count()
+    submit_batch(plans, srcs, outs)
+    torch.cuda.synchronize()
+    assert native.ipf_launch_count() - before == 1
+    with pytest.raises(native.IsofftError) as ei:
+        plans[0].check()
+    assert ei.value.status == native.IPF_TIMEOUT
+    plans[0].check()  # the status word was cleared
+    plans[0].close()
+    plans[0] = Plan(shapes[0], h, "f32")
+    submit_batch(plans, srcs, outs)
+    torch.cuda.synchronize()
+    for p, x, o in zip(plans, srcs, outs):
+        p.check()
+        assert torch.equal(o, p.solve(x))
+        p.close()
+
+
 @pytest.mark.parametrize("fused", ["0", "1", "2"])
 def test_mixed_batch_fused_and_per_grid(fused, monkeypatch):
     """A batch mixing small FP32 grids (with ISOFFT_BATCH_FUSED=1 one launch
