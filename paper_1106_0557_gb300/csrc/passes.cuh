@@ -478,10 +478,18 @@ __device__ __forceinline__ void x_inverse_row_at(const Cx<T> *in, In<T> *__restr
     // (The mirror point X[L-k] goes through shared memory here: a shuffle
     // from the loaded registers, as in K1, measured slower, since every
     // shuffle then waits on the row's global loads.)
+    // The row is staged for the mirror reads X[L - k].  For 256-point FP32
+    // rows (16 points a thread, 16 lanes a row) it is staged unswizzled: a
+    // half-warp's mirror reads then fall in one 16-element group (offsets
+    // 1..15) plus thread 0's read at offset 0 of the next group, 16 distinct
+    // bank pairs; the exchange swizzle would put thread 0's read on a bank
+    // pair another lane uses.  The FFT below swizzles its own exchanges.
+    constexpr bool PLAIN = sizeof(T) == 4 && L == 256 && E == 16;
+    auto at0 = [](int p) { return PLAIN ? p : RowPad<T, L>::at(p); };
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         const int k = t + m * NT;
-        line[RowPad<T, L>::at(k)] = active ? ld_cx<CG>(in + k) : Cx<T>{(T)0, (T)0};
+        line[at0(k)] = active ? ld_cx<CG>(in + k) : Cx<T>{(T)0, (T)0};
     }
     row_sync<NT>();
     // rebuild the half-length spectrum of z[m] = y[2m] + i y[2m+1]:
@@ -490,13 +498,14 @@ __device__ __forceinline__ void x_inverse_row_at(const Cx<T> *in, In<T> *__restr
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         const int k = t + m * NT;
-        const Cx<T> xk = line[RowPad<T, L>::at(k)];
+        const Cx<T> xk = line[at0(k)];
         Cx<T> a, b;
         if (k == 0) {
             a = {xk.x + xk.y, (T)0};
             b = {xk.x - xk.y, (T)0};
         } else {
-            const Cx<T> xr = cconj(line[RowPad<T, L>::at(L - k)]);
+            const Cx<T> xm = line[at0(L - k)];
+            const Cx<T> xr = cconj(xm);
             a = cadd(xk, xr);
             b = cmul(csub(xk, xr), cconj(rtw[k]));
         }
