@@ -251,19 +251,32 @@ struct ZCfg {
     static constexpr int TX = z_tile_width((int)sizeof(T), NT, L, E);
     static constexpr int COLS = 2 * TX;
     static constexpr int THREADS = COLS * NT;
+    // FP32 tiles of 8 columns (64-byte rows): a half-warp reads one position
+    // row of both line groups, whose staging regions lie a multiple of 128
+    // bytes apart, so both land on the same half of the banks (a 2-way
+    // conflict on every input read).  Line group 1 is therefore staged from
+    // plane -1 (zeros), one row later, which puts it on the other half.
+    static constexpr bool SHIFT = sizeof(T) == 4 && TX * (int)sizeof(Cx<T>) == 64;
+    static constexpr int ZROWS = LH + (SHIFT ? 1 : 0);  // rows staged per line group
     // tensor boxes: NZB equal boxes of at most 256 planes per line group
+    // (exactly LH planes, or with SHIFT at least LH + 1 in boxes of an even
+    // number of rows, so that every box starts 128-byte aligned)
     static constexpr int boxes()
     {
         int n = 1;
-        while (LH % n != 0 || LH / n > 256) ++n;
+        if (SHIFT) {
+            while ((ZROWS + n - 1) / n > 256) ++n;
+        } else {
+            while (LH % n != 0 || LH / n > 256) ++n;
+        }
         return n;
     }
     static constexpr int NZB = boxes();
-    static constexpr int BOXZ = LH / NZB;
+    static constexpr int BOXZ = SHIFT ? ((ZROWS + NZB - 1) / NZB + 1) / 2 * 2 : LH / NZB;
     static constexpr int EPC = (int)sizeof(Cx<T>) / 8;  // 8-byte tensor elements per complex
     static constexpr int GBLK = z_spec_block(TX, LH + 1, (int)sizeof(T));
     static constexpr size_t XCH = (size_t)L * COLS * sizeof(Cx<T>);
-    static constexpr size_t IN_GROUP = (size_t)LH * TX * sizeof(Cx<T>);  // one line group
+    static constexpr size_t IN_GROUP = (size_t)NZB * BOXZ * TX * sizeof(Cx<T>);  // one line group
     static constexpr size_t IN_SET = 2 * IN_GROUP;
     static constexpr size_t G_BLK = (size_t)GBLK * sizeof(T);
     static constexpr size_t G_SET = 2 * G_BLK;  // the blocks of k_y' = pr and of My/2 (pr = 0 only)
@@ -301,7 +314,8 @@ struct ZCfg {
     static_assert(MIN_BLOCKS * SMEM <= 227 * 1024, "z pass CTAs per SM exceed shared memory");
     static_assert(THREADS <= 1024, "z tile too large");
     static_assert(SMEM <= 227 * 1024, "z tile exceeds shared memory");
-    static_assert(BOXZ * NZB == LH && BOXZ <= 256, "tensor boxes must tile the half line");
+    static_assert((SHIFT ? BOXZ * NZB >= ZROWS : BOXZ * NZB == LH) && BOXZ <= 256,
+                  "tensor boxes must cover the half line");
     static_assert(TX * sizeof(Cx<T>) % 16 == 0, "tensor box rows must be multiples of 16 bytes");
     static_assert(XCH % 128 == 0 && IN_GROUP % 128 == 0 && ((size_t)BOXZ * TX * sizeof(Cx<T>)) % 128 == 0,
                   "tensor copy destinations must stay 128-byte aligned");
@@ -1039,7 +1053,8 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
         for (int zb = 0; zb < C::NZB; ++zb) {
             const size_t off = (size_t)zb * C::BOXZ * TX * sizeof(Cx<T>);
             tma_load_3d(s_in + off, &tmW, xt * TX * C::EPC, pr, zb * C::BOXZ, &bar[0]);
-            tma_load_3d(s_in + C::IN_GROUP + off, &tmW, xt * TX * C::EPC, ky1, zb * C::BOXZ, &bar[0]);
+            tma_load_3d(s_in + C::IN_GROUP + off, &tmW, xt * TX * C::EPC, ky1, zb * C::BOXZ - (C::SHIFT ? 1 : 0),
+                        &bar[0]);
         }
         T *gdst = s_g + (size_t)set * 2 * C::GBLK;
         bulk_load(gdst, G + lay.block(pr, xt), (uint32_t)C::G_BLK, &bar[0]);
@@ -1066,7 +1081,8 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
             break;
         }
         const int pr = tile / ntx, xt = tile - pr * ntx;
-        const Cx<T> *sin = reinterpret_cast<const Cx<T> *>(s_in + g * C::IN_GROUP);
+        // line group 1 staged one row later with SHIFT (its row 0 is plane -1)
+        const Cx<T> *sin = reinterpret_cast<const Cx<T> *>(s_in + g * C::IN_GROUP) + (C::SHIFT && g ? TX : 0);
         const T *sg = s_g + ((size_t)set * 2 + (pr == 0 ? g : 0)) * C::GBLK;
         z_tile<T, L, TX>(sin, sg, pr, xt, W, Gs, gscale, Nz, My, Kx, 0, c, g, t, twr, twz, xch, [] { return true; });
     }
