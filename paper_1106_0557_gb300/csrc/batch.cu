@@ -209,7 +209,8 @@ __device__ __forceinline__ void batch_z_stage(const BatchGrid &g, uint32_t idx, 
         const int gi = i / (Lh * CH), r = i % (Lh * CH), z = r / CH, q = r % CH;
         const bool ok = live && z < g.Nz;
         const Cx<float> *src = ok ? g.W + ((size_t)z * g.My + (gi == 0 ? pr : ky1)) * g.Kx + xt * TX + 2 * q : g.W;
-        cp_async<16>(s_in + (size_t)(gi * Lh + z) * TX + 2 * q, src, ok);
+        // line group 1 one row later (ZCfg::SHIFT: opposite bank halves)
+        cp_async<16>(s_in + (size_t)(gi * (Lh + (C::SHIFT ? 1 : 0)) + z) * TX + 2 * q, src, ok);
     }
     const ZSpecLayout lay{TX, ntx, Lh + 1, C::GBLK};
     for (int i = lt; i < 2 * C::GBLK / 4; i += C::THREADS) {
@@ -247,7 +248,8 @@ __device__ __forceinline__ void batch_z_compute(const BatchGrid &g, uint32_t idx
     const float *sg = s_g + (pr == 0 ? grp : 0) * C::GBLK;
     // every sub-group meets the packed column's barriers (the sub-groups'
     // tiles differ in xt)
-    z_tile<float, L, TX, true>(s_in + grp * Lh * TX, sg, pr, xt, g.W, g.Gs, g.gscale, g.Nz, g.My, Kx, 0, c, grp, t,
+    z_tile<float, L, TX, true>(s_in + grp * (Lh + (C::SHIFT ? 1 : 0)) * TX, sg, pr, xt, g.W, g.Gs, g.gscale, g.Nz,
+                               g.My, Kx, 0, c, grp, t,
                                twr, g.tw_z, xch, [] { return true; });
 }
 
