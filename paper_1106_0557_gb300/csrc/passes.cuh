@@ -289,10 +289,17 @@ struct ZCfg {
     // instead of two; the input is then staged once per tile (the next
     // tile's copies start after the first exchange's barrier, when every
     // thread has read its input).  Taken wherever the extra buffer fits the
-    // CTAs per SM (k_z_convolve; every length but 2304).  Otherwise one
-    // exchange buffer and an input set twice as wide (k_z_convolve_pairs).
+    // CTAs per SM (k_z_convolve; every length but 2304) and the tiles are
+    // wider than one 16-byte column.  Otherwise one exchange buffer and an
+    // input set twice as wide (k_z_convolve_pairs: 2304-point lines, and the
+    // 768-point lines of 16-byte points, 6.93 -> 6.62 ms for a df64 384^3
+    // solve's z pass).
     static constexpr size_t SMEM_DBX = 2 * XCH + IN_SET + 2 * G_SET + 16 + TWS;
-    static constexpr bool DBX = SMEM_DBX <= 227 * 1024 && MIN_BLOCKS * (SMEM_DBX + 1024) <= 228 * 1024;
+    // 16-byte points on 1-column tiles copy 16-byte rows; two tiles per box
+    // (the paired form) make them 32 bytes
+    static constexpr bool PAIR_NARROW = sizeof(Cx<T>) == 16 && TX == 1;
+    static constexpr bool DBX =
+        !PAIR_NARROW && SMEM_DBX <= 227 * 1024 && MIN_BLOCKS * (SMEM_DBX + 1024) <= 228 * 1024;
     static constexpr int NXB = DBX ? 2 : 1;  // exchange buffers
     static constexpr int NIN = DBX ? 1 : 2;  // input sets of one tile's width
     static constexpr size_t OFF_IN = NXB * XCH, OFF_G = OFF_IN + NIN * IN_SET, OFF_BAR = OFF_G + 2 * G_SET,
@@ -1007,7 +1014,7 @@ k_z_convolve(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, con
              unsigned *__restrict__ status, unsigned test_extra_tx)
 {
     using C = ZCfg<T, L>;
-    static_assert(C::DBX, "lines without room for two exchange buffers take k_z_convolve_pairs");
+    static_assert(C::DBX, "the paired lines take k_z_convolve_pairs");
     constexpr int E = C::E, TX = C::TX, COLS = C::COLS;
     constexpr int Lh = L / 2;
     extern __shared__ __align__(128) unsigned char zsmem[];
