@@ -518,7 +518,7 @@ ISOFFT_SHAPE(Shape32, 768, 12, 12, 4, 4, 4)
 ISOFFT_SHAPE(Shape32, 1024, 16, 16, 8, 8)
 ISOFFT_SHAPE(Shape32, 1152, 12, 12, 12, 4, 2)
 ISOFFT_SHAPE(Shape32, 1536, 12, 12, 4, 4, 4, 2)
-ISOFFT_SHAPE(Shape32, 2304, 12, 12, 12, 4, 4)
+ISOFFT_SHAPE(Shape32, 2304, 24, 24, 24, 4)
 ISOFFT_SHAPE(Shape64, 1024, 8, 8, 8, 8, 2)
 #undef ISOFFT_SHAPE
 

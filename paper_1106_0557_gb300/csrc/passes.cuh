@@ -205,7 +205,8 @@ struct ColCfg {
     static constexpr int NT = L / E;
     static constexpr int TX0 = 128 / (int)sizeof(Cx<T>);
     static constexpr int TXS = 32 / (int)sizeof(Cx<T>);  // one 32-byte sector
-    static constexpr int TXT = TX0 * NT <= 512 ? TX0 : (512 / NT >= 1 ? 512 / NT : 1);
+    static constexpr int pow2_floor(int v) { return v >= 2 ? 2 * pow2_floor(v / 2) : 1; }
+    static constexpr int TXT = TX0 * NT <= 512 ? TX0 : pow2_floor(512 / NT >= 1 ? 512 / NT : 1);
     static constexpr int TXW = TXT >= TXS || TXS * NT > 1024 ? TXT : TXS;
     static constexpr int TX = NARROW ? (TXW > 1 ? TXW / 2 : 1) : TXW;
     static constexpr int THREADS = TX * NT;
