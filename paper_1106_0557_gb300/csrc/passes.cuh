@@ -201,7 +201,7 @@ struct RowCfg {
 // per CTA, twice the CTAs).
 template <typename T, int L, bool NARROW = false>
 struct ColCfg {
-    static constexpr int E = Shape<T, L>::E;
+    static constexpr int E = YShape<T, L>::E;
     static constexpr int NT = L / E;
     static constexpr int TX0 = 128 / (int)sizeof(Cx<T>);
     static constexpr int TXS = 32 / (int)sizeof(Cx<T>);  // one 32-byte sector
@@ -576,7 +576,7 @@ __device__ __forceinline__ void y_forward_tile(Cx<T> *__restrict__ W, const Cx<T
                                                int z, int kx0, Cx<T> *smem, int c, int t,
                                                const Cx<T> *staged = nullptr, int zsh = 0)
 {
-    constexpr int E = Shape<T, L>::E, NT = L / E;
+    constexpr int E = YShape<T, L>::E, NT = L / E;
     const int kx = kx0 + c;
     const bool active = kx < Kx;
     Cx<T> *base = W + (BLK ? w_row(z, 0, L, zsh) : (size_t)z * L) * Kx + (active ? kx : 0);
@@ -592,7 +592,7 @@ __device__ __forceinline__ void y_forward_tile(Cx<T> *__restrict__ W, const Cx<T
             v[m] = ok ? ld_cx<CG>(base + (size_t)y * ys) : Cx<T>{(T)0, (T)0};
     }
     ColXch<T, L, E, TX> xch{smem, c};
-    run_stages<T, L, E, true>(v, t, tw, xch, typename Shape<T, L>::Rad{});
+    run_stages<T, L, E, true>(v, t, tw, xch, typename YShape<T, L>::Rad{});
     if (active) {
 #pragma unroll
         for (int m = 0; m < E; ++m) base[(size_t)(t + m * NT) * ys] = v[m];
@@ -605,7 +605,7 @@ __device__ __forceinline__ void y_inverse_tile(Cx<T> *__restrict__ W, const Cx<T
                                                int z, int kx0, Cx<T> *smem, int c, int t,
                                                const Cx<T> *staged = nullptr, int zsh = 0)
 {
-    constexpr int E = Shape<T, L>::E, NT = L / E;
+    constexpr int E = YShape<T, L>::E, NT = L / E;
     const int kx = kx0 + c;
     const bool active = kx < Kx;
     Cx<T> *base = W + (BLK ? w_row(z, 0, L, zsh) : (size_t)z * L) * Kx + (active ? kx : 0);
@@ -620,7 +620,7 @@ __device__ __forceinline__ void y_inverse_tile(Cx<T> *__restrict__ W, const Cx<T
             v[m] = active ? cswap(ld_cx<CG>(base + (size_t)y * ys)) : Cx<T>{(T)0, (T)0};
     }
     ColXch<T, L, E, TX> xch{smem, c};
-    run_stages<T, L, E, false>(v, t, tw, xch, typename Shape<T, L>::Rad{});
+    run_stages<T, L, E, false>(v, t, tw, xch, typename YShape<T, L>::Rad{});
     if (active) {
 #pragma unroll
         for (int m = 0; m < E / 2; ++m) {
@@ -764,7 +764,7 @@ struct ZXch {
 // ---------------------------------------------------------------------
 template <typename T, int L>
 struct YCfg {
-    static constexpr int E = Shape<T, L>::E;
+    static constexpr int E = YShape<T, L>::E;
     static constexpr int NT = L / E;
     static constexpr int CB = (int)sizeof(Cx<T>);
     static constexpr size_t smem_i(int tx) { return (size_t)3 * L * tx * CB + 16; }
@@ -848,7 +848,7 @@ k_y_pass(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, const C
         }
     };
     auto no_hook = [](int) {};
-    using Rad = typename Shape<T, L>::Rad;
+    using Rad = typename YShape<T, L>::Rad;
     typename ZTwiddles<C::TW_REGS, T, L, E, Rad>::type twr;
     twr.load(tw, t);
     int tile = blockIdx.x, it = 0;

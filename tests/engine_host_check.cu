@@ -148,6 +148,11 @@ static void check_all(const char *tag)
     check<T, XShapeF<T, 768>, 768>(tag, "xf", 20);
     check<T, XShapeF<T, 1152>, 1152>(tag, "xf", 21);
     check<T, XShape<T, 1152>, 1152>(tag, "x", 22);
+    // the y passes' own shapes (24 points a thread for FP32 lines of 384 to 2304)
+    check<T, YShape<T, 384>, 384>(tag, "y", 23);
+    check<T, YShape<T, 768>, 768>(tag, "y", 24);
+    check<T, YShape<T, 1536>, 1536>(tag, "y", 25);
+    check<T, YShape<T, 2304>, 2304>(tag, "y", 26);
 #undef SH
 }
 
