@@ -573,6 +573,22 @@ struct ZShape<float, 512> {
     using Rad = Radices<8, 8, 8>;
     static constexpr bool TW_REGS = true;
 };
+// FP32 384- and 768-point lines: 24 points a thread in three stages (24 4 4,
+// 24 8 4) instead of 12 in four or five: one or two exchanges fewer per
+// transform, at 8 warps per SM instead of 16 (about 250 registers);
+// measured 14-16 % faster (384^3 z pass 1.124 -> 0.960 ms).
+template <>
+struct ZShape<float, 384> {
+    static constexpr int E = 24;
+    using Rad = Radices<24, 4, 4>;
+    static constexpr bool TW_REGS = true;
+};
+template <>
+struct ZShape<float, 768> {
+    static constexpr int E = 24;
+    using Rad = Radices<24, 8, 4>;
+    static constexpr bool TW_REGS = true;
+};
 // 16-byte points on 768-point lines (one-column tiles of 128 threads): the
 // radix 12 goes last, where a thread's stage twiddles are shared by all its
 // butterflies (the thread count is a multiple of every stage's stride): 17

@@ -138,6 +138,7 @@ static void check_all(const char *tag)
     check<T, Shape<T, 1536>, 1536>(tag, "col", 12);
     check<T, Shape<T, 2304>, 2304>(tag, "col", 13);
     // z-pass shapes
+    check<T, ZShape<T, 384>, 384>(tag, "z", 27);
     check<T, ZShape<T, 512>, 512>(tag, "z", 14);
     check<T, ZShape<T, 768>, 768>(tag, "z", 15);
     check<T, ZShape<T, 2304>, 2304>(tag, "z", 16);
