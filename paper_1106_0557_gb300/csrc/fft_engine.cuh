@@ -90,32 +90,84 @@ __host__ __device__ constexpr double cos48(int j)
 }
 __host__ __device__ constexpr double sin48(int j) { return cos48(12 - j); }
 
-// Multiply by the compile-time root W_R^e = e^{-2 pi i e / R} (48 % R == 0).
+// cos(2 pi j / 96) for j in [0, 24], for the radices that 48 does not
+// divide (32); even j are the 48-table's values.  The odd ones were summed
+// from the Taylor series in 50-digit decimal arithmetic and rounded.
+__host__ __device__ constexpr double cos96_base(int j)
+{
+    constexpr double odd[12] = {0.9978589232386035, 0.9807852804032304, 0.9469301294951057,
+                                0.8968727415326883, 0.8314696123025452, 0.7518398074789774,
+                                0.6593458151000688, 0.5555702330196022, 0.4422886902190013,
+                                0.3214394653031616, 0.19509032201612828, 0.06540312923014306};
+    return (j & 1) ? odd[j / 2] : cos48_base(j / 2);
+}
+__host__ __device__ constexpr double cos96(int j)
+{
+    j %= 96;
+    if (j < 0) j += 96;
+    if (j > 48) j = 96 - j;
+    return j > 24 ? -cos96_base(48 - j) : cos96_base(j);
+}
+__host__ __device__ constexpr double sin96(int j) { return cos96(24 - j); }
+
+// Multiply by the compile-time root W_R^e = e^{-2 pi i e / R} (96 % R == 0).
+template <typename T, int R, int e>
+ISOFFT_HD Cx<T> mul_root96(Cx<T> a)
+{
+    static_assert(96 % R == 0, "roots of unity of 96ths");
+    constexpr int ee = ((e % R) + R) % R;
+    constexpr int j = ee * (96 / R);  // angle in units of 2 pi / 96
+    if constexpr (j != 0 && j % 24 != 0) a = crenorm(a);  // a product follows
+    if constexpr (j == 0) {
+        return a;
+    } else if constexpr (j == 24) {
+        return cmul_mi(a);  // -i
+    } else if constexpr (j == 48) {
+        return {-a.x, -a.y};
+    } else if constexpr (j == 72) {
+        return {-a.y, a.x};  // +i
+    } else if constexpr (j == 12 || j == 36 || j == 60 || j == 84) {
+        constexpr T r = (T)0.7071067811865476;
+        constexpr bool cp = cos96(j) > 0, sp = sin96(j) > 0;
+        const T cx = cp ? a.x : -a.x, cy = cp ? a.y : -a.y;
+        const T sx = sp ? a.x : -a.x, sy = sp ? a.y : -a.y;
+        return {(cx + sy) * r, (cy - sx) * r};  // normalised sums: products follow
+    } else {
+        constexpr T c = (T)cos96(j);
+        constexpr T s = (T)sin96(j);
+        return {radd(rmul(a.x, c), rmul(a.y, s)), rsub(rmul(a.y, c), rmul(a.x, s))};
+    }
+}
+
 template <typename T, int R, int e>
 ISOFFT_HD Cx<T> mul_root(Cx<T> a)
 {
-    constexpr int ee = ((e % R) + R) % R;
-    constexpr int j = ee * (48 / R);  // angle in units of 2 pi / 48
-    if constexpr (j != 0 && j % 12 != 0) a = crenorm(a);  // a product follows
-    if constexpr (j == 0) {
-        return a;
-    } else if constexpr (j == 12) {
-        return cmul_mi(a);  // -i
-    } else if constexpr (j == 24) {
-        return {-a.x, -a.y};
-    } else if constexpr (j == 36) {
-        return {-a.y, a.x};  // +i
-    } else if constexpr (j == 6 || j == 18 || j == 30 || j == 42) {
-        // |cos| = |sin| = 1/sqrt(2): a * (c - i s) with only the signs differing
-        constexpr T r = (T)0.7071067811865476;
-        constexpr bool cp = cos48(j) > 0, sp = sin48(j) > 0;
-        const T cx = cp ? a.x : -a.x, cy = cp ? a.y : -a.y;  // c a / |c|
-        const T sx = sp ? a.x : -a.x, sy = sp ? a.y : -a.y;  // s a / |s|
-        return {(cx + sy) * r, (cy - sx) * r};  // normalised sums: products follow
+    if constexpr (48 % R != 0) {
+        return mul_root96<T, R, e>(a);
     } else {
-        constexpr T c = (T)cos48(j);
-        constexpr T s = (T)sin48(j);
-        return {radd(rmul(a.x, c), rmul(a.y, s)), rsub(rmul(a.y, c), rmul(a.x, s))};
+        constexpr int ee = ((e % R) + R) % R;
+        constexpr int j = ee * (48 / R);  // angle in units of 2 pi / 48
+        if constexpr (j != 0 && j % 12 != 0) a = crenorm(a);  // a product follows
+        if constexpr (j == 0) {
+            return a;
+        } else if constexpr (j == 12) {
+            return cmul_mi(a);  // -i
+        } else if constexpr (j == 24) {
+            return {-a.x, -a.y};
+        } else if constexpr (j == 36) {
+            return {-a.y, a.x};  // +i
+        } else if constexpr (j == 6 || j == 18 || j == 30 || j == 42) {
+            // |cos| = |sin| = 1/sqrt(2): a * (c - i s) with only the signs differing
+            constexpr T r = (T)0.7071067811865476;
+            constexpr bool cp = cos48(j) > 0, sp = sin48(j) > 0;
+            const T cx = cp ? a.x : -a.x, cy = cp ? a.y : -a.y;  // c a / |c|
+            const T sx = sp ? a.x : -a.x, sy = sp ? a.y : -a.y;  // s a / |s|
+            return {(cx + sy) * r, (cy - sx) * r};  // normalised sums: products follow
+        } else {
+            constexpr T c = (T)cos48(j);
+            constexpr T s = (T)sin48(j);
+            return {radd(rmul(a.x, c), rmul(a.y, s)), rsub(rmul(a.y, c), rmul(a.x, s))};
+        }
     }
 }
 
@@ -272,6 +324,10 @@ struct Dft<T, 12> {
 template <typename T>
 struct Dft<T, 16> {
     static ISOFFT_HD void run(Cx<T> (&a)[16]) { DftCT<T, 4, 4>::run(a); }
+};
+template <typename T>
+struct Dft<T, 32> {
+    static ISOFFT_HD void run(Cx<T> (&a)[32]) { DftCT<T, 4, 8>::run(a); }
 };
 template <typename T>
 struct Dft<T, 24> {
@@ -559,8 +615,11 @@ struct YShape<float, 384> {
 };
 
 // The z pass holds two lines groups per tile and stages its prefetches in
-// shared memory; for 512-point FP32 lines it runs 16 points per thread on
-// 512 threads so the transform never competes with a 64-register cap.
+// shared memory.  512-point FP32 lines run 32 points per thread in two
+// stages (16 32): one exchange per transform instead of two with 8 8 8 (16
+// points), on 256 threads at 254 registers (8 warps per SM instead of 16):
+// 221.2 -> 198.7 us at 256^3, the shared-memory traffic and a twiddle
+// stage halved.
 // TW_REGS: the pass keeps its twiddles in registers across tiles (else it
 // reads them from the table, through L1).
 template <typename T, int L>
@@ -569,8 +628,8 @@ struct ZShape : Shape<T, L> {
 };
 template <>
 struct ZShape<float, 512> {
-    static constexpr int E = 16;
-    using Rad = Radices<8, 8, 8>;
+    static constexpr int E = 32;
+    using Rad = Radices<16, 32>;
     static constexpr bool TW_REGS = true;
 };
 // FP32 384- and 768-point lines: 24 points a thread in three stages (24 4 4,
