@@ -250,8 +250,10 @@ int ipf_noalloc_check(void *stream);
  * work enqueued on `stream` afterwards starts after the whole batch.  The
  * first batch of two or more solves on a device creates those streams; make
  * it before capturing `stream` into a CUDA graph (a capture then records the
- * batch as parallel branches).  Results are bitwise those of ipf_solve.
- * Asynchronous. */
+ * batch as parallel branches).  Results are bitwise those of ipf_solve,
+ * except that the five- and one-launch forms (ISOFFT_BATCH_FUSED=1 or 2) run
+ * z lines of 128 to 256 points in another radix order than ipf_solve: there
+ * the two agree to FP32 rounding.  Asynchronous. */
 int ipf_submit_batch(const ipf_plan_t *plans, int count, const void *const *d_src,
                      void *const *d_phi, void *stream);
 

@@ -172,9 +172,18 @@ k_batch_y(const BatchGrid *__restrict__ grids, const BatchItem *__restrict__ ite
 // this one.  (The single-solve kernel's tensor copies would need one tensor
 // map per grid.)
 // ---------------------------------------------------------------------
+// The batched z pass keeps 8 points per thread on every class (radices of 8
+// and a last 4 or 6): its CTAs of 512 threads run several tiles side by side
+// within 128 registers a thread, where the single-solve kernel's 16- and
+// 24-point shapes would spill.
+template <int L>
+struct BZShape : Shape<float, L> {
+    static constexpr bool TW_REGS = true;
+};
 template <int L>
 struct BZ {
-    using C = ZCfg<float, L>;
+    using SH = BZShape<L>;
+    using C = ZCfg<float, L, SH>;
     static constexpr int SUB = kBatchColThreads / C::THREADS;
     static_assert(SUB >= 1 && SUB * C::THREADS == kBatchColThreads, "batched z tiles fill the CTA");
     static_assert(C::TX % 2 == 0, "16-byte copies of tile rows");
@@ -229,7 +238,7 @@ __device__ __forceinline__ void batch_z_compute(const BatchGrid &g, uint32_t idx
     using B = BZ<L>;
     using C = typename B::C;
     constexpr int TX = C::TX, COLS = C::COLS, Lh = L / 2, E = C::E;
-    using Rad = typename ZShape<float, L>::Rad;
+    using Rad = typename B::SH::Rad;
     const int s = threadIdx.x / C::THREADS, lt = threadIdx.x % C::THREADS;
     const int c = lt % TX, grp = (lt / TX) & 1, t = lt / COLS;
     const int ntx = g.Kx / TX;
@@ -248,7 +257,7 @@ __device__ __forceinline__ void batch_z_compute(const BatchGrid &g, uint32_t idx
     const float *sg = s_g + (pr == 0 ? grp : 0) * C::GBLK;
     // every sub-group meets the packed column's barriers (the sub-groups'
     // tiles differ in xt)
-    z_tile<float, L, TX, true>(s_in + grp * (Lh + (C::SHIFT ? 1 : 0)) * TX, sg, pr, xt, g.W, g.Gs, g.gscale, g.Nz,
+    z_tile<float, L, TX, true, typename B::SH>(s_in + grp * (Lh + (C::SHIFT ? 1 : 0)) * TX, sg, pr, xt, g.W, g.Gs, g.gscale, g.Nz,
                                g.My, Kx, 0, c, grp, t,
                                twr, g.tw_z, xch, [] { return true; });
 }

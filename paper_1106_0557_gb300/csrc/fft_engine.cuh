@@ -590,9 +590,15 @@ struct Shape<df64, L> : Shape64<L> {};  // float pairs: register footprint of FP
 // The y passes' line shapes: Shape<T, L>, except FP32 lines where 24 points
 // a thread in three stages measured faster than 12 in four or more (one or
 // two exchanges fewer per transform, at about 168 registers and half the
-// warps).
+// warps), and 512-point lines, 32 points a thread in two stages (16 32) as in
+// the z pass (at 256^3: K2 81.1 -> 78.3 us, K4 74.1 -> 68.5 us).
 template <typename T, int L>
 struct YShape : Shape<T, L> {};
+template <>
+struct YShape<float, 512> {
+    static constexpr int E = 32;
+    using Rad = Radices<16, 32>;
+};
 template <>
 struct YShape<float, 2304> {
     static constexpr int E = 24;
@@ -632,10 +638,37 @@ struct ZShape<float, 512> {
     using Rad = Radices<16, 32>;
     static constexpr bool TW_REGS = true;
 };
-// FP32 384- and 768-point lines: 24 points a thread in three stages (24 4 4,
-// 24 8 4) instead of 12 in four or five: one or two exchanges fewer per
-// transform, at 8 warps per SM instead of 16 (about 250 registers);
-// measured 14-16 % faster (384^3 z pass 1.124 -> 0.960 ms).
+// The other FP32 lengths likewise run two or three stages of 16 to 32
+// points a thread instead of three to five of 8 or 12: one or two exchanges
+// fewer per transform, at half the warps per SM (170-255 registers).
+// Measured, z pass alone: 128 points (16 8) 22.1 -> 20.4 us at 128^2 x 64;
+// 192 (24 8) 32.7 -> 26.7 us at 128^2 x 96; 256 (16 16) 38.9 -> 32.7 us at
+// 128^3; 384 (24 4 4) and 768 (24 8 4) 14-16 % (384^3: 1.124 -> 0.960 ms);
+// 1024 (32 32) 2.90 -> 2.79 ms at 512^3.
+template <>
+struct ZShape<float, 128> {
+    static constexpr int E = 16;
+    using Rad = Radices<16, 8>;
+    static constexpr bool TW_REGS = true;
+};
+template <>
+struct ZShape<float, 192> {
+    static constexpr int E = 24;
+    using Rad = Radices<24, 8>;
+    static constexpr bool TW_REGS = true;
+};
+template <>
+struct ZShape<float, 256> {
+    static constexpr int E = 16;
+    using Rad = Radices<16, 16>;
+    static constexpr bool TW_REGS = true;
+};
+template <>
+struct ZShape<float, 1024> {
+    static constexpr int E = 32;
+    using Rad = Radices<32, 32>;
+    static constexpr bool TW_REGS = true;
+};
 template <>
 struct ZShape<float, 384> {
     static constexpr int E = 24;

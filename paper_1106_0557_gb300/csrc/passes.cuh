@@ -244,9 +244,11 @@ constexpr int z_tile_width(int rb, int nt, int L, int e)
     return tx;
 }
 
-template <typename T, int L>
+// SH: the line's shape (points per thread, radices, where the twiddles
+// live); the batched z pass takes its own (tiles that fit its CTAs).
+template <typename T, int L, typename SH = ZShape<T, L>>
 struct ZCfg {
-    static constexpr int E = ZShape<T, L>::E;
+    static constexpr int E = SH::E;
     static constexpr int NT = L / E;
     static constexpr int LH = L / 2;
     static constexpr int TX = z_tile_width((int)sizeof(T), NT, L, E);
@@ -283,7 +285,7 @@ struct ZCfg {
     static constexpr size_t G_SET = 2 * G_BLK;  // the blocks of k_y' = pr and of My/2 (pr = 0 only)
     // without register twiddles the CTA keeps the line's twiddle table in
     // shared memory (read by every stage, loaded once per CTA)
-    static constexpr bool TWR = ZShape<T, L>::TW_REGS;
+    static constexpr bool TWR = SH::TW_REGS;
     static constexpr size_t TWS = TWR ? 0 : (size_t)L * sizeof(Cx<T>);
     static constexpr int MIN_BLOCKS = sizeof(T) == 8 && E == 12 && NT >= 32 && NT <= 64 ? 3 : 1;
     // Two exchange buffers used in turn need one CTA barrier per exchange
@@ -907,13 +909,14 @@ k_y_pass(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, const C
 // offset to the tile's first column; `sg`: the spectrum block of the
 // thread's line, [kz'][TX].  `before_g` runs before the spectrum is read and
 // returns false (the same on every thread) to abandon the tile.
-template <typename T, int L, int IS, bool SYNC_ALL = false, typename TWR, typename Xch, typename BeforeG>
+template <typename T, int L, int IS, bool SYNC_ALL = false, typename SH = ZShape<T, L>, typename TWR, typename Xch,
+          typename BeforeG>
 __device__ __forceinline__ bool z_tile(const Cx<T> *sin, const T *sg, int pr, int xt, Cx<T> *__restrict__ W,
                                        const T *__restrict__ Gs, T gscale, int Nz, int My, int Kx, int zsh, int c,
                                        int g, int t, const TWR &twr, const Cx<T> *twz, Xch &xch, BeforeG before_g)
 {
-    using C = ZCfg<T, L>;
-    using Rad = typename ZShape<T, L>::Rad;
+    using C = ZCfg<T, L, SH>;
+    using Rad = typename SH::Rad;
     constexpr int E = C::E, NT = C::NT, TX = C::TX, COLS = C::COLS, Lh = L / 2;
     const int col = g * TX + c;
     const int ky = g == 0 ? pr : (pr == 0 ? My / 2 : My - pr);

@@ -142,6 +142,10 @@ static void check_all(const char *tag)
     check<T, ZShape<T, 512>, 512>(tag, "z", 14);
     check<T, ZShape<T, 768>, 768>(tag, "z", 15);
     check<T, ZShape<T, 2304>, 2304>(tag, "z", 16);
+    check<T, ZShape<T, 128>, 128>(tag, "z", 28);
+    check<T, ZShape<T, 192>, 192>(tag, "z", 29);
+    check<T, ZShape<T, 256>, 256>(tag, "z", 30);
+    check<T, ZShape<T, 1024>, 1024>(tag, "z", 31);
     // x rows (half-length complex transforms of the real rows)
     check<T, XShape<T, 16>, 16>(tag, "x", 17);
     check<T, XShape<T, 24>, 24>(tag, "x", 18);
@@ -149,7 +153,9 @@ static void check_all(const char *tag)
     check<T, XShapeF<T, 768>, 768>(tag, "xf", 20);
     check<T, XShapeF<T, 1152>, 1152>(tag, "xf", 21);
     check<T, XShape<T, 1152>, 1152>(tag, "x", 22);
-    // the y passes' own shapes (24 points a thread for FP32 lines of 384 to 2304)
+    // the y passes' own shapes (24 points a thread for FP32 lines of 384 to
+    // 2304, 32 for 512)
+    check<T, YShape<T, 512>, 512>(tag, "y", 32);
     check<T, YShape<T, 384>, 384>(tag, "y", 23);
     check<T, YShape<T, 768>, 768>(tag, "y", 24);
     check<T, YShape<T, 1536>, 1536>(tag, "y", 25);

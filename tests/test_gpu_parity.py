@@ -190,13 +190,26 @@ def test_batch_matches_single_solves():
         p.close()
 
 
+def assert_like_single(o, ref, exact):
+    """`exact`: bitwise.  Otherwise within 1e-5 of max|ref| (the FP32
+    tolerance): the five- and one-launch batch forms run the z pass of lines
+    of 128 to 256 points at 8 points a thread (their CTAs of 512 threads
+    allow 128 registers), where a single solve runs 16 or 24, so the two
+    round differently; on shorter lines they are bitwise the same."""
+    if exact:
+        assert torch.equal(o, ref)
+    else:
+        assert float((o - ref).abs().max()) <= 1e-5 * float(ref.abs().max())
+
+
 @pytest.mark.parametrize("mode,launches", [("1", 5), ("2", 1)])
 def test_ragged_batch_of_64_runs_in_five_launches_or_one(mode, launches, monkeypatch):
     """The config-4 batch (64 grids, each axis from {32,48,64,96,128}, FP32)
     with ISOFFT_BATCH_FUSED=1: one launch per pass over all grids (a table
     of work items); with ISOFFT_BATCH_FUSED=2: one persistent launch for all
-    five passes (per-(grid, pass) completion counters).  Results bitwise
-    those of the single solves, and no wait ran out."""
+    five passes (per-(grid, pass) completion counters).  Results those of
+    the single solves (bitwise where the doubled z length is at most 96,
+    else to FP32 rounding), and no wait ran out."""
     from paper_1106_0557_gb300 import Plan, submit_batch
     monkeypatch.setenv("ISOFFT_BATCH_FUSED", mode)
     wl = sources.ragged_batch(count=64)
@@ -211,16 +224,16 @@ def test_ragged_batch_of_64_runs_in_five_launches_or_one(mode, launches, monkeyp
     submit_batch(plans, srcs, outs)
     torch.cuda.synchronize()
     assert native.ipf_launch_count() - before == launches
-    for p, s, o in zip(plans, srcs, outs):
+    for w, p, s, o in zip(wl, plans, srcs, outs):
         p.check()
-        assert torch.equal(o, p.solve(s))
+        assert_like_single(o, p.solve(s), 2 * w.N[2] <= 96)
     # again, after other work: the counters restart from zero every launch
     for o in outs:
         o.zero_()
     submit_batch(plans, srcs, outs)
     torch.cuda.synchronize()
-    for p, s, o in zip(plans, srcs, outs):
-        assert torch.equal(o, p.solve(s))
+    for w, p, s, o in zip(wl, plans, srcs, outs):
+        assert_like_single(o, p.solve(s), 2 * w.N[2] <= 96)
     for p in plans:
         p.close()
 
@@ -261,8 +274,9 @@ def test_one_launch_batch_wait_runs_out_and_the_gpu_stays_usable(monkeypatch):
 def test_mixed_batch_fused_and_per_grid(fused, monkeypatch):
     """A batch mixing small FP32 grids (with ISOFFT_BATCH_FUSED=1 one launch
     per pass, with 2 one launch in all), an FP64 grid and an FP32 grid beyond the batched lengths
-    (their own passes on the library's streams): every result bitwise its
-    single solve's, and in place (d_src = d_phi) too."""
+    (their own passes on the library's streams): every result its single
+    solve's, bitwise except the batched FP32 grids' on z lines of 128 to 256
+    points (FP32 rounding), and in place (d_src = d_phi) too."""
     from paper_1106_0557_gb300 import Plan, submit_batch
     monkeypatch.setenv("ISOFFT_BATCH_FUSED", fused)
     shapes = [((40, 33, 24), "f32"), ((20, 70, 9), "f32"), ((48, 48, 48), "f64"), ((150, 20, 16), "f32"),
@@ -276,8 +290,8 @@ def test_mixed_batch_fused_and_per_grid(fused, monkeypatch):
         srcs.append(s)
     submit_batch(plans, srcs, srcs)  # in place
     torch.cuda.synchronize()
-    for p, s, r in zip(plans, srcs, singles):
-        assert torch.equal(s, r)
+    for (N, dt), p, s, r in zip(shapes, plans, srcs, singles):
+        assert_like_single(s, r, fused == "0" or dt != "f32" or 2 * N[2] <= 96)
         p.close()
 
 
