@@ -333,6 +333,10 @@ template <typename T>
 struct Dft<T, 24> {
     static ISOFFT_HD void run(Cx<T> (&a)[24]) { DftCT<T, 8, 3>::run(a); }
 };
+template <typename T>
+struct Dft<T, 48> {
+    static ISOFFT_HD void run(Cx<T> (&a)[48]) { DftCT<T, 16, 3>::run(a); }
+};
 
 // DFT of R inputs whose upper half a[R/2..R) is zero (first stage of a line
 // that is half zero padding): even bins are the length-R/2 DFT of a, odd bins
@@ -590,8 +594,10 @@ struct Shape<df64, L> : Shape64<L> {};  // float pairs: register footprint of FP
 // The y passes' line shapes: Shape<T, L>, except FP32 lines where 24 points
 // a thread in three stages measured faster than 12 in four or more (one or
 // two exchanges fewer per transform, at about 168 registers and half the
-// warps), and 512-point lines, 32 points a thread in two stages (16 32) as in
-// the z pass (at 256^3: K2 81.1 -> 78.3 us, K4 74.1 -> 68.5 us).
+// warps), 512-point lines, 32 points a thread in two stages (16 32) as in
+// the z pass (at 256^3: K2 81.1 -> 78.3 us, K4 74.1 -> 68.5 us), and
+// 2304-point lines, 48 points a thread in two stages (48 48; at 1152^3: K2
+// 13.4 -> 10.6 ms, K4 10.1 -> 9.5 ms).
 template <typename T, int L>
 struct YShape : Shape<T, L> {};
 template <>
@@ -601,8 +607,8 @@ struct YShape<float, 512> {
 };
 template <>
 struct YShape<float, 2304> {
-    static constexpr int E = 24;
-    using Rad = Radices<24, 24, 4>;
+    static constexpr int E = 48;
+    using Rad = Radices<48, 48>;
 };
 template <>
 struct YShape<float, 1536> {
@@ -700,7 +706,9 @@ struct ZShape<df64, 768> : ZShape16B768 {};
 // would not fit in registers next to its points).  FP32 takes 24 points per
 // thread and three stages, so that a tile of two columns (16 bytes, the
 // narrowest tensor-copy row) fits 384 threads; 16-byte FP64-class points
-// keep 12 per thread on one-column tiles.
+// keep 12 per thread on one-column tiles.  (48 points a thread in two
+// stages, as the y passes take, measured 11 % slower here: 192 threads, 6
+// warps per SM.)
 template <typename T>
 struct ZShape<T, 2304> : Shape<T, 2304> {
     static constexpr bool TW_REGS = false;

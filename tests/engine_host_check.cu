@@ -154,7 +154,7 @@ static void check_all(const char *tag)
     check<T, XShapeF<T, 1152>, 1152>(tag, "xf", 21);
     check<T, XShape<T, 1152>, 1152>(tag, "x", 22);
     // the y passes' own shapes (24 points a thread for FP32 lines of 384 to
-    // 2304, 32 for 512)
+    // 1536, 32 for 512, 48 for 2304)
     check<T, YShape<T, 512>, 512>(tag, "y", 32);
     check<T, YShape<T, 384>, 384>(tag, "y", 23);
     check<T, YShape<T, 768>, 768>(tag, "y", 24);
