@@ -591,19 +591,30 @@ struct Shape<double, L> : Shape64<L> {};
 template <int L>
 struct Shape<df64, L> : Shape64<L> {};  // float pairs: register footprint of FP64
 
-// The y passes' line shapes: Shape<T, L>, except FP32 lines where 24 points
-// a thread in three stages measured faster than 12 in four or more (one or
-// two exchanges fewer per transform, at about 168 registers and half the
-// warps), 512-point lines, 32 points a thread in two stages (16 32) as in
-// the z pass (at 256^3: K2 81.1 -> 78.3 us, K4 74.1 -> 68.5 us), and
-// 2304-point lines, 48 points a thread in two stages (48 48; at 1152^3: K2
-// 13.4 -> 10.6 ms, K4 10.1 -> 9.5 ms).
+// The y passes' line shapes: Shape<T, L>, except FP32 lines where fewer,
+// wider stages measured faster (one or two exchanges fewer per transform, at
+// 170-255 registers and half the warps):
+//   512 points: 16 32 (at 256^3: K2 81.1 -> 78.3 us, K4 74.1 -> 68.5 us);
+//   1024: 32 32 (at 512^3: K2 0.739 -> 0.620 ms, K4 0.595 -> 0.550 ms);
+//   384: 48 8 (at 192^3: K2 41.1 -> 37.4 us, K4 36.8 -> 36.1 us);
+//   768 and 1536: 24 8 4 and 24 8 8 (5-28 %; 48 16 at 768 was 10 % slower);
+//   2304: 48 48 (at 1152^3: K2 13.4 -> 10.6 ms, K4 10.1 -> 9.5 ms).
 template <typename T, int L>
 struct YShape : Shape<T, L> {};
 template <>
 struct YShape<float, 512> {
     static constexpr int E = 32;
     using Rad = Radices<16, 32>;
+};
+template <>
+struct YShape<float, 1024> {
+    static constexpr int E = 32;
+    using Rad = Radices<32, 32>;
+};
+template <>
+struct YShape<float, 384> {
+    static constexpr int E = 48;
+    using Rad = Radices<48, 8>;
 };
 template <>
 struct YShape<float, 2304> {
@@ -619,11 +630,6 @@ template <>
 struct YShape<float, 768> {
     static constexpr int E = 24;
     using Rad = Radices<24, 8, 4>;
-};
-template <>
-struct YShape<float, 384> {
-    static constexpr int E = 24;
-    using Rad = Radices<24, 4, 4>;
 };
 
 // The z pass holds two lines groups per tile and stages its prefetches in
@@ -733,13 +739,21 @@ struct XShape<float, 256> {
 };
 // K1's rows: FP32 rows of 768 and 1152 points run 24 points per thread in
 // three stages (two exchanges instead of three); measured 42 % and 22 %
-// faster than 12 points per thread, while K5 on the same rows was slower.
+// faster than 12 points per thread, while K5 on the same rows was slower
+// (48 24 at 1152 points: 18 % slower again).  512-point rows run 32 points
+// in two stages (32 16) instead of 8 in three: K1 0.477 -> 0.402 ms at
+// 512^3.
 template <typename T, int L>
 struct XShapeF : XShape<T, L> {};
 template <>
 struct XShapeF<float, 768> {
     static constexpr int E = 24;
     using Rad = Radices<24, 8, 4>;
+};
+template <>
+struct XShapeF<float, 512> {
+    static constexpr int E = 32;
+    using Rad = Radices<32, 16>;
 };
 template <>
 struct XShapeF<float, 1152> {
