@@ -597,6 +597,8 @@ struct Shape<df64, L> : Shape64<L> {};  // float pairs: register footprint of FP
 //   512 points: 16 32 (at 256^3: K2 81.1 -> 78.3 us, K4 74.1 -> 68.5 us);
 //   1024: 32 32 (at 512^3: K2 0.739 -> 0.620 ms, K4 0.595 -> 0.550 ms);
 //   384: 48 8 (at 192^3: K2 41.1 -> 37.4 us, K4 36.8 -> 36.1 us);
+//   256: 16 16 (at 128^3: K2 14.5 -> 12.9 us, K4 14.3 -> 12.6 us);
+//   192: 24 8 (at 96^3: K2 10.3 -> 9.4 us; 16 8 at 128 points no faster);
 //   768 and 1536: 24 8 4 and 24 8 8 (5-28 %; 48 16 at 768 was 10 % slower);
 //   2304: 48 48 (at 1152^3: K2 13.4 -> 10.6 ms, K4 10.1 -> 9.5 ms).
 template <typename T, int L>
@@ -615,6 +617,16 @@ template <>
 struct YShape<float, 384> {
     static constexpr int E = 48;
     using Rad = Radices<48, 8>;
+};
+template <>
+struct YShape<float, 256> {
+    static constexpr int E = 16;
+    using Rad = Radices<16, 16>;
+};
+template <>
+struct YShape<float, 192> {
+    static constexpr int E = 24;
+    using Rad = Radices<24, 8>;
 };
 template <>
 struct YShape<float, 2304> {

@@ -154,9 +154,12 @@ static void check_all(const char *tag)
     check<T, XShapeF<T, 1152>, 1152>(tag, "xf", 21);
     check<T, XShape<T, 1152>, 1152>(tag, "x", 22);
     // the y passes' own shapes (FP32: 48 points a thread on 384- and
-    // 2304-point lines, 32 on 512 and 1024, 24 on 768 and 1536)
+    // 2304-point lines, 32 on 512 and 1024, 24 on 192, 768 and 1536, 16 on
+    // 256)
     check<T, YShape<T, 512>, 512>(tag, "y", 32);
     check<T, YShape<T, 1024>, 1024>(tag, "y", 33);
+    check<T, YShape<T, 256>, 256>(tag, "y", 35);
+    check<T, YShape<T, 192>, 192>(tag, "y", 36);
     check<T, XShapeF<T, 512>, 512>(tag, "xf", 34);
     check<T, YShape<T, 384>, 384>(tag, "y", 23);
     check<T, YShape<T, 768>, 768>(tag, "y", 24);
