@@ -56,6 +56,8 @@ SHAPES = [
     ((64, 48, 96), (1.0, 1.0, 1.0)),
     ((100, 70, 30), (0.01, 0.01, 0.02)),
     ((7, 130, 9), (1.0, 1.0, 1.0)),
+    ((20, 120, 60), (1.0, 0.5, 1.0)),    # My = 256, Mz = 128
+    ((24, 20, 120), (1.0, 1.0, 0.5)),    # Mz = 256
 ]
 
 
