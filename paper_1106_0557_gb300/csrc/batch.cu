@@ -172,10 +172,10 @@ k_batch_y(const BatchGrid *__restrict__ grids, const BatchItem *__restrict__ ite
 // this one.  (The single-solve kernel's tensor copies would need one tensor
 // map per grid.)
 // ---------------------------------------------------------------------
-// The batched z pass keeps 8 points per thread on every class (radices of 8
-// and a last 4 or 6): its CTAs of 512 threads run several tiles side by side
+// The batched z pass keeps the 8- and 12-point shapes (three or four stages)
+// on every class: its CTAs of 512 threads run several tiles side by side
 // within 128 registers a thread, where the single-solve kernel's 16- and
-// 24-point shapes would spill.
+// 24-point shapes (lines of 128 to 256 points) would spill.
 template <int L>
 struct BZShape : Shape<float, L> {
     static constexpr bool TW_REGS = true;

@@ -195,9 +195,9 @@ def test_batch_matches_single_solves():
 def assert_like_single(o, ref, exact):
     """`exact`: bitwise.  Otherwise within 1e-5 of max|ref| (the FP32
     tolerance): the five- and one-launch batch forms run the z pass of lines
-    of 128 to 256 points at 8 points a thread (their CTAs of 512 threads
-    allow 128 registers), where a single solve runs 16 or 24, so the two
-    round differently; on shorter lines they are bitwise the same."""
+    of 128 to 256 points at 8 or 12 points a thread (their CTAs of 512
+    threads allow 128 registers), where a single solve runs 16 or 24, so the
+    two round differently; on shorter lines they are bitwise the same."""
     if exact:
         assert torch.equal(o, ref)
     else:
