@@ -726,8 +726,11 @@ k_y_inverse(Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny, int Kx,
 // the barrier of the exchange in between, which follows every read of its
 // previous use.  `hook(k)` runs after the (first) barrier of the tile's
 // exchange k, when every thread has finished what preceded that exchange;
-// `free_buf()` is a buffer that no thread still reads.
-template <typename T, int L, int E, int COLS, bool SWZ, bool DB, typename Hook>
+// `free_buf()` is a buffer that no thread still reads.  PREWAIT: thread 0
+// first waits, before that barrier, until its tensor stores have read their
+// shared-memory source (an output staging area the threads write again
+// after the barrier).
+template <typename T, int L, int E, int COLS, bool SWZ, bool DB, typename Hook, bool PREWAIT = false>
 struct ZXch {
     using Rows = ColXch<T, L, E, COLS, SWZ>;
     Cx<T> *a;  // DB: the second buffer follows at a + L COLS
@@ -745,6 +748,9 @@ struct ZXch {
         for (int q = 0; q < G::B; ++q)
 #pragma unroll
             for (int r = 0; r < R; ++r) s[Rows::row(G::out_pos(t, q, r)) * COLS + c] = v[q + r * G::B];
+        if constexpr (PREWAIT) {
+            if (threadIdx.x == 0) bulk_wait_read_all();
+        }
         __syncthreads();
         hook(k);
 #pragma unroll
@@ -762,7 +768,13 @@ struct ZXch {
 // Nz}) into the other of two staging sets while the CTA transforms the
 // current tile; completion and bounded waits as in the z pass.  Twiddles
 // stay in registers across tiles (lines up to 1024 points), and the
-// exchanges alternate between two buffers where both fit (ZXch).
+// exchanges alternate between two buffers where both fit (ZXch).  K2 on the
+// plain workspace with one exchange per transform stages its output tile in
+// the second exchange buffer, which that exchange leaves unused, and thread
+// 0 writes it by tensor stores (tmO: dims {Kx EPC, My, Nz}) after the next
+// tile's first barrier, when every thread has staged its points: the
+// threads issue shared-memory stores instead of global ones (K2 writes
+// twice what it reads).
 // ---------------------------------------------------------------------
 template <typename T, int L>
 struct YCfg {
@@ -812,14 +824,16 @@ struct YCfg {
 
 template <typename T, int L, bool FWD, bool BLK = false>
 __global__ void __launch_bounds__(YCfg<T, L>::THREADS, YCfg<T, L>::MIN_BLOCKS)
-k_y_pass(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, const Cx<T> *__restrict__ tw, int Ny,
-         int Kx, int ntiles, unsigned *__restrict__ status, int zsh)
+k_y_pass(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmO, Cx<T> *__restrict__ W,
+         const Cx<T> *__restrict__ tw, int Ny, int Kx, int ntiles, unsigned *__restrict__ status, int zsh)
 {
     using C = YCfg<T, L>;
+    using Rad = typename YShape<T, L>::Rad;
     constexpr int E = C::E, NT = C::NT, TX = C::TX;
     constexpr int NB = FWD ? C::NB_F : C::NB_I, BOX = FWD ? C::BOX_F : C::BOX_I;
     constexpr size_t IN = FWD ? C::IN_F : C::IN_I;
     constexpr bool DBX = FWD ? C::DBX_F : C::DBX_I;
+    constexpr bool TSTORE = FWD && !BLK && DBX && RadixCount<Rad>::value == 2;
     extern __shared__ __align__(128) unsigned char ysmem[];
     Cx<T> *xs = reinterpret_cast<Cx<T> *>(ysmem);            // exchange buffer(s)
     unsigned char *s_in = ysmem + (DBX ? 2 : 1) * C::XCH;  // [set][row][TX]
@@ -850,9 +864,17 @@ k_y_pass(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, const C
         }
     };
     auto no_hook = [](int) {};
-    using Rad = typename YShape<T, L>::Rad;
     typename ZTwiddles<C::TW_REGS, T, L, E, Rad>::type twr;
     twr.load(tw, t);
+    Cx<T> *so = xs + (size_t)L * TX;  // TSTORE: output staging [row][TX], 128-byte aligned
+    int prev = -1;                     // TSTORE: the tile whose staged output awaits its stores
+    auto store_prev = [&]() {          // thread 0
+        const int z = prev / ntx, xt = prev - z * ntx;
+#pragma unroll
+        for (int b = 0; b < C::NB_I; ++b)
+            tma_store_3d(&tmO, so + (size_t)b * C::BOX_I * TX, xt * TX * C::EPC, b * C::BOX_I, z);
+        bulk_commit();
+    };
     int tile = blockIdx.x, it = 0;
     bool ok = true;
     if (tid == 0 && tile < ntiles) issue(tile, 0);
@@ -865,10 +887,13 @@ k_y_pass(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, const C
             ok = false;
             break;
         }
+        if constexpr (TSTORE) {
+            if (tid == 0 && prev >= 0) store_prev();
+        }
         const int z = tile / ntx, xt = tile - z * ntx;
         const int kx = xt * TX + c;
         const Cx<T> *sin = reinterpret_cast<const Cx<T> *>(s_in + set * IN) + t * TX + c;
-        ZXch<T, L, E, TX, true, DBX, decltype(no_hook)> xch{xs, c, no_hook};
+        ZXch<T, L, E, TX, true, DBX, decltype(no_hook), TSTORE> xch{xs, c, no_hook};
         Cx<T> v[E];
         if constexpr (FWD) {
 #pragma unroll
@@ -878,7 +903,14 @@ k_y_pass(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, const C
             for (int m = 0; m < E; ++m) v[m] = cswap(sin[m * NT * TX]);
         }
         z_fft<C::TW_REGS, FWD, T, L, E>(v, t, twr, tw, xch, Rad{});
-        if (kx < Kx) {
+        if constexpr (TSTORE) {
+            // the exchange's barrier followed thread 0's wait for the previous
+            // tile's stores to read this area
+#pragma unroll
+            for (int m = 0; m < E; ++m) so[(size_t)(t + m * NT) * TX + c] = v[m];
+            fence_async_smem();
+            prev = tile;
+        } else if (kx < Kx) {
             Cx<T> *base = W + (BLK ? w_row(z, 0, L, zsh) : (size_t)z * L) * Kx + kx;
             const int ys = BLK ? Kx << zsh : Kx;  // row stride
             if constexpr (FWD) {
@@ -891,6 +923,13 @@ k_y_pass(const __grid_constant__ CUtensorMap tmW, Cx<T> *__restrict__ W, const C
                     if (y < Ny) base[(size_t)y * ys] = cswap(v[m]);
                 }
             }
+        }
+    }
+    if constexpr (TSTORE) {
+        __syncthreads();  // every thread has staged the last tile (the exit is uniform)
+        if (tid == 0) {
+            if (prev >= 0) store_prev();
+            bulk_wait_all();  // the stores have read the staging area before the CTA ends
         }
     }
     if (!ok && tid == 0) {

@@ -205,7 +205,18 @@ static cudaError_t run_y_stream(void *W, const void *tw, int Ny, int Kx, int Nz,
                zsh ? box4 : box3, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
-    k<<<grid, C::THREADS, SMEM, st>>>(map, (Cx<T> *)W, (const Cx<T> *)tw, Ny, Kx, ntiles, status, zsh);
+    // K2's output map on the plain workspace (every row y < My), for the
+    // kernels that write their tiles by tensor stores; elsewhere unused
+    CUtensorMap omap = map;
+    if (FWD && !zsh) {
+        const cuuint64_t odims[3] = {(cuuint64_t)Kx * C::EPC, (cuuint64_t)L, (cuuint64_t)Nz};
+        const cuuint32_t obox[3] = {(cuuint32_t)(C::TX * C::EPC), (cuuint32_t)C::BOX_I, 1u};
+        if (encode(&omap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, W, odims, strides3, obox, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    k<<<grid, C::THREADS, SMEM, st>>>(map, omap, (Cx<T> *)W, (const Cx<T> *)tw, Ny, Kx, ntiles, status, zsh);
     count_launch();
     return cudaGetLastError();
 }

@@ -104,6 +104,26 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
         : "memory");
 }
 
+// 3-D tiled tensor store of one box from shared memory (bulk-group
+// completion).  Elements past the tensor's extent are not written; no
+// coordinate may be negative, x times the element size must be a multiple
+// of 16 bytes, and the source must be 128-byte aligned.  The threads that
+// wrote the source run fence_async_smem() and a CTA barrier first.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, const void *src, int x, int y, int z)
+{
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];\n" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(smem_addr(src)), "r"(x), "r"(y), "r"(z)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+// until this thread's committed tensor stores have read their source
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+// until this thread's committed tensor stores are complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+// this thread's shared-memory writes become visible to the tensor copies
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
 // Time limit of one wait for a tile's copies (they normally land within
 // microseconds).
 constexpr uint64_t kCopyWaitNs = 2000000000ull;

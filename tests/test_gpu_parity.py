@@ -473,11 +473,14 @@ def test_async_host_solves_in_flight_together(dtype):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f64", "df64"])
-@pytest.mark.parametrize("N", [(64, 64, 64), (37, 200, 13), (256, 256, 40), (20, 300, 17), (9, 700, 8), (9, 1100, 8)])
+@pytest.mark.parametrize("N", [(64, 64, 64), (37, 200, 13), (256, 256, 40), (20, 300, 17), (9, 700, 8), (9, 1100, 8),
+                               (16, 8, 16), (20, 24, 9), (24, 90, 8), (40, 100, 12), (30, 150, 10), (8, 400, 8)])
 def test_y_pass_forms_are_bitwise_equal(N, dtype):
     """The three forms of the y passes (tiles, streamed, half-width tiles)
     run the same arithmetic in the same order: forcing any gives bitwise the
-    same potential, and a tuned plan picks one of the three for each pass."""
+    same potential, and a tuned plan picks one of the three for each pass.
+    M_y runs over 16, 48, 128, 192, 256, 384, 512, 768, 1024, 1536 and 2304
+    (the two-stage lines write K2's tiles by tensor stores)."""
     from paper_1106_0557_gb300 import Plan
     src = torch.from_numpy(rand_src(N, 4).astype(NP[dtype])).cuda()
     outs = []
